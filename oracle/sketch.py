@@ -1,0 +1,221 @@
+"""Sketch operators S in R^{d x m} and their application to [A | b] (steps 1-2 of the
+sketch-and-solve paradigm, Sec. 1.2).  FP64 throughout.  TEST INFRASTRUCTURE ONLY.
+
+Three families, as the paper lists them:
+
+* Clarkson-Woodruff / CountSketch (Sec. 1.2.2, the paper's default): one nonzero
+  per column of S, S[h(i), i] = s(i).  Reading: no scaling (E[S^T S] = I already,
+  and a common scale does not change the minimiser).
+* Gaussian (Sec. 1.2.1): S = G / sqrt(d) with G iid Gaussian.  Reading (the paper
+  fixes no generator): G[k, i] = T[j], j a 12-bit index drawn from the hash
+  stream, T[j] the BF16-rounded normal quantile Phi^{-1}((j + 1/2) / 4096).  Row
+  k of G uses 16-bit field (k mod 4) of SplitMix64 output i * ceil(d/4) + k // 4
+  of stream 3, and j is the top 12 bits of that field.  The tensor-core path
+  multiplies BF16 operands, so the oracle offers SA for both the exact A and the
+  BF16-rounded A.
+* Subsampled randomized Hadamard (Sec. 1.2.1): S = (1/sqrt(d)) P H D with
+  m' = 2^ceil(log2 m) (rows m..m'-1 of [A | b] are zero), H the unnormalised
+  Sylvester-Hadamard matrix H[p, i] = (-1)^popcount(p & i) applied by the fast
+  Walsh-Hadamard transform, D = diag of signs from stream 1, and P the selection
+  of d distinct rows of [0, m') drawn by Floyd's algorithm from stream 2, sorted
+  ascending.  Reading: sampling without replacement.
+"""
+import math
+
+import numpy as np
+from scipy.special import ndtri
+
+from . import hashing as H
+
+# ---------------------------------------------------------------- CountSketch
+
+def countsketch_matrix(m, d, seed):
+    """Dense CountSketch S (d x m, FP64): S[h(i), i] = s(i), zeros elsewhere."""
+    h, s = H.countsketch_hash(seed, m, d)
+    S = np.zeros((d, m))
+    S[h, np.arange(m)] = s
+    return S
+
+
+def countsketch_apply(A, d, seed):
+    """SA by the row-scatter form of the definition: SA[k] = sum over rows i with
+    h(i) = k of s(i) * A[i].  Works for a matrix or a vector; FP64."""
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    h, s = H.countsketch_hash(seed, m, d)
+    out = np.zeros((d,) + A.shape[1:])
+    signed = A * s.reshape((m,) + (1,) * (A.ndim - 1))
+    np.add.at(out, h, signed)
+    return out
+
+
+def countsketch_apply_csr(rowptr, col, val, n, d, seed):
+    """SA for A given in CSR form (rowptr of length m+1, column indices, values):
+    SA[h(i), col] += s(i) * val for every stored entry of row i.  FP64."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    m = len(rowptr) - 1
+    h, s = H.countsketch_hash(seed, m, d)
+    counts = np.diff(rowptr)
+    row_of_entry = np.repeat(np.arange(m), counts)
+    out = np.zeros((d, n))
+    np.add.at(out, (h[row_of_entry], np.asarray(col, dtype=np.int64)),
+              s[row_of_entry] * np.asarray(val, dtype=np.float64))
+    return out
+
+# ---------------------------------------------------------------- BF16 helper
+
+def round_to_bf16(x):
+    """Round FP64 values to the nearest BF16 number (8 significant bits), ties to
+    even, returned as FP64.  Normal range only (the values used here are)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0
+    mant, expo = np.frexp(x[nz])           # x = mant * 2^expo, 0.5 <= |mant| < 1
+    scaled = np.ldexp(mant, 8)             # 8 significant bits before the point
+    out[nz] = np.ldexp(np.round(scaled), expo - 8)   # np.round: half to even
+    return out
+
+
+def round_to_bf16_via_f32(x):
+    """BF16 rounding of FP32 values (round-to-nearest-even on the FP32 bit
+    pattern), returned as FP64.  Used for the A operand of the Gaussian path,
+    which starts from FP32 data."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+# ---------------------------------------------------------------- Gaussian
+
+GAUSS_TABLE_BITS = 12
+
+
+def gaussian_table():
+    """T[j] = BF16(Phi^{-1}((j + 1/2) / 4096)), j = 0..4095, as FP64."""
+    n = 1 << GAUSS_TABLE_BITS
+    q = ndtri((np.arange(n, dtype=np.float64) + 0.5) / n)
+    return round_to_bf16(q)
+
+
+def gaussian_indices(m, d, seed):
+    """Table index j[k, i] (d x m, int64) of every entry of G."""
+    groups = (d + 3) // 4
+    i = np.arange(m, dtype=np.uint64)[None, :]
+    k = np.arange(d, dtype=np.uint64)[:, None]
+    counter = i * np.uint64(groups) + (k >> np.uint64(2))
+    key = H.splitmix64_at(H.stream_state(seed, H.STREAM_GAUSSIAN), counter)
+    field = (key >> (np.uint64(16) * (k & np.uint64(3)))) & np.uint64(0xFFFF)
+    return (field >> np.uint64(4)).astype(np.int64)
+
+
+def gaussian_matrix(m, d, seed):
+    """Dense Gaussian sketch S = G / sqrt(d) (d x m, FP64)."""
+    return gaussian_table()[gaussian_indices(m, d, seed)] / math.sqrt(d)
+
+
+def gaussian_apply(A, d, seed, bf16_operand=True):
+    """SA = (G / sqrt(d)) A.  With bf16_operand the matrix A is first rounded to
+    BF16 (the operand the tensor-core path multiplies); the product is FP64."""
+    A = np.asarray(A)
+    Ause = round_to_bf16_via_f32(A) if bf16_operand else A.astype(np.float64)
+    S = gaussian_matrix(A.shape[0], d, seed)
+    return S @ Ause
+
+# ---------------------------------------------------------------- SRHT
+
+def next_pow2(m):
+    return 1 << max(0, (int(m) - 1).bit_length())
+
+
+def hadamard_matrix(mp):
+    """Unnormalised Sylvester-Hadamard matrix of order mp (a power of two):
+    H[p, i] = (-1)^popcount(p & i)."""
+    p = np.arange(mp)[:, None]
+    i = np.arange(mp)[None, :]
+    pc = np.vectorize(lambda v: bin(int(v)).count("1"))(p & i)
+    return np.where(pc % 2 == 0, 1.0, -1.0)
+
+
+def fwht(X):
+    """Unnormalised fast Walsh-Hadamard transform along axis 0 (length a power of
+    two): returns H X, by log2(len) butterfly stages (u, v) -> (u + v, u - v)."""
+    X = np.array(X, dtype=np.float64, copy=True)
+    n = X.shape[0]
+    assert n & (n - 1) == 0
+    h = 1
+    while h < n:
+        Y = X.reshape((n // (2 * h), 2, h) + X.shape[1:])
+        u = Y[:, 0].copy()
+        v = Y[:, 1].copy()
+        Y[:, 0] = u + v
+        Y[:, 1] = u - v
+        X = Y.reshape(X.shape)
+        h *= 2
+    return X
+
+
+def srht_signs(m, seed):
+    """Diagonal of D for rows 0..m-1 (float64, +-1), stream 1, bit 63."""
+    k = H.splitmix64_at(H.stream_state(seed, H.STREAM_SRHT_SIGN), np.arange(m, dtype=np.uint64))
+    return H.sign_of(k)
+
+
+def srht_sample(mp, d, seed):
+    """d distinct row indices of [0, mp), sorted ascending (Floyd's algorithm).
+
+    Step t = 0..d-1 considers the range [0, J], J = mp - d + t, draws
+    u = ((k_t mod 2^32) * (J + 1)) >> 32 with k_t output t of stream 2, and keeps u
+    unless it was already chosen, in which case it keeps J."""
+    assert 1 <= d <= mp < (1 << 32)
+    keys = H.splitmix64_at(H.stream_state(seed, H.STREAM_SRHT_SAMPLE), np.arange(d, dtype=np.uint64))
+    chosen = set()
+    for t in range(d):
+        J = mp - d + t
+        u = ((int(keys[t]) & 0xFFFFFFFF) * (J + 1)) >> 32
+        chosen.add(J if u in chosen else u)
+    return np.array(sorted(chosen), dtype=np.int64)
+
+
+def srht_matrix(m, d, seed):
+    """Dense SRHT S = (1/sqrt(d)) P H D restricted to the m real columns (d x m)."""
+    mp = next_pow2(m)
+    P = srht_sample(mp, d, seed)
+    Hm = hadamard_matrix(mp)
+    return Hm[P][:, :m] * srht_signs(m, seed)[None, :] / math.sqrt(d)
+
+
+def srht_apply(A, d, seed):
+    """SA by the fast transform: pad [A] to m' rows, multiply by D, FWHT, take the
+    sampled rows, scale by 1/sqrt(d)."""
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    mp = next_pow2(m)
+    X = np.zeros((mp,) + A.shape[1:])
+    X[:m] = A * srht_signs(m, seed).reshape((m,) + (1,) * (A.ndim - 1))
+    Y = fwht(X)
+    return Y[srht_sample(mp, d, seed)] / math.sqrt(d)
+
+# ---------------------------------------------------------------- dispatch
+
+KINDS = ("countsketch", "gaussian", "srht")
+
+
+def sketch_apply(kind, A, d, seed, bf16_operand=True):
+    if kind == "countsketch":
+        return countsketch_apply(A, d, seed)
+    if kind == "gaussian":
+        return gaussian_apply(A, d, seed, bf16_operand=bf16_operand)
+    if kind == "srht":
+        return srht_apply(A, d, seed)
+    raise ValueError(kind)
+
+
+def sketch_matrix(kind, m, d, seed):
+    if kind == "countsketch":
+        return countsketch_matrix(m, d, seed)
+    if kind == "gaussian":
+        return gaussian_matrix(m, d, seed)
+    if kind == "srht":
+        return srht_matrix(m, d, seed)
+    raise ValueError(kind)

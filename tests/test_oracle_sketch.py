@@ -1,0 +1,151 @@
+"""Pins of the oracle's sketch operators against definitions, closed forms and
+independent library routines."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.special import ndtr
+
+from oracle import hashing as H
+from oracle import sketch as S
+from oracle import solve as L
+
+
+def test_countsketch_dense_equals_scatter_exactly():
+    rng = np.random.default_rng(0)
+    A = rng.integers(-50, 50, size=(333, 9)).astype(np.float64)
+    for d in (1, 7, 64):
+        Sm = S.countsketch_matrix(333, d, seed=11)
+        assert np.array_equal(Sm @ A, S.countsketch_apply(A, d, 11))
+
+
+def test_countsketch_structure_one_signed_entry_per_column():
+    Sm = S.countsketch_matrix(500, 40, seed=2)
+    assert np.array_equal(np.abs(Sm).sum(axis=0), np.ones(500))
+    assert set(np.unique(Sm)) <= {-1.0, 0.0, 1.0}
+    h, s = H.countsketch_hash(2, 500, 40)
+    assert np.array_equal(Sm[h, np.arange(500)], s)
+
+
+def test_countsketch_isometry_in_expectation():
+    # E ||S x||^2 = ||x||^2 (E[S^T S] = I)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(400)
+    vals = [np.linalg.norm(S.countsketch_apply(x, 32, seed)) ** 2 for seed in range(400)]
+    se = np.std(vals) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - x @ x) < 4 * se
+
+
+def test_countsketch_csr_equals_dense():
+    from synth import csr_problem
+    A, b, _ = csr_problem(300, 20, seed=4, density=0.2, n_dense=3)
+    ref = S.countsketch_apply(A.to_dense(), 50, 9)
+    got = S.countsketch_apply_csr(A.rowptr, A.col, A.val, A.n, 50, 9)
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(2)
+    x = (rng.standard_normal(100000) * np.exp(rng.uniform(-20, 20, 100000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.round_to_bf16_via_f32(x), ref)
+    assert np.array_equal(S.round_to_bf16(x.astype(np.float64)), ref)
+
+
+def test_gaussian_table_is_normal_quantiles():
+    T = S.gaussian_table()
+    n = T.size
+    assert n == 4096
+    assert np.array_equal(T, -T[::-1])                           # symmetric
+    assert np.all(np.diff(T) >= 0)                               # monotone
+    # each entry is a BF16 number within half a BF16 ulp of the exact quantile:
+    # Phi(T[j]) brackets (j + 1/2)/4096 between the neighbouring BF16 values
+    p = (np.arange(n) + 0.5) / n
+    ulp = np.ldexp(1.0, np.frexp(T)[1] - 8)
+    assert np.all(ndtr(T - ulp / 2) <= p + 1e-15)
+    assert np.all(ndtr(T + ulp / 2) >= p - 1e-15)
+    assert abs(T.mean()) < 1e-12 and abs((T ** 2).mean() - 1) < 2e-3
+
+
+def test_gaussian_indices_uniform_and_field_layout():
+    d, m = 10, 2000
+    j = S.gaussian_indices(m, d, seed=5)
+    assert j.shape == (d, m) and j.min() >= 0 and j.max() < 4096
+    counts = np.bincount(j.ravel() >> 6, minlength=64)          # 64 coarse bins
+    e = j.size / 64
+    assert ((counts - e) ** 2 / e).sum() < 64 + 6 * math.sqrt(128)
+    # row k uses the top 12 bits of 16-bit field k % 4 of output i*ceil(d/4) + k//4
+    key = H.splitmix64_at(H.stream_state(5, 3), np.array([7 * 3 + 2], dtype=np.uint64))
+    assert j[9, 7] == (int(key[0]) >> (16 * 1 + 4)) & 0xFFF
+
+
+def test_gaussian_sketch_and_solve_expected_residual():
+    # For Gaussian S with d > n + 1: E ||A x^ - b||^2 = (1 + n/(d-n-1)) ||A x* - b||^2.
+    rng = np.random.default_rng(3)
+    m, n, d = 1500, 8, 30
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    _, rn = L.exact_lstsq(A, b)
+    ratios = []
+    for seed in range(250):
+        Sm = S.gaussian_matrix(m, d, seed)
+        x, _, _ = L.sketch_and_solve(Sm @ A, Sm @ b)
+        ratios.append(np.linalg.norm(A @ x - b) ** 2 / rn ** 2)
+    expect = 1 + n / (d - n - 1)
+    se = np.std(ratios) / math.sqrt(len(ratios))
+    assert abs(np.mean(ratios) - expect) < 3.5 * se
+
+
+def test_gaussian_apply_bf16_operand():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((100, 5)).astype(np.float32)
+    Ab = torch.from_numpy(A).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.allclose(S.gaussian_apply(A, 12, 1, bf16_operand=True), S.gaussian_matrix(100, 12, 1) @ Ab,
+                       rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("mp", [1, 2, 4, 64, 1024, 4096])
+def test_hadamard_orthogonality(mp):
+    Hm = S.hadamard_matrix(mp)
+    assert np.array_equal(Hm @ Hm.T, mp * np.eye(mp))
+    if mp >= 2:   # Sylvester recursion H_{2k} = [[H_k, H_k], [H_k, -H_k]]
+        h = S.hadamard_matrix(mp // 2)
+        assert np.array_equal(Hm, np.block([[h, h], [h, -h]]))
+
+
+@pytest.mark.parametrize("mp", [1, 2, 8, 512, 2048])
+def test_fwht_equals_explicit_product(mp):
+    rng = np.random.default_rng(mp)
+    X = rng.standard_normal((mp, 3))
+    assert np.allclose(S.fwht(X), S.hadamard_matrix(mp) @ X, rtol=0, atol=1e-10)
+
+
+def test_srht_sample_properties_and_uniformity():
+    for (mp, d) in [(1, 1), (16, 16), (1024, 10), (1 << 20, 1024)]:
+        P = S.srht_sample(mp, d, seed=3)
+        assert P.size == d and np.all(np.diff(P) > 0) and P[0] >= 0 and P[-1] < mp
+    # Floyd's algorithm: every d-subset equally likely (mp = 5, d = 2: 10 subsets)
+    counts = {}
+    for seed in range(5000):
+        key = tuple(S.srht_sample(5, 2, seed))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 10
+    c = np.array(list(counts.values()))
+    assert ((c - 500) ** 2 / 500).sum() < 35          # chi2(9) far tail
+
+
+@pytest.mark.parametrize("m", [1, 5, 64, 300])
+def test_srht_fast_equals_dense(m):
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, 4))
+    d = min(S.next_pow2(m), 16)
+    assert np.allclose(S.srht_apply(A, d, 8), S.srht_matrix(m, d, 8) @ A, rtol=0, atol=1e-10)
+
+
+def test_srht_isometry_in_expectation():
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(200)
+    vals = [np.linalg.norm(S.srht_apply(x, 32, seed)) ** 2 for seed in range(300)]
+    se = np.std(vals) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - x @ x) < 4 * se

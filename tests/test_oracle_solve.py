@@ -1,0 +1,131 @@
+"""Pins of the oracle's solvers: LAPACK/SciPy routines, consistent systems,
+identity/permutation sketches, brute-force normal equations, closed forms."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.sparse.linalg import lsqr as scipy_lsqr
+
+from oracle import sketch as S
+from oracle import solve as L
+from synth import gaussian_problem, ill_conditioned_problem
+
+
+def _q_from(V, tau):
+    p = V.shape[0]
+    Q = np.eye(p)
+    for j in reversed(range(V.shape[1])):      # Q = H_0 H_1 ... H_{q-1}
+        v = V[j:, j]
+        Q[j:, :] -= tau[j] * np.outer(v, v @ Q[j:, :])
+    return Q
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (5, 5), (40, 7), (257, 64)])
+def test_householder_qr_factorisation(shape):
+    rng = np.random.default_rng(shape[0])
+    M = rng.standard_normal(shape)
+    R, V, tau = L.householder_qr(M)
+    Q = _q_from(V, tau)
+    q = shape[1]
+    assert np.allclose(Q.T @ Q, np.eye(shape[0]), atol=1e-13)
+    assert np.allclose(Q[:, :q] @ R, M, atol=1e-13)
+    assert np.array_equal(R, np.triu(R))
+    Rl = np.linalg.qr(M, mode="r")             # LAPACK geqrf
+    assert np.allclose(np.abs(np.diag(R)), np.abs(np.diag(Rl)), rtol=1e-12)
+    y = rng.standard_normal(shape[0])
+    assert np.allclose(L.apply_qt(V, tau, y), Q.T @ y, atol=1e-12)
+
+
+def test_triangular_solves_match_scipy():
+    rng = np.random.default_rng(1)
+    R = np.triu(rng.standard_normal((30, 30))) + 5 * np.eye(30)
+    z = rng.standard_normal(30)
+    assert np.allclose(L.back_solve(R, z), sla.solve_triangular(R, z), rtol=1e-12)
+    assert np.allclose(L.forward_solve_transposed(R, z), sla.solve_triangular(R, z, trans="T"), rtol=1e-12)
+
+
+def test_exact_lstsq_matches_lapack():
+    A, b, _ = ill_conditioned_problem(2000, 30, seed=3, kappa=1e4, noise=1e-3, dtype=np.float64)
+    x, rn = L.exact_lstsq(A, b)
+    xr = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e4 * 1e-14
+    assert np.isclose(rn, np.linalg.norm(A @ xr - b), rtol=1e-10)
+
+
+def test_consistent_system_recovers_x_true():
+    # paper config 1 shape: 4096 x 64 FP64 N(0,1), CountSketch d = 256, seed 0
+    A, _, x_true = gaussian_problem(4096, 64, seed=1001)
+    b = A @ x_true
+    SA, Sb = S.countsketch_apply(A, 256, 0), S.countsketch_apply(b, 256, 0)
+    x, _, rn = L.sketch_and_solve(SA, Sb)
+    assert np.linalg.norm(x - x_true) / np.linalg.norm(x_true) < 1e-13
+    assert rn < 1e-10
+
+
+def test_identity_and_permutation_sketch_reduce_to_plain_lstsq():
+    A, b, _ = gaussian_problem(200, 6, seed=2, noise=1.0)
+    xr = np.linalg.lstsq(A, b, rcond=None)[0]
+    x, _, _ = L.sketch_and_solve(A, b)
+    assert np.allclose(x, xr, rtol=1e-12, atol=1e-13)
+    perm = np.random.default_rng(0).permutation(200)
+    x2, _, _ = L.sketch_and_solve(A[perm], b[perm])
+    assert np.allclose(x2, xr, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", S.KINDS)
+def test_sketch_and_solve_brute_force_normal_equations(kind):
+    A, b, _ = gaussian_problem(120, 5, seed=7, noise=0.5)
+    d = 32
+    SA, Sb = S.sketch_apply(kind, A, d, 3, bf16_operand=False), S.sketch_apply(kind, b, d, 3, bf16_operand=False)
+    x, _, rn = L.sketch_and_solve(SA, Sb)
+    xn = np.linalg.solve(SA.T @ SA, SA.T @ Sb)
+    assert np.allclose(x, xn, rtol=1e-9, atol=1e-12)
+    assert np.isclose(rn, np.linalg.norm(SA @ x - Sb), rtol=1e-10)
+
+
+@pytest.mark.parametrize("kind", S.KINDS)
+def test_residual_ratio_bound_config1(kind):
+    A, b, _ = gaussian_problem(4096, 64, seed=1001)
+    x_star, rn = L.exact_lstsq(A, b)
+    SA, Sb = S.sketch_apply(kind, A, 256, 0, bf16_operand=False), S.sketch_apply(kind, b, 256, 0, bf16_operand=False)
+    x, _, _ = L.sketch_and_solve(SA, Sb)
+    ratio = np.linalg.norm(A @ x - b) / rn
+    assert 1.0 <= ratio <= 2.0
+
+
+def test_rank_deficient_detected():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((50, 4))
+    A[:, 3] = A[:, 0] + A[:, 1]
+    with pytest.raises(L.RankDeficient):
+        L.sketch_and_solve(A, rng.standard_normal(50))
+
+
+def test_eta_zero_at_solution_and_positive_elsewhere():
+    A, b, _ = gaussian_problem(500, 10, seed=4, noise=0.1)
+    x, _ = L.exact_lstsq(A, b)
+    assert L.eta(A, b, x) < 1e-14
+    assert L.eta(A, b, x + 1e-3) > 1e-6
+
+
+def test_lsqr_iterates_match_scipy_lsqr():
+    # with R = I the iteration is plain LSQR: compare iterates after k steps
+    A, b, _ = gaussian_problem(300, 12, seed=5, noise=0.3)
+    for k in (1, 3, 6):
+        x, it, _ = L.lsqr_preconditioned(A, b, np.eye(12), np.zeros(12), tol=0.0, max_iter=k)
+        xs = scipy_lsqr(A, b, atol=0, btol=0, iter_lim=k)[0]
+        assert it == k
+        assert np.allclose(x, xs, rtol=1e-10, atol=1e-12)
+
+
+def test_sap_fixed_point_is_exact_solution_ill_conditioned():
+    A, b, _ = ill_conditioned_problem(3000, 20, seed=6, kappa=1e8, noise=1e-4, dtype=np.float64)
+    x_star, _ = L.exact_lstsq(A, b)
+    SA, Sb = S.countsketch_apply(A, 80, 1), S.countsketch_apply(b, 80, 1)
+    x, it, est, xhat = L.sketch_and_precondition(A, b, SA, Sb, tol=1e-15, max_iter=200)
+    assert np.linalg.norm(x - x_star) / np.linalg.norm(x_star) < 1e8 * 1e-14
+    # eta at the FP64 rounding floor of forming r itself (that of LAPACK's answer)
+    xr = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert L.eta(A, b, x) < 10 * L.eta(A, b, xr) + 1e-14
+    # preconditioned LSQR needs far fewer iterations than plain LSQR here
+    _, it_plain, _ = L.lsqr_preconditioned(A, b, np.eye(20), xhat, tol=1e-10, max_iter=200)
+    assert it < it_plain
