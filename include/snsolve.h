@@ -1,0 +1,203 @@
+/*
+ * snsolve.h -- C ABI of a GB300 (sm_103a) library for randomized least squares
+ * by sketch-and-solve and sketch-and-precondition.
+ *
+ * Problem (Eq. 1 of "Sketch 'n Solve", arXiv 2409.14309, Sec. 1.3):
+ *     min_x || A x - b ||_2^2,   A in R^{m x n}, b in R^m, m >> n.
+ * Sketch-and-solve (Sec. 1.2 steps 1-3 and the reduced problem of Sec. 1.3):
+ * draw S in R^{d x m} (d >= n), form SA and Sb, and solve
+ *     min_x^ || SA x^ - Sb ||_2^2
+ * by an FP64 Householder QR of [SA | Sb] and back substitution.
+ * Sketch-and-precondition (SAP-SAS, Sec. 2.1): when a tolerance below what
+ * sketch-and-solve reaches is asked for, R from that QR right-preconditions an
+ * iterative solve on the original A, started from x^.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrix and vector arguments are DEVICE pointers owned by the caller
+ *    (unless stated otherwise).  Dense matrices are row-major with a leading
+ *    dimension in elements.
+ *  - Work is enqueued on the caller's `stream` (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream).  Argument errors are
+ *    returned synchronously before anything is launched.
+ *  - The library allocates no device memory on any compute path: scratch is a
+ *    caller-provided workspace whose size comes from the matching *_size query.
+ *    A workspace must be 256-byte aligned.
+ *  - There is no CPU fallback: every arithmetic step runs in this library's
+ *    CUDA kernels.  A missing or non-sm_103a device yields SNS_ECUDA.
+ *  - Functions are thread-safe for distinct contexts; one context may be used
+ *    from several threads if each call uses its own stream and workspace.
+ */
+#ifndef SNSOLVE_H
+#define SNSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every call and stored in sns_info.status. */
+typedef enum {
+  SNS_OK = 0,
+  SNS_EINVAL = 1,    /* invalid argument (shape, pointer, alignment, option) */
+  SNS_ENOMEM = 2,    /* workspace too small / server pool exhausted */
+  SNS_ERANK = 3,     /* |R_jj| <= n * 2^-53 * max_i |R_ii| in the QR of SA */
+  SNS_ENOTCONV = 4,  /* iteration cap reached before the tolerance */
+  SNS_EAGAIN = 5,    /* request not finished yet (poll) */
+  SNS_ETIMEOUT = 6,  /* bounded wait expired (poll, or a device-side wait) */
+  SNS_ECUDA = 7,     /* CUDA runtime error; see snsolve_last_cuda_error */
+  SNS_EBUDGET = 8    /* one request alone exceeds the server's HBM budget */
+} sns_status;
+
+/* Sketch families (Sec. 1.2.1 dense: Gaussian, Hadamard; Sec. 1.2.2 sparse:
+ * Clarkson-Woodruff, the paper's default). */
+typedef enum {
+  SNS_COUNTSKETCH = 0,  /* S[h(i), i] = s(i): one signed nonzero per column */
+  SNS_GAUSSIAN = 1,     /* S = G / sqrt(d), G from a BF16 normal-quantile table */
+  SNS_SRHT = 2          /* S = P H D / sqrt(d) on m' = 2^ceil(log2 m) rows */
+} sns_sketch_kind;
+
+/* Storage of A (the paper handles dense and sparse A through one interface,
+ * Sec. 2.1). */
+typedef enum {
+  SNS_DENSE_F32 = 0,    /* A float, row-major, lda >= n; b float */
+  SNS_DENSE_F64 = 1,    /* A double, row-major, lda >= n; b double */
+  SNS_CSR_F32 = 2       /* CSR: rowptr int64[m+1], col int32[nnz], val float[nnz]; b float */
+} sns_format;
+
+/* CountSketch variants. */
+typedef enum {
+  SNS_CS_AUTO = 0,          /* library picks (deterministic unless d is too large) */
+  SNS_CS_SORTED = 1,        /* bucket-sorted segmented sum: bitwise reproducible */
+  SNS_CS_STREAM = 2         /* one streaming pass with vector reductions into SA (order of
+                               additions varies run to run) */
+} sns_cs_variant;
+
+/* Implicit sketch descriptor.  S is never stored: its entries are functions of
+ * (seed, row index) through the SplitMix64 counter-based stream (Steele, Lea &
+ * Flood 2014): output i of stream t is mix64((seed ^ (t << 56)) + (i+1)*gamma).
+ * CountSketch (t = 0): h(i) = ((k mod 2^32) * d) >> 32, s(i) = bit 63 ? -1 : +1.
+ * SRHT: signs from t = 1, d distinct rows of [0, m') by Floyd's algorithm on t = 2.
+ * Gaussian: G[k, i] = T[12-bit field (k mod 4) of output i*ceil(d/4) + k/4 of t = 3],
+ * T[j] = BF16(Phi^-1((j + 1/2)/4096)). */
+typedef struct {
+  int32_t kind;        /* sns_sketch_kind */
+  int32_t variant;     /* sns_cs_variant (CountSketch only; ignored otherwise) */
+  int64_t d;           /* sketch rows, n <= d; SRHT also d <= m' */
+  uint64_t seed;
+} sns_sketch_desc;
+
+/* One least-squares problem. */
+typedef struct {
+  int64_t m, n;
+  int32_t fmt;             /* sns_format */
+  int32_t reserved;
+  const void* A;           /* dense: m x n row-major, leading dimension lda */
+  int64_t lda;
+  const int64_t* rowptr;   /* CSR only */
+  const int32_t* col;      /* CSR only, each in [0, n) */
+  const float* val;        /* CSR only */
+  int64_t nnz;             /* CSR only: rowptr[m] */
+  const void* b;           /* m entries, float (F32, CSR) or double (F64) */
+} sns_problem;
+
+/* Solve options. tol <= 0: sketch-and-solve only.  tol > 0: after
+ * sketch-and-solve, eta(x) = ||A^T r|| / (||A||_F ||r||), r = b - A x, is
+ * computed with FP64-class accumulation; while eta > tol the solver runs
+ * R-preconditioned refinement steps (SAP-SAS) up to max_iter FP32 passes. */
+typedef struct {
+  sns_sketch_desc sk;
+  double tol;
+  int32_t max_iter;        /* cap on inner passes over A (0 = library default 400) */
+  int32_t inner;           /* inner CG steps per refinement step (0 = default) */
+  int32_t precondition;    /* 1 = R from QR(SA) (default when nonzero); 0 = R = I
+                              (unpreconditioned reference iteration) */
+  int32_t reserved;
+} sns_opts;
+
+/* Per-solve report. */
+typedef struct {
+  int32_t status;          /* sns_status of the solve */
+  int32_t iters;           /* inner passes over A (FP32 normal-equation passes) */
+  int32_t outer;           /* FP64-class residual passes */
+  int32_t reserved;
+  double eta;              /* final eta(x) (tol > 0), else 0 */
+  double resid_norm;       /* ||b - A x|| (tol > 0), else 0 */
+  double sketch_resid;     /* ||SA x^ - Sb|| from the QR: |R_aug[n, n]| */
+} sns_info;
+
+typedef struct sns_ctx sns_ctx;
+
+/* Create a context on CUDA device `device`.  Checks that the device is
+ * sm_103 and that the library's kernels load.  *ctx is NULL on failure. */
+sns_status snsolve_create(sns_ctx** ctx, int device);
+void snsolve_destroy(sns_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* snsolve_status_string(int status);
+/* Last CUDA error string seen by this thread (static thread-local storage). */
+const char* snsolve_last_cuda_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int snsolve_version(void);
+
+/* ---- Step 2 of the paradigm (Sec. 1.2): SA and Sb -------------------------
+ * Workspace bytes needed by snsolve_sketch for this problem and sketch. */
+sns_status snsolve_sketch_workspace_size(const sns_problem* prob, const sns_sketch_desc* sk,
+                                         size_t* bytes);
+
+/* SA = S A (d x n, row-major, leading dimension ldsa >= n) and Sb = S b
+ * (d entries).  SA and Sb are float for F32/CSR input and double for F64 input.
+ * Gaussian sketches multiply BF16-rounded A in the tensor cores with FP32
+ * accumulation (F32 input only).  Asynchronous on `stream`. */
+sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk,
+                          void* SA, int64_t ldsa, void* Sb,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Step 3 (Sec. 1.2) and SAP-SAS (Sec. 2.1) ------------------------------
+ * Workspace bytes for snsolve_lstsq. */
+sns_status snsolve_lstsq_workspace_size(const sns_problem* prob, const sns_opts* opts,
+                                        size_t* bytes);
+
+/* Least-squares solve.  x: n doubles (device).  info: HOST pointer, filled
+ * before return.  With tol <= 0 the call is asynchronous except that it waits
+ * for the QR's rank check; with tol > 0 it synchronizes `stream` between
+ * refinement steps (convergence scalars are computed on the device and read
+ * from pinned memory).  Returns the same status as info->status. */
+sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* opts,
+                         double* x, sns_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Batched sketch-and-solve ----------------------------------------------
+ * nprob independent dense F32 problems (each d = opts[i].sk.d, CountSketch),
+ * solved by one fused persistent launch per stage (sketch, QR, back-solve)
+ * that is captured once into a CUDA graph and replayed.  probs, opts, x and
+ * infos are HOST arrays of length nprob; x[i] is a device pointer to n_i
+ * doubles; infos may be NULL.  Synchronizes `stream` before returning. */
+sns_status snsolve_lstsq_batched_workspace_size(const sns_problem* probs, const sns_opts* opts,
+                                                int nprob, size_t* bytes);
+sns_status snsolve_lstsq_batched(sns_ctx* ctx, const sns_problem* probs, const sns_opts* opts,
+                                 int nprob, double* const* x, sns_info* infos,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Serving: continuous batching over a fixed device pool -----------------
+ * A server owns one worker thread and `hbm_budget_bytes` of device memory
+ * (allocated once here; never during serving).  Requests are admitted while
+ * their footprint fits the free budget and a slot is free; admitted requests'
+ * work overlaps on the device.  Problem pointers given to submit must stay
+ * valid until the request is polled done. */
+typedef struct sns_server sns_server;
+sns_status snsolve_server_create(sns_server** srv, sns_ctx* ctx, size_t hbm_budget_bytes,
+                                 int max_slots);
+void snsolve_server_destroy(sns_server* srv);
+/* Queue a request; x is a device pointer to n doubles.  SNS_EBUDGET when the
+ * request's footprint alone exceeds the budget. */
+sns_status snsolve_submit(sns_server* srv, const sns_problem* prob, const sns_opts* opts,
+                          double* x, uint64_t* req_id);
+/* SNS_OK with *info filled once done; SNS_EAGAIN if still pending after
+ * timeout_us microseconds (0 = do not wait). */
+sns_status snsolve_poll(sns_server* srv, uint64_t req_id, int64_t timeout_us, sns_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNSOLVE_H */

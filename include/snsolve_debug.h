@@ -1,0 +1,49 @@
+/*
+ * snsolve_debug.h -- verification entry points of the snsolve library.
+ *
+ * They expose, bit for bit, the random structure of the implicit sketch S as
+ * the library's kernels compute it ("generate a sketch matrix S", step 1 of the
+ * sketch-and-solve paradigm, Sec. 1.2 of arXiv 2409.14309), so tests can compare
+ * it with an independent implementation.  Not needed to solve problems.
+ * Device pointers unless stated; asynchronous on `stream` like snsolve.h.
+ */
+#ifndef SNSOLVE_DEBUG_H
+#define SNSOLVE_DEBUG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "snsolve.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CountSketch bucket h(i) in [0, d) and sign s(i) in {-1, +1} of rows 0..m-1
+ * (Clarkson-Woodruff sketch, Sec. 1.2.2): h and s are device arrays of m
+ * entries.  SNS_EINVAL if m < 0, d < 1 or a pointer is NULL. */
+sns_status snsolve_debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s,
+                                          void* stream);
+
+/* Raw 64-bit outputs start..start+count-1 of SplitMix64 stream `stream_id`
+ * (0 = CountSketch, 1 = SRHT signs, 2 = SRHT sampling, 3 = Gaussian) for
+ * `seed`; keys is a device array of count entries. */
+sns_status snsolve_debug_stream_keys(uint64_t seed, int stream_id, int64_t start, int64_t count, uint64_t* keys,
+                                     void* stream);
+
+/* The d sorted, distinct SRHT row indices of [0, mp) (mp a power of two,
+ * 1 <= d <= min(mp, 16384), Sec. 1.2.1 Hadamard sketch), written to idx
+ * (device, d int64).  ws: device workspace of snsolve_debug_srht_sample_ws
+ * bytes. */
+sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes);
+sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* idx, void* ws, size_t ws_bytes,
+                                     void* stream);
+
+/* The 4096-entry BF16 normal-quantile table T of the Gaussian sketch
+ * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array. */
+sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNSOLVE_DEBUG_H */

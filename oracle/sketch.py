@@ -219,3 +219,17 @@ def sketch_matrix(kind, m, d, seed):
     if kind == "srht":
         return srht_matrix(m, d, seed)
     raise ValueError(kind)
+
+
+def countsketch_rows(A, d, seed, rows):
+    """Selected output rows k of SA (and of Sb when A is a vector) straight from
+    the definition SA[k] = sum over i with h(i) = k of s(i) A[i]; FP64.  Used to
+    check full-size results one output row at a time."""
+    A = np.asarray(A)
+    m = A.shape[0]
+    h, s = H.countsketch_hash(seed, m, d)
+    out = []
+    for k in rows:
+        idx = np.nonzero(h == k)[0]
+        out.append((s[idx].reshape((-1,) + (1,) * (A.ndim - 1)) * A[idx].astype(np.float64)).sum(axis=0))
+    return np.array(out)

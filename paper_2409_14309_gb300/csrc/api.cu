@@ -1,0 +1,371 @@
+// C ABI of snsolve: argument validation, workspace layout and the solve driver
+// (sketch -> FP64 QR -> back-solve -> optional preconditioned refinement).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "snsolve.h"
+#include "snsolve_debug.h"
+
+struct sns_ctx {
+  int device;
+  double* pinned;   // host pinned scalars (eta, ||r||, ||g||, ||A||_F, status, sres, ...)
+};
+
+namespace sns {
+
+static thread_local char t_err[256] = "";
+
+sns_status record_cuda_error(cudaError_t e) {
+  snprintf(t_err, sizeof(t_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return SNS_ECUDA;
+}
+
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static bool is_f64(const sns_problem* p) { return p->fmt == SNS_DENSE_F64; }
+
+static sns_status validate_problem(const sns_problem* p) {
+  if (!p) return SNS_EINVAL;
+  if (p->m < 1 || p->n < 1 || p->m < p->n || p->m >= ((int64_t)1 << 31)) return SNS_EINVAL;
+  if (!p->b) return SNS_EINVAL;
+  if (p->fmt == SNS_DENSE_F32 || p->fmt == SNS_DENSE_F64) {
+    if (!p->A || p->lda < p->n) return SNS_EINVAL;
+  } else if (p->fmt == SNS_CSR_F32) {
+    if (!p->rowptr || (p->nnz > 0 && (!p->col || !p->val)) || p->nnz < 0) return SNS_EINVAL;
+  } else {
+    return SNS_EINVAL;
+  }
+  return SNS_OK;
+}
+
+static int64_t next_pow2(int64_t m) {
+  int64_t p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* sk) {
+  if (!sk) return SNS_EINVAL;
+  if (sk->d < p->n || sk->d < 1 || sk->d > ((int64_t)1 << 24)) return SNS_EINVAL;
+  switch (sk->kind) {
+    case SNS_COUNTSKETCH:
+      if (sk->variant < SNS_CS_AUTO || sk->variant > SNS_CS_STREAM) return SNS_EINVAL;
+      if (sk->variant == SNS_CS_SORTED && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
+      if (sk->variant == SNS_CS_STREAM && p->fmt != SNS_DENSE_F32) return SNS_EINVAL;
+      if (p->fmt == SNS_CSR_F32 && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
+      if (p->fmt == SNS_CSR_F32 && p->n > 50000) return SNS_EINVAL;
+      return SNS_OK;
+    case SNS_GAUSSIAN:
+      if (p->fmt != SNS_DENSE_F32) return SNS_EINVAL;
+      return SNS_OK;
+    case SNS_SRHT:
+      if (p->fmt == SNS_CSR_F32) return SNS_EINVAL;
+      if (sk->d > next_pow2(p->m) || next_pow2(p->m) >= ((int64_t)1 << 31)) return SNS_EINVAL;
+      return SNS_OK;
+    default:
+      return SNS_EINVAL;
+  }
+}
+
+static bool cs_use_sorted(const sns_problem* p, const sns_sketch_desc* sk) {
+  if (p->fmt != SNS_DENSE_F32) return true;
+  if (sk->variant == SNS_CS_STREAM) return false;
+  if (sk->variant == SNS_CS_SORTED) return true;
+  return sk->d <= cs_sorted_max_d();
+}
+
+static size_t sketch_ws(const sns_problem* p, const sns_sketch_desc* sk) {
+  switch (sk->kind) {
+    case SNS_COUNTSKETCH:
+      if (!cs_use_sorted(p, sk)) return 0;
+      return cs_layout(p->m, p->n, sk->d, is_f64(p), p->fmt == SNS_CSR_F32).bytes;
+    case SNS_GAUSSIAN:
+      return gauss_ws_bytes(p->m, p->n, sk->d);
+    case SNS_SRHT:
+      return srht_ws_bytes(p->m, p->n, sk->d, is_f64(p));
+  }
+  return 0;
+}
+
+static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, void* SA, int64_t ldsa, void* Sb,
+                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
+  DenseArgs da{p->A, p->lda, p->b, p->m, p->n, is_f64(p)};
+  switch (sk->kind) {
+    case SNS_COUNTSKETCH:
+      if (p->fmt == SNS_CSR_F32) {
+        CsrArgs ca{p->rowptr, p->col, p->val, static_cast<const float*>(p->b), p->m, p->n, p->nnz};
+        return cs_apply_csr(ca, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, ws,
+                            ws_bytes, st);
+      }
+      if (cs_use_sorted(p, sk)) return cs_apply_dense_sorted(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, ws, ws_bytes, st);
+      return cs_apply_dense_stream(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, st);
+    case SNS_GAUSSIAN:
+      return gauss_apply_dense(da, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, ws,
+                               ws_bytes, st);
+    case SNS_SRHT:
+      return srht_apply_dense(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, ws, ws_bytes, st);
+  }
+  return SNS_EINVAL;
+}
+
+// Workspace of snsolve_lstsq.
+struct LsLayout {
+  size_t off_saug, off_sk, sk_bytes, off_w, off_dev, off_iter, bytes;
+  int grid;
+};
+static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
+  LsLayout L{};
+  const int64_t d = o->sk.d, q = p->n + 1;
+  const size_t esz = is_f64(p) ? 8 : 4;
+  size_t off = 0;
+  L.off_saug = off; off += al((size_t)d * q * esz);
+  L.sk_bytes = sketch_ws(p, &o->sk);
+  L.off_sk = off; off += al(L.sk_bytes);
+  L.off_w = off; off += al((size_t)d * q * 8);
+  L.off_dev = off; off += al(64);
+  L.grid = iter_grid();
+  L.off_iter = off;
+  if (o->tol > 0) off += al(iter_ws_bytes(p->n, L.grid));
+  L.bytes = off;
+  return L;
+}
+
+static sns_status validate_opts(const sns_problem* p, const sns_opts* o) {
+  if (!o) return SNS_EINVAL;
+  sns_status s = validate_sketch(p, &o->sk);
+  if (s != SNS_OK) return s;
+  if (o->max_iter < 0 || o->inner < 0) return SNS_EINVAL;
+  if (o->sk.d > 16384) return SNS_EINVAL;   // the QR keeps one column of SA in shared memory
+  if (o->tol > 0 && p->fmt != SNS_CSR_F32 && p->n > 1024) return SNS_EINVAL;
+  if (!(o->tol == o->tol)) return SNS_EINVAL;  // NaN
+  return SNS_OK;
+}
+
+}  // namespace sns
+
+using namespace sns;
+
+extern "C" {
+
+const char* snsolve_status_string(int s) {
+  switch (s) {
+    case SNS_OK: return "SNS_OK";
+    case SNS_EINVAL: return "SNS_EINVAL";
+    case SNS_ENOMEM: return "SNS_ENOMEM";
+    case SNS_ERANK: return "SNS_ERANK";
+    case SNS_ENOTCONV: return "SNS_ENOTCONV";
+    case SNS_EAGAIN: return "SNS_EAGAIN";
+    case SNS_ETIMEOUT: return "SNS_ETIMEOUT";
+    case SNS_ECUDA: return "SNS_ECUDA";
+    case SNS_EBUDGET: return "SNS_EBUDGET";
+  }
+  return "SNS_UNKNOWN";
+}
+
+const char* snsolve_last_cuda_error(void) { return t_err; }
+
+int snsolve_version(void) { return 100; }
+
+sns_status snsolve_create(sns_ctx** ctx, int device) {
+  if (!ctx) return SNS_EINVAL;
+  *ctx = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return record_cuda_error(e);
+  if (device < 0 || device >= ndev) return SNS_EINVAL;
+  int major = 0, minor = 0;
+  SNS_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+  SNS_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
+  if (major != 10 || minor != 3) {
+    snprintf(t_err, sizeof(t_err), "device %d is sm_%d%d; this library is built for sm_103a", device, major, minor);
+    return SNS_ECUDA;
+  }
+  int cur = 0;
+  SNS_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != device) SNS_CUDA_TRY(cudaSetDevice(device));
+  sns_ctx* c = new sns_ctx();
+  c->device = device;
+  e = cudaHostAlloc(&c->pinned, 4096, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    delete c;
+    return record_cuda_error(e);
+  }
+  memset(c->pinned, 0, 4096);
+  *ctx = c;
+  return SNS_OK;
+}
+
+void snsolve_destroy(sns_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+sns_status snsolve_sketch_workspace_size(const sns_problem* prob, const sns_sketch_desc* sk, size_t* bytes) {
+  if (!bytes) return SNS_EINVAL;
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_sketch(prob, sk);
+  if (s != SNS_OK) return s;
+  *bytes = sketch_ws(prob, sk);
+  return SNS_OK;
+}
+
+sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk, void* SA, int64_t ldsa,
+                          void* Sb, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !SA || !Sb) return SNS_EINVAL;
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_sketch(prob, sk);
+  if (s != SNS_OK) return s;
+  if (ldsa < prob->n) return SNS_EINVAL;
+  if (ws_bytes < sketch_ws(prob, sk) || (ws_bytes > 0 && !ws && sketch_ws(prob, sk) > 0)) return SNS_ENOMEM;
+  if (ws && ((uintptr_t)ws % 256)) return SNS_EINVAL;
+  return run_sketch(prob, sk, SA, ldsa, Sb, 1, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+sns_status snsolve_lstsq_workspace_size(const sns_problem* prob, const sns_opts* opts, size_t* bytes) {
+  if (!bytes) return SNS_EINVAL;
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_opts(prob, opts);
+  if (s != SNS_OK) return s;
+  *bytes = ls_layout(prob, opts).bytes;
+  return SNS_OK;
+}
+
+static void info_fill(sns_info* info, int status, int iters, int outer, double eta, double rn, double sres) {
+  if (!info) return;
+  info->status = status;
+  info->iters = iters;
+  info->outer = outer;
+  info->reserved = 0;
+  info->eta = eta;
+  info->resid_norm = rn;
+  info->sketch_resid = sres;
+}
+
+sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* opts, double* x, sns_info* info,
+                         void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !x) return SNS_EINVAL;
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_opts(prob, opts);
+  if (s != SNS_OK) return s;
+  const LsLayout L = ls_layout(prob, opts);
+  if (!ws || ws_bytes < L.bytes) return SNS_ENOMEM;
+  if ((uintptr_t)ws % 256) return SNS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  const int64_t n = prob->n, d = opts->sk.d, q = n + 1;
+  const bool f64 = is_f64(prob);
+  double* W = reinterpret_cast<double*>(w + L.off_w);
+  int32_t* dstatus = reinterpret_cast<int32_t*>(w + L.off_dev);
+  double* dsres = reinterpret_cast<double*>(w + L.off_dev + 8);
+  double* hp = ctx->pinned;
+  const bool precond = opts->precondition != 0 || opts->tol <= 0;
+
+  double sres = 0.0;
+  if (precond) {
+    // steps 1-2: S [A | b] into the augmented buffer (ld = n + 1)
+    void* SA = w + L.off_saug;
+    void* Sb = w + L.off_saug + (size_t)n * (f64 ? 8 : 4);
+    s = run_sketch(prob, &opts->sk, SA, q, Sb, q, w + L.off_sk, L.sk_bytes, st);
+    if (s != SNS_OK) return s;
+    // step 3: FP64 Householder QR of [SA | Sb] and back substitution
+    s = qr_load_colmajor(SA, q, f64, d, q, W, st);
+    if (s != SNS_OK) return s;
+    QrOut o{W, d, q, x, dstatus, dsres};
+    s = qr_solve_one(o, st);
+    if (s != SNS_OK) return s;
+    SNS_CUDA_TRY(cudaMemcpyAsync(hp + 16, w + L.off_dev, 16, cudaMemcpyDeviceToHost, st));
+    SNS_CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t qs;
+    memcpy(&qs, hp + 16, 4);
+    sres = hp[17];
+    if (qs != SNS_OK) {
+      info_fill(info, qs, 0, 0, 0.0, 0.0, sres);
+      return (sns_status)qs;
+    }
+    if (opts->tol <= 0) {
+      info_fill(info, SNS_OK, 0, 0, 0.0, 0.0, sres);
+      return SNS_OK;
+    }
+  } else {
+    SNS_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * 8, st));
+  }
+
+  // SAP-SAS refinement
+  const IterWs I = iter_ws_carve(w + L.off_iter, n, L.grid);
+  SNS_CUDA_TRY(cudaMemsetAsync(I.ticket, 0, 64, st));
+  s = rinv_build(W, d, n, I.Rinv, I.RinvT, !precond, st);
+  if (s != SNS_OK) return s;
+  DenseArgs da{prob->A, prob->lda, prob->b, prob->m, n, f64};
+  CsrArgs ca{prob->rowptr, prob->col, prob->val, static_cast<const float*>(prob->b), prob->m, n, prob->nnz};
+  const DenseArgs* dap = prob->fmt == SNS_CSR_F32 ? nullptr : &da;
+  const CsrArgs* cap = prob->fmt == SNS_CSR_F32 ? &ca : nullptr;
+  const int max_iter = opts->max_iter > 0 ? opts->max_iter : 400;
+  const int inner = opts->inner > 0 ? opts->inner : 6;
+  int passes = 0, outer = 0;
+  double eta = 0.0, rn = 0.0;
+  for (;;) {
+    s = resid_pass(dap, cap, x, I, outer == 0, st);
+    if (s != SNS_OK) return s;
+    s = eta_eval(I, n, hp, st);
+    if (s != SNS_OK) return s;
+    SNS_CUDA_TRY(cudaStreamSynchronize(st));
+    ++outer;
+    eta = hp[0];
+    rn = hp[1];
+    if (!(eta > opts->tol)) break;       // converged (also stops on eta == 0)
+    if (passes >= max_iter) {
+      info_fill(info, SNS_ENOTCONV, passes, outer, eta, rn, sres);
+      return SNS_ENOTCONV;
+    }
+    // inner CG on the preconditioned normal equations
+    s = small_matvec(I.RinvT, I.g, n, I.rhs, nullptr, 0.0, nullptr, st);
+    if (s != SNS_OK) return s;
+    s = cg_init(I, n, st);
+    if (s != SNS_OK) return s;
+    for (int k = 0; k < inner && passes < max_iter; ++k, ++passes) {
+      if ((s = small_matvec(I.Rinv, I.p, n, I.z, I.z32, 0.0, nullptr, st)) != SNS_OK) return s;
+      if ((s = normal_pass(dap, cap, I, st)) != SNS_OK) return s;
+      if ((s = small_matvec(I.RinvT, I.w, n, I.qv, nullptr, 0.0, nullptr, st)) != SNS_OK) return s;
+      if ((s = cg_step(I, n, st)) != SNS_OK) return s;
+    }
+    s = small_matvec(I.Rinv, I.y, n, nullptr, nullptr, 1.0, x, st);
+    if (s != SNS_OK) return s;
+  }
+  info_fill(info, SNS_OK, passes, outer, eta, rn, sres);
+  return SNS_OK;
+}
+
+// ---------------------------------------------------------------- debug ABI
+sns_status snsolve_debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s, void* stream) {
+  if (m < 0 || d < 1 || !h || !s) return SNS_EINVAL;
+  return debug_countsketch_hash(m, d, seed, h, s, static_cast<cudaStream_t>(stream));
+}
+sns_status snsolve_debug_stream_keys(uint64_t seed, int stream_id, int64_t start, int64_t count, uint64_t* keys,
+                                     void* stream) {
+  if (count < 0 || start < 0 || !keys || stream_id < 0 || stream_id > 255) return SNS_EINVAL;
+  return debug_stream_keys(seed, stream_id, start, count, keys, static_cast<cudaStream_t>(stream));
+}
+sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* idx, void* ws, size_t ws_bytes,
+                                     void* stream) {
+  if (mp < 1 || (mp & (mp - 1)) || d < 1 || d > mp || !idx || mp >= ((int64_t)1 << 31)) return SNS_EINVAL;
+  return debug_srht_sample(mp, d, seed, idx, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes) {
+  if (!bytes || mp < 1 || d < 1) return SNS_EINVAL;
+  *bytes = ((size_t)d * 4 + 255) / 256 * 256 + (size_t)(mp < 1024 ? mp : 1024) + 256;
+  return SNS_OK;
+}
+sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host) {
+  if (!bf16_bits_host) return SNS_EINVAL;
+  gauss_table_host(bf16_bits_host);
+  return SNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal interfaces between the snsolve dispatch layer and its kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "snsolve.h"
+
+namespace sns {
+
+struct DenseArgs {
+  const void* A;
+  int64_t lda;
+  const void* b;
+  int64_t m, n;
+  bool f64;
+};
+struct CsrArgs {
+  const int64_t* rowptr;
+  const int32_t* col;
+  const float* val;
+  const float* b;
+  int64_t m, n, nnz;
+};
+
+// CountSketch workspace layout.
+struct CsLayout {
+  int64_t nblk, spi, parts, ct, ntile;
+  size_t off_sorted, off_seg, off_ticket, off_part, bytes;
+};
+CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr);
+int64_t cs_sorted_max_d();
+int num_sms();
+
+sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
+                                 int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
+                                 int64_t sbs, cudaStream_t st);
+sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb, int64_t sbs,
+                        void* ws, size_t ws_bytes, cudaStream_t st);
+sns_status debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s, cudaStream_t st);
+sns_status debug_stream_keys(uint64_t seed, int stream, int64_t start, int64_t count, uint64_t* out, cudaStream_t st);
+
+// SRHT.
+size_t srht_ws_bytes(int64_t m, int64_t n, int64_t d, bool f64);
+sns_status srht_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
+                            int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out, void* ws, size_t ws_bytes,
+                             cudaStream_t st);
+
+// Gaussian.
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d);
+sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
+                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+void gauss_table_host(uint16_t* out4096);
+
+// QR / triangular solves (FP64).  W is column-major d x q with leading dim d.
+struct QrOut {
+  double* W;        // in: column-major [SA | Sb] in FP64; out: R_aug in the upper triangle
+  int64_t d, q;     // q = n + 1
+  double* x;        // n entries: x^ = R^{-1} z (may be null)
+  int32_t* status;  // device int: SNS_OK / SNS_ERANK
+  double* sres;     // device double: |R_aug[n, n]|
+};
+sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, int64_t q, double* W, cudaStream_t st);
+sns_status qr_solve_one(const QrOut& o, cudaStream_t st);
+sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st);
+sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
+                      cudaStream_t st);
+
+// Iterative refinement (SAP-SAS).
+struct IterWs {
+  double *Rinv, *RinvT;       // n x n row-major
+  double *g, *w, *rhs, *y, *res, *p, *qv, *z, *scal;  // n-vectors and scalars
+  float *xhi, *xlo, *z32;     // n
+  float* part;                // partial n-vectors from passes [grid][n]
+  double* partd;              // FP64 partials [grid][n + 4]
+  uint32_t* ticket;           // one counter
+  int grid;
+};
+size_t iter_ws_bytes(int64_t n, int grid);
+IterWs iter_ws_carve(void* base, int64_t n, int grid);
+int iter_grid();
+sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, const IterWs& W, bool want_anorm,
+                      cudaStream_t st);
+sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, cudaStream_t st);
+sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
+                        double* accum, cudaStream_t st);
+sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st);
+sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st);
+sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st);
+
+// Batched.
+}  // namespace sns

@@ -1,0 +1,194 @@
+// FP64 Householder QR of the sketched augmented matrix [SA | Sb] (d x (n+1)) and
+// the triangular solves of sketch-and-solve (Sec. 1.2 step 3: "solve on SA
+// using existing algorithms"; the reduced problem of Sec. 1.3).
+//
+// R_aug = the (n+1) x (n+1) triangular factor of [SA | Sb]: its leading n x n
+// block is R, its last column holds z = (Q^T Sb)[0:n], and |R_aug[n, n]| is the
+// sketched residual ||SA x^ - Sb||.  x^ = R^{-1} z.
+//
+// Reflector convention: for column x (rows j..d-1), alpha = -sign(x_0) ||x||
+// (x_0 = 0 counts as positive), v = x - alpha e_0 scaled so v_0 = 1,
+// tau = -v_0 / alpha; R[j, j] = alpha.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sns {
+
+constexpr int kQrThreads = 256;
+constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
+
+template <typename T>
+__global__ void qr_load_kernel(const T* __restrict__ S, int64_t ld, int64_t d, int64_t q, double* __restrict__ W) {
+  const int64_t total = d * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / q, c = e % q;
+    W[c * d + r] = (double)S[r * ld + c];
+  }
+}
+
+sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, int64_t q, double* W, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((d * q + 255) / 256, (int64_t)num_sms() * 8);
+  if (f64)
+    qr_load_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(SAaug), ld, d, q, W);
+  else
+    qr_load_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(SAaug), ld, d, q, W);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+// One CTA factorises one problem held column-major in global memory (L2
+// resident at these sizes), then checks the rank and back-substitutes.
+SNS_D void qr_factor_cta(double* __restrict__ W, int64_t d, int64_t q, double* v, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int64_t j = 0; j < q && j < d; ++j) {
+    double* cj = W + j * d;
+    double part = 0.0;
+    for (int64_t i = j + tid; i < d; i += nt) {
+      const double x = cj[i];
+      part = fma(x, x, part);
+    }
+    const double nrm2 = block_sum(part, red);
+    const double x0 = cj[j];
+    const double normx = sqrt(nrm2);
+    double alpha = x0, tau = 0.0, inv_v0 = 0.0;
+    if (normx > 0.0) {
+      alpha = (x0 >= 0.0) ? -normx : normx;
+      const double v0 = x0 - alpha;
+      tau = -v0 / alpha;
+      inv_v0 = 1.0 / v0;
+    }
+    for (int64_t i = j + tid; i < d; i += nt) v[i] = (i == j) ? 1.0 : cj[i] * inv_v0;
+    __syncthreads();
+    if (tid == 0) cj[j] = alpha;
+    if (tau != 0.0) {
+      for (int64_t c = j + 1 + wid; c < q; c += nw) {
+        double* cc = W + c * d;
+        double s = 0.0;
+        for (int64_t i = j + lane; i < d; i += 32) s = fma(v[i], cc[i], s);
+        s = warp_sum(s);
+        const double f = tau * s;
+        for (int64_t i = j + lane; i < d; i += 32) cc[i] = fma(-f, v[i], cc[i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Rank check and back substitution x = R^{-1} z, column-oriented: after x_k is
+// known, z[0:k] -= R[0:k, k] x_k.  z lives in shared memory.
+SNS_D void qr_finish_cta(const double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ x,
+                         int32_t* status, double* sres, double* z, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t n = q - 1;
+  double mx = 0.0;
+  for (int64_t i = tid; i < n; i += nt) mx = fmax(mx, fabs(W[i * d + i]));
+  // block max via the sum helper's staging area
+  mx = warp_max(mx);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  double gmax = 0.0;
+  for (int w = 0; w < (nt >> 5); ++w) gmax = fmax(gmax, red[w]);
+  __syncthreads();
+  int bad = 0;
+  for (int64_t i = tid; i < n; i += nt) bad |= (fabs(W[i * d + i]) <= (double)n * kU64 * gmax) ? 1 : 0;
+  bad = __syncthreads_or(bad);
+  if (tid == 0) {
+    if (status) *status = (bad || gmax == 0.0) ? SNS_ERANK : SNS_OK;
+    if (sres) *sres = (n < d) ? fabs(W[n * d + n]) : 0.0;
+  }
+  if (!x) return;
+  for (int64_t i = tid; i < n; i += nt) z[i] = W[n * d + i];
+  __syncthreads();
+  for (int64_t k = n - 1; k >= 0; --k) {
+    const double xk = z[k] / W[k * d + k];
+    __syncthreads();
+    if (tid == 0) {
+      z[k] = xk;
+      x[k] = (bad || gmax == 0.0) ? 0.0 : xk;
+    }
+    for (int64_t i = tid; i < k; i += nt) z[i] = fma(-W[k * d + i], xk, z[i]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kQrThreads) qr_tasks_kernel(const QrOut* __restrict__ tasks, int ntasks) {
+  extern __shared__ double qsm[];
+  __shared__ double red[32];
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const QrOut o = tasks[t];
+    double* v = qsm;                 // d entries
+    qr_factor_cta(o.W, o.d, o.q, v, red);
+    qr_finish_cta(o.W, o.d, o.q, o.x, o.status, o.sres, qsm, red);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kQrThreads) qr_one_kernel(QrOut o) {
+  extern __shared__ double qsm[];
+  __shared__ double red[32];
+  qr_factor_cta(o.W, o.d, o.q, qsm, red);
+  qr_finish_cta(o.W, o.d, o.q, o.x, o.status, o.sres, qsm, red);
+}
+
+sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
+  const size_t smem = (size_t)std::max<int64_t>(o.d, o.q) * 8;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  qr_one_kernel<<<1, kQrThreads, smem, st>>>(o);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st) {
+  const size_t smem = (size_t)max_d * 8;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_tasks_kernel, kQrThreads, smem));
+  const int grid = std::min(ntasks, num_sms() * std::max(occ, 1));
+  qr_tasks_kernel<<<grid, kQrThreads, smem, st>>>(tasks_dev, ntasks);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+// Explicit R^{-1} (upper triangular, FP64) for the preconditioner applications
+// of the iterative phase: one warp per column j solves R y = e_j by
+// column-oriented back substitution.  Writes Rinv (row-major) and its
+// transpose RinvT (row-major), zeros below/above the diagonal.  With
+// `identity`, writes the identity (unpreconditioned iteration).
+__global__ void rinv_kernel(const double* __restrict__ W, int64_t ldw, int64_t n, double* __restrict__ Rinv,
+                            double* __restrict__ RinvT, int identity) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = gw; j < n; j += nw) {
+    // y[0..j] kept in the output column (Rinv[i*n + j]); start from e_j
+    for (int64_t i = lane; i < n; i += 32) {
+      Rinv[i * n + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    if (!identity) {
+      for (int64_t k = j; k >= 0; --k) {
+        const double yk = Rinv[k * n + j] / W[k * ldw + k];
+        __syncwarp();
+        if (lane == 0) Rinv[k * n + j] = yk;
+        for (int64_t i = lane; i < k; i += 32) Rinv[i * n + j] = fma(-W[k * ldw + i], yk, Rinv[i * n + j]);
+        __syncwarp();
+      }
+    }
+    for (int64_t i = lane; i < n; i += 32) RinvT[j * n + i] = Rinv[i * n + j];
+  }
+}
+
+sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
+                      cudaStream_t st) {
+  const int warps = 8;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + warps - 1) / warps, (int64_t)num_sms() * 4));
+  rinv_kernel<<<grid, warps * 32, 0, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+}  // namespace sns

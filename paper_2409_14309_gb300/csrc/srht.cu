@@ -1,0 +1,301 @@
+// Subsampled randomized Hadamard sketch (Sec. 1.2.1: Hadamard sketches built
+// from normalized Hadamard matrices and applied by the fast Hadamard transform):
+//   S [A | b] = (1/sqrt(d)) P H_{m'} D [A | b],   m' = 2^ceil(log2 m),
+// H unnormalised Sylvester-Hadamard (H[p, i] = (-1)^popcount(p & i)), D the
+// signs of stream 1, P the d rows of [0, m') chosen by Floyd's algorithm on
+// stream 2 and sorted ascending.  Rows m..m'-1 of [A | b] are zero.
+//
+// H_{m'} = H_{m1} (x) H_{m2} with m2 = min(m', 1024) and the row index split as
+// i = i1 * m2 + i2.  Pass 1 transforms every 1024-row block over i2 (a warp
+// holds one column of the block: 5 butterfly stages across its 32 registers,
+// 5 across lanes by shuffles) and keeps only outputs p2 that some sampled row
+// needs.  Pass 2 forms each sampled row p = p1 * m2 + p2 as
+// sum_{i1} (-1)^popcount(p1 & i1) Y[i1, p2, :].
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sns {
+
+constexpr int kM2 = 1024;
+template <typename T>
+constexpr int srht_ct() { return sizeof(T) == 4 ? 32 : 16; }   // columns per pass-1 tile
+constexpr int kSrhtMaxD = 16384;
+
+static int64_t np2(int64_t m) {
+  int64_t p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+struct SrhtLayout {
+  int64_t mp, m1, m2, q;
+  size_t off_sample, off_need, off_y, bytes;
+};
+static SrhtLayout srht_layout(int64_t m, int64_t n, int64_t d, bool f64) {
+  SrhtLayout L{};
+  L.mp = np2(m);
+  L.m2 = std::min<int64_t>(L.mp, kM2);
+  L.m1 = L.mp / L.m2;
+  L.q = n + 1;
+  size_t off = 0;
+  auto take = [&](size_t b) { size_t o = off; off += (b + 255) & ~(size_t)255; return o; };
+  L.off_sample = take((size_t)d * 4);
+  L.off_need = take((size_t)L.m2);
+  L.off_y = take((size_t)L.mp * L.q * (f64 ? 8 : 4));
+  L.bytes = off;
+  return L;
+}
+size_t srht_ws_bytes(int64_t m, int64_t n, int64_t d, bool f64) { return srht_layout(m, n, d, f64).bytes; }
+
+// Floyd's algorithm on one CTA: keys are drawn 32 at a time by warp 0; lane 0
+// runs the sequential membership test on an open-addressing set in shared
+// memory; the chosen values are then bitonic-sorted.  Also marks needed p2.
+__global__ void __launch_bounds__(1024)
+srht_sample_kernel(int64_t mp, int64_t d, uint64_t s0, int32_t* __restrict__ sample, uint8_t* __restrict__ need,
+                   int64_t m2) {
+  extern __shared__ __align__(16) int32_t ssm[];
+  int cap = 1;
+  while (cap < 2 * d) cap <<= 1;
+  int32_t* table = ssm;            // cap entries, -1 = empty
+  int32_t* sel = ssm + cap;        // pow2 >= d entries
+  int dp = 1;
+  while (dp < d) dp <<= 1;
+  for (int i = threadIdx.x; i < cap; i += blockDim.x) table[i] = -1;
+  for (int i = threadIdx.x; i < dp; i += blockDim.x) sel[i] = 0x7FFFFFFF;
+  for (int64_t i = threadIdx.x; i < m2; i += blockDim.x) need[i] = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int64_t t0 = 0; t0 < d; t0 += 32) {
+      const int64_t t = t0 + lane;
+      uint32_t u = 0;
+      if (t < d) {
+        const uint64_t key = splitmix_at(s0, (uint64_t)t);
+        const uint64_t J = (uint64_t)(mp - d + t);
+        u = (uint32_t)(((key & 0xFFFFFFFFull) * (J + 1)) >> 32);
+      }
+      for (int l = 0; l < 32 && t0 + l < d; ++l) {
+        const uint32_t ul = __shfl_sync(0xffffffffu, u, l);
+        if (lane == 0) {
+          const uint32_t J = (uint32_t)(mp - d + t0 + l);
+          // membership of ul
+          uint32_t h = (uint32_t)((ul * 0x9E3779B1u) & (uint32_t)(cap - 1));
+          bool found = false;
+          while (table[h] != -1) {
+            if ((uint32_t)table[h] == ul) { found = true; break; }
+            h = (h + 1) & (cap - 1);
+          }
+          const uint32_t v = found ? J : ul;
+          // insert v (J is never present yet: all earlier values are < J)
+          uint32_t h2 = (uint32_t)((v * 0x9E3779B1u) & (uint32_t)(cap - 1));
+          while (table[h2] != -1) h2 = (h2 + 1) & (cap - 1);
+          table[h2] = (int32_t)v;
+          sel[t0 + l] = (int32_t)v;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  // bitonic sort of sel[0..dp)
+  for (int k = 2; k <= dp; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a = sel[i], b = sel[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { sel[i] = b; sel[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+    sample[i] = sel[i];
+    need[sel[i] % m2] = 1;
+  }
+}
+
+static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sample, uint8_t* need, int64_t m2,
+                              cudaStream_t st) {
+  int cap = 1;
+  while (cap < 2 * d) cap <<= 1;
+  int dp = 1;
+  while (dp < d) dp <<= 1;
+  const size_t smem = (size_t)(cap + dp) * 4;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(srht_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, m2);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+// Pass 1: CTA per (block i1, column tile).  Tile = m2 rows x kSrhtCT columns in
+// shared memory (column-major with padding).  D is applied on load.
+template <typename T>
+__global__ void __launch_bounds__(256)
+srht_pass1(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, int64_t m, int64_t n, int64_t m2,
+           int64_t ntile, uint64_t s_sign, const uint8_t* __restrict__ need, T* __restrict__ Y, int64_t ldy) {
+  constexpr int kSrhtCT = srht_ct<T>();
+  extern __shared__ __align__(16) uint8_t srm[];
+  T* tile = reinterpret_cast<T*>(srm);          // [kSrhtCT][m2 + 1]
+  T* sgn = tile + (size_t)kSrhtCT * (m2 + 1);   // [m2]
+  const int64_t ldt = m2 + 1;
+  const int64_t i1 = blockIdx.x / ntile;
+  const int64_t c0 = (blockIdx.x % ntile) * kSrhtCT;
+  const int64_t q = n + 1;
+  const int ncol = (int)std::min<int64_t>(kSrhtCT, q - c0);
+  const int64_t r0 = i1 * m2;
+  for (int64_t rl = threadIdx.x; rl < m2; rl += blockDim.x) {
+    const int64_t row = r0 + rl;
+    sgn[rl] = (row < m) ? ((splitmix_at(s_sign, (uint64_t)row) >> 63) ? T(-1) : T(1)) : T(0);
+  }
+  __syncthreads();
+  // load D [A | b] (rows coalesced along columns)
+  for (int64_t e = threadIdx.x; e < m2 * kSrhtCT; e += blockDim.x) {
+    const int64_t rl = e / kSrhtCT;
+    const int c = (int)(e % kSrhtCT);
+    const int64_t row = r0 + rl;
+    T v = T(0);
+    if (row < m && c < ncol) {
+      const int64_t col = c0 + c;
+      v = sgn[rl] * ((col < n) ? A[row * lda + col] : b[row]);
+    }
+    tile[(int64_t)c * ldt + rl] = v;
+  }
+  __syncthreads();
+  // transform: one warp per column; lane holds x[k] = tile[32 k + lane]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (m2 == kM2) {
+    for (int c = w; c < ncol; c += blockDim.x / 32) {
+      T* col = tile + (int64_t)c * ldt;
+      T x[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = col[32 * k + lane];
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1)          // strides 32*s across registers
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if ((k & s) == 0) {
+            const T a = x[k], bb = x[k + s];
+            x[k] = a + bb;
+            x[k + s] = a - bb;
+          }
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1)          // strides 1..16 across lanes
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const T o = __shfl_xor_sync(0xffffffffu, x[k], s);
+          x[k] = (lane & s) ? (o - x[k]) : (x[k] + o);
+        }
+#pragma unroll
+      for (int k = 0; k < 32; ++k) col[32 * k + lane] = x[k];
+    }
+  } else {
+    // small m' (< 1024): plain shared-memory butterflies
+    for (int64_t h = 1; h < m2; h <<= 1) {
+      for (int64_t e = threadIdx.x; e < (m2 / 2) * ncol; e += blockDim.x) {
+        const int c = (int)(e / (m2 / 2));
+        const int64_t t = e % (m2 / 2);
+        const int64_t i = (t / h) * 2 * h + (t % h);
+        T* col = tile + (int64_t)c * ldt;
+        const T a = col[i], bb = col[i + h];
+        col[i] = a + bb;
+        col[i + h] = a - bb;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // store needed outputs p2 (row-major Y[i1*m2 + p2, c0 + c])
+  for (int64_t e = threadIdx.x; e < m2 * kSrhtCT; e += blockDim.x) {
+    const int64_t p2 = e / kSrhtCT;
+    const int c = (int)(e % kSrhtCT);
+    if (c < ncol && need[p2]) Y[(r0 + p2) * ldy + c0 + c] = tile[(int64_t)c * ldt + p2];
+  }
+}
+
+// Pass 2: CTA per sampled row.
+template <typename T>
+__global__ void __launch_bounds__(256)
+srht_pass2(const T* __restrict__ Y, int64_t ldy, int64_t q, int64_t m1, int64_t m2, const int32_t* __restrict__ sample,
+           T scale, T* __restrict__ SA, int64_t ldsa, T* __restrict__ Sb, int64_t sbs) {
+  const int64_t k = blockIdx.x;
+  const int64_t p = sample[k];
+  const int64_t p1 = p / m2, p2 = p % m2;
+  for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
+    // compensated (Kahan-Babuska) summation of the m1 signed terms
+    T acc = T(0), err = T(0);
+#pragma unroll 8
+    for (int64_t i1 = 0; i1 < m1; ++i1) {
+      T v = Y[(i1 * m2 + p2) * ldy + c];
+      v = (__popcll((unsigned long long)(p1 & i1)) & 1) ? -v : v;
+      const T s = acc + v;
+      err += (fabs(acc) >= fabs(v)) ? ((acc - s) + v) : ((v - s) + acc);
+      acc = s;
+    }
+    acc = (acc + err) * scale;
+    if (c < q - 1) SA[k * ldsa + c] = acc;
+    else Sb[k * sbs] = acc;
+  }
+}
+
+template <typename T>
+static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, int64_t ldsa, T* Sb, int64_t sbs,
+                           uint8_t* ws, const SrhtLayout& L, cudaStream_t st) {
+  int32_t* sample = reinterpret_cast<int32_t*>(ws + L.off_sample);
+  uint8_t* need = ws + L.off_need;
+  T* Y = reinterpret_cast<T*>(ws + L.off_y);
+  sns_status s = srht_sample(L.mp, d, seed, sample, need, L.m2, st);
+  if (s != SNS_OK) return s;
+  constexpr int kSrhtCT = srht_ct<T>();
+  const int64_t ntile = (L.q + kSrhtCT - 1) / kSrhtCT;
+  const size_t smem = ((size_t)kSrhtCT * (L.m2 + 1) + L.m2) * sizeof(T);
+  SNS_CUDA_TRY(cudaFuncSetAttribute(srht_pass1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  srht_pass1<T><<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(static_cast<const T*>(a.A), a.lda,
+                                                              static_cast<const T*>(a.b), a.m, a.n, L.m2, ntile,
+                                                              stream_state(seed, kStreamSrhtSign), need, Y, L.q);
+  SNS_CUDA_TRY(cudaGetLastError());
+  srht_pass2<T><<<(unsigned)d, 256, 0, st>>>(Y, L.q, L.q, L.m1, L.m2, sample, (T)(1.0 / std::sqrt((double)d)), SA,
+                                             ldsa, Sb, sbs);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+sns_status srht_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
+                            int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const SrhtLayout L = srht_layout(a.m, a.n, d, a.f64);
+  if (ws_bytes < L.bytes || !ws) return SNS_ENOMEM;
+  if (d > kSrhtMaxD) return SNS_EINVAL;
+  if (a.f64)
+    return srht_run<double>(a, d, seed, static_cast<double*>(SA), ldsa, static_cast<double*>(Sb), sbs,
+                            static_cast<uint8_t*>(ws), L, st);
+  return srht_run<float>(a, d, seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs,
+                         static_cast<uint8_t*>(ws), L, st);
+}
+
+__global__ void widen_i32(const int32_t* in, int64_t n, int64_t* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+  const int64_t m2 = std::min<int64_t>(mp, kM2);
+  const size_t need = ((size_t)d * 4 + 255) / 256 * 256 + (size_t)m2;
+  if (!ws || ws_bytes < need || d > kSrhtMaxD) return SNS_ENOMEM;
+  int32_t* sample = static_cast<int32_t*>(ws);
+  uint8_t* nd = static_cast<uint8_t*>(ws) + ((size_t)d * 4 + 255) / 256 * 256;
+  sns_status s = srht_sample(mp, d, seed, sample, nd, m2, st);
+  if (s != SNS_OK) return s;
+  widen_i32<<<64, 256, 0, st>>>(sample, d, out);
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+}  // namespace sns

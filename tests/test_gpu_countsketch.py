@@ -1,0 +1,108 @@
+"""CountSketch apply on the GPU vs the FP64 oracle (Sec. 1.2.2 sketch; the
+paper's default operator).  Bucket ids and signs must match bit for bit; SA and
+Sb within ||SA_gpu - SA_ref||_F / ||[A | b]||_F <= 1e-6 for FP32 data (1e-13
+for FP64 data); the sorted variant must be bitwise reproducible."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import ctx, dev, rel_fro
+from oracle import hashing as OH
+from oracle import sketch as OS
+from synth import csr_problem, gaussian_problem, ill_conditioned_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+
+
+@pytest.mark.parametrize("m,d", [(1, 1), (33, 7), (5000, 1024), (100003, 2048), (70000, 8192)])
+def test_hash_bit_exact(m, d):
+    c = ctx()
+    for seed in (0, 1, 2**63 + 5):
+        h, s = c.countsketch_hash(m, d, seed)
+        hr, sr = OH.countsketch_hash(seed, m, d)
+        assert np.array_equal(h.cpu().numpy().astype(np.int64), hr)
+        assert np.array_equal(s.cpu().numpy().astype(np.float64), sr)
+
+
+def test_stream_keys_bit_exact():
+    c = ctx()
+    for stream in (0, 1, 2, 3):
+        k = c.stream_keys(1234567, stream, 10, 1000).cpu().numpy().view(np.uint64)
+        kr = OH.splitmix64_at(OH.stream_state(1234567, stream), np.arange(10, 1010, dtype=np.uint64))
+        assert np.array_equal(k, kr)
+
+
+CASES = [  # m, n, d, lda_pad
+    (1, 1, 1, 0), (31, 7, 7, 0), (33, 7, 28, 3), (4097, 64, 256, 0), (12305, 257, 1028, 0),
+    (9000, 128, 512, 4), (20000, 300, 1200, 0), (4096, 3, 5, 1), (50000, 16, 64, 0),
+]
+
+
+@pytest.mark.parametrize("variant", ["sorted", "stream"])
+@pytest.mark.parametrize("m,n,d,pad", CASES)
+def test_countsketch_dense_f32(variant, m, n, d, pad):
+    c = ctx()
+    rng = np.random.default_rng(m * 7 + n)
+    Afull = rng.standard_normal((m, n + pad)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    Ad = dev(Afull)[:, :n]
+    SA, Sb = c.sketch(Ad, dev(b), d, seed=m, variant=variant)
+    A = Afull[:, :n]
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
+    assert rel_fro(SA.cpu().numpy(), OS.countsketch_apply(A, d, m), scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, m), scale) <= TOL32
+
+
+@pytest.mark.parametrize("m,n,d", [(1, 1, 1), (4097, 64, 256), (9001, 33, 100)])
+def test_countsketch_dense_f64(m, n, d):
+    c = ctx()
+    A, b, _ = gaussian_problem(m, n, seed=m)
+    SA, Sb = c.sketch(dev(A), dev(b), d, seed=3)
+    scale = np.linalg.norm(np.column_stack([A, b]))
+    assert rel_fro(SA.cpu().numpy(), OS.countsketch_apply(A, d, 3), scale) <= 1e-14
+    assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 3), scale) <= 1e-14
+
+
+def test_sorted_variant_bitwise_reproducible():
+    c = ctx()
+    rng = np.random.default_rng(5)
+    A = dev(rng.standard_normal((60000, 96)).astype(np.float32))
+    b = dev(rng.standard_normal(60000).astype(np.float32))
+    r1 = c.sketch(A, b, 384, seed=9, variant="sorted")
+    r2 = c.sketch(A, b, 384, seed=9, variant="sorted")
+    assert torch.equal(r1[0], r2[0]) and torch.equal(r1[1], r2[1])
+
+
+@pytest.mark.parametrize("m,n,d,dens", [(1, 1, 1, 1.0), (5000, 40, 160, 0.05), (70001, 512, 2048, 0.01)])
+def test_countsketch_csr(m, n, d, dens):
+    c = ctx()
+    A, b, _ = csr_problem(m, n, seed=m, density=dens, n_dense=min(8, m))
+    SA, Sb = c.sketch_csr(dev(A.rowptr), dev(A.col), dev(A.val), dev(b), n, d, seed=4)
+    ref = OS.countsketch_apply_csr(A.rowptr, A.col, A.val, n, d, 4)
+    scale = np.sqrt(np.sum(A.val.astype(np.float64) ** 2) + np.sum(b.astype(np.float64) ** 2))
+    assert rel_fro(SA.cpu().numpy(), ref, scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 4), scale) <= TOL32
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["sorted", "stream"])
+def test_full_size_ill_conditioned_sampled_rows(variant):
+    """2^20 x 256 FP32, d = 1024, the benchmark's launch configuration: sampled
+    output rows against the oracle's per-row definition."""
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(1 << 20, 256, seed=1002, kappa=1e6, noise=1e-4)
+    SA, Sb = c.sketch(dev(A), dev(b), 1024, seed=1, variant=variant)
+    rows = [0, 1, 17, 511, 512, 1000, 1023]
+    ref = OS.countsketch_rows(A, 1024, 1, rows)
+    refb = OS.countsketch_rows(b, 1024, 1, rows)
+    SAh = SA.cpu().numpy()
+    Sbh = Sb.cpu().numpy()
+    scale = np.linalg.norm(ref)
+    assert rel_fro(SAh[rows], ref, scale) <= TOL32
+    assert rel_fro(Sbh[rows], refb, np.linalg.norm(refb)) <= TOL32
+    # property that holds at any size: ||SA||_F^2 + ||Sb||^2 close to ||[A|b]||_F^2 (E[S^T S] = I)
+    tot = np.linalg.norm(SAh.astype(np.float64)) ** 2 + np.linalg.norm(Sbh.astype(np.float64)) ** 2
+    ref_tot = np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2
+    assert abs(tot / ref_tot - 1) < 0.2

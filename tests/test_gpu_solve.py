@@ -1,0 +1,111 @@
+"""Sketch-and-solve and sketch-and-precondition on the GPU vs the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import ctx, dev
+from oracle import sketch as OS
+from oracle import solve as OL
+from synth import csr_problem, gaussian_problem, ill_conditioned_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _xhat_tol(SA_ref):
+    s = np.linalg.svd(SA_ref, compute_uv=False)
+    return max(1e-5, 10 * (s[0] / s[-1]) * 2.0 ** -24)
+
+
+def test_config1_sketch_and_solve_f64():
+    """4096 x 64 FP64 N(0,1), noise 1e-3, CountSketch d = 256 from seed 0."""
+    c = ctx()
+    A, b, _ = gaussian_problem(4096, 64, seed=1001, noise=1e-3)
+    x, info = c.lstsq(dev(A), dev(b), 256, seed=0)
+    assert info.status == 0
+    SA, Sb = OS.countsketch_apply(A, 256, 0), OS.countsketch_apply(b, 256, 0)
+    x_ref, _, rn = OL.sketch_and_solve(SA, Sb)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref) < 1e-12
+    assert abs(info.sketch_resid - rn) < 1e-10 * max(rn, 1.0)
+    x_star, r_star = OL.exact_lstsq(A, b)
+    assert np.linalg.norm(A @ xg - b) / r_star <= 2.0
+
+
+@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian"])
+@pytest.mark.parametrize("m,n,d", [(3000, 20, 80), (4097, 64, 256), (20000, 100, 333)])
+def test_sketch_and_solve_f32_matches_oracle(kind, m, n, d):
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(m, n, seed=m + n, kappa=1e3, noise=1e-3)
+    x, info = c.lstsq(dev(A), dev(b), d, kind=kind, seed=7)
+    assert info.status == 0
+    SA = OS.sketch_apply(kind, A, d, 7)
+    Sb = OS.sketch_apply(kind, b, d, 7)
+    x_ref, _, _ = OL.sketch_and_solve(SA, Sb)
+    err = np.linalg.norm(x.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
+    assert err <= _xhat_tol(SA), err
+
+
+def test_consistent_system_exact():
+    c = ctx()
+    A, _, xt = gaussian_problem(5000, 32, seed=3)
+    b = A @ xt
+    x, info = c.lstsq(dev(A), dev(b), 128, seed=2)
+    assert info.status == 0
+    assert np.linalg.norm(x.cpu().numpy() - xt) / np.linalg.norm(xt) < 1e-12
+
+
+def test_rank_deficient_reported():
+    c = ctx()
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((2000, 8))
+    A[:, 5] = A[:, 1] - 2 * A[:, 2]
+    x, info = c.lstsq(dev(A), dev(rng.standard_normal(2000)), 32, seed=1)
+    assert info.status == 3   # SNS_ERANK
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_sketch_and_precondition_reaches_tol(tol):
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(65536, 64, seed=11, kappa=1e6, noise=1e-4)
+    x, info = c.lstsq(dev(A), dev(b), 256, seed=1, tol=tol)
+    assert info.status == 0, info.status
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    xg = x.cpu().numpy()
+    eta = OL.eta(A64, b64, xg)
+    assert eta <= tol * 1.5, (eta, info.eta)
+    assert abs(info.eta - eta) <= 0.05 * eta + 1e-15
+    x_star, r_star = OL.exact_lstsq(A64, b64)
+    assert np.linalg.norm(A64 @ xg - b64) / r_star - 1 < 1e-6
+
+
+def test_sap_forward_error_converged():
+    """Run to the FP64-class floor: x agrees with x* to the FP64 perturbation
+    bound kappa * u64 (times a small constant)."""
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(65536, 64, seed=12, kappa=1e6, noise=1e-4)
+    x, info = c.lstsq(dev(A), dev(b), 256, seed=1, tol=1e-13, max_iter=400)
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    x_star, _ = OL.exact_lstsq(A64, b64)
+    err = np.linalg.norm(x.cpu().numpy() - x_star) / np.linalg.norm(x_star)
+    assert err <= 100 * 1e6 * 2.0 ** -53, err
+
+
+def test_csr_preconditioned_vs_unpreconditioned():
+    c = ctx()
+    A, b, _ = csr_problem(200000, 128, seed=5, density=0.02, n_dense=16)
+    args = (dev(A.rowptr), dev(A.col), dev(A.val), dev(b), 128, 512)
+    x1, i1 = c.lstsq_csr(*args, seed=3, tol=1e-8, max_iter=2000)
+    x2, i2 = c.lstsq_csr(*args, seed=3, tol=1e-8, max_iter=4000, precondition=False)
+    assert i1.status == 0 and i2.status == 0, (i1.status, i2.status)
+    D = A.to_dense()
+    x_star, _ = OL.exact_lstsq(D, b.astype(np.float64))
+    for x in (x1, x2):
+        assert OL.eta(D, b.astype(np.float64), x.cpu().numpy()) <= 1.5e-8
+    assert i1.iters < i2.iters
+
+
+def test_max_iter_reports_not_converged():
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(20000, 32, seed=13, kappa=1e6, noise=1e-4)
+    x, info = c.lstsq(dev(A), dev(b), 128, seed=1, tol=1e-14, max_iter=2, inner=1)
+    assert info.status == 4   # SNS_ENOTCONV
