@@ -1,0 +1,398 @@
+"""Benchmark of the sketch-and-solve least-squares path on GB300.
+
+Workload (the configuration the headline metric is quoted on): dense
+A = G diag(sigma) Q of 1,048,576 x 256 FP32 with kappa = 1e6, b = A x_true +
+1e-4 noise, CountSketch with d = 1024.  One step = one complete solve through
+the C ABI: sketch [A | b] -> FP64 Householder QR -> back-solve ->
+R-preconditioned refinement until eta(x) = ||A^T r|| / (||A||_F ||r||) <= 1e-6.
+
+Reported: LS solves/s (value), p50/p99 solve latency, the sketch-apply HBM
+bandwidth and the dominant kernel's roofline fraction (per-kernel CUDA-event
+times measured on the launch stream inside the timed region), an end-to-end
+figure with host-resident inputs copied in every step, and the CPU oracle timed
+on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank solves its own independent problem (replicas,
+weak scaling); timing is the max over ranks.
+"""
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sketch-apply HBM GB/s vs peak; LS solves/s + p99 latency at rel-res ≤1e-6"
+M, N, D, KAPPA, NOISE, TOL = 1 << 20, 256, 1024, 1e6, 1e-4, 1e-6
+DATA_SEED, SKETCH_SEED = 1002, 1
+FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (vector and tensor), for ALU-bound kernels
+WORKLOAD = ("dense FP32 A = G diag(sigma) Q, 1048576 x 256, kappa 1e6, noise 1e-4; CountSketch d=1024; "
+            "sketch-and-solve then R-preconditioned refinement to eta <= 1e-6")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_inputs(rank, device):
+    import torch
+    from synth import ill_conditioned_problem
+    A, b, _ = ill_conditioned_problem(M, N, seed=DATA_SEED + 1000 * rank, kappa=KAPPA, noise=NOISE)
+    return A, b
+
+
+def kernel_profile(L):
+    nk = L.snsolve_profile_num_kernels()
+    ms = (C.c_double * nk)()
+    cnt = (C.c_uint64 * nk)()
+    L.snsolve_profile_read(ms, cnt, nk)
+    return {L.snsolve_profile_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(nk) if cnt[i]}
+
+
+def algorithmic(name, m, n, d):
+    """(bound, algorithmic bytes or flops per launch) of a kernel class."""
+    if name in ("normal_pass",):
+        return "hbm", m * n * 4.0
+    if name in ("resid_pass",):
+        return "hbm", m * (n + 1) * 4.0
+    if name in ("cs_gather_dense", "cs_stream_dense", "cs_sort_blocks"):
+        return "hbm", m * (n + 1) * 4.0
+    if name in ("qr_house",):
+        q = n + 1
+        return "alu", 2.0 * d * q * q - 2.0 / 3.0 * q ** 3
+    return None, None
+
+
+def traffic_table():
+    """Per-launch DRAM bytes from the committed ncu summaries (profiles/traffic.md),
+    with the source hash they were taken at."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        mm = re.match(r"^\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\w+)\s*\|", line)
+        if mm:
+            out[mm.group(1)] = (float(mm.group(2)), mm.group(3))
+    return out
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_14309_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:12]
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_solve_sample(A, b, rows):
+    """The oracle's sketch-and-solve + SAP on the first `rows` rows; returns the
+    seconds of (sketch, qr+solve, iterations) and the iteration count."""
+    from oracle import sketch as OS
+    from oracle import solve as OL
+    As = A[:rows].astype(np.float64)
+    bs = b[:rows].astype(np.float64)
+    t0 = time.perf_counter()
+    SA = OS.countsketch_apply(As, D, SKETCH_SEED)
+    Sb = OS.countsketch_apply(bs, D, SKETCH_SEED)
+    t1 = time.perf_counter()
+    xhat, R, _ = OL.sketch_and_solve(SA, Sb)
+    t2 = time.perf_counter()
+    x, it, _ = OL.lsqr_preconditioned(As, bs, R, xhat, tol=TOL, max_iter=500)
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2, it
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(A, b, steps=1):
+    """Oracle timed on a bounded sample: the first m/8 rows; the row-proportional
+    phases (sketch, iterations) are scaled by 8, the QR (independent of m) is not."""
+    frac = 8
+    rows = M // frac
+    ts = []
+    its = 0
+    for _ in range(max(1, steps)):
+        t_sk, t_qr, t_it, its = oracle_solve_sample(A, b, rows)
+        ts.append(t_sk * frac + t_qr + t_it * frac)
+    t = float(np.median(ts))
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"oracle (numpy FP64) sketch-and-solve + preconditioned LSQR to eta<=1e-6 on the first "
+                      f"{rows} rows of the workload ({its} LSQR iterations); row-proportional phase times x{frac}"}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    warm = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2409_14309_gb300 as sns
+    from paper_2409_14309_gb300 import abi
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    ctx = sns.Context(local)
+    L = abi.lib()
+
+    A_h, b_h = make_inputs(rank, dev)
+    A = torch.from_numpy(A_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    prob = sns.dense_problem(A, b)
+    op = sns.opts(D, "countsketch", SKETCH_SEED, "auto", tol=TOL)
+    ws = torch.empty(ctx.lstsq_workspace(prob, op), dtype=torch.uint8, device=dev)
+    x = torch.empty(N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(warm):
+        _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
+    torch.cuda.synchronize()
+
+    # timed region: K solves; per-kernel events on; clocks sampled
+    clk = ClockSampler(local)
+    L.snsolve_profile(1)
+    kernel_profile(L)                              # clear
+    launches0 = L.snsolve_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    infos = []
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
+        infos.append((info.status, info.iters, info.outer, info.eta))
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = L.snsolve_launch_count() - launches0
+    prof = kernel_profile(L)
+    L.snsolve_profile(0)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel and of the sketch apply
+    hbm_peak, bf16_peak, peak_kind = peaks()
+    traffic = traffic_table()
+    src = source_hash()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+
+    def roof(name):
+        ms, cnt = prof[name]
+        bound, amount = algorithmic(name, M, N, D)
+        if bound is None:
+            return None
+        avg_s = ms / cnt / 1e3
+        tr = traffic.get(name)
+        tval = tr[0] if tr and tr[1] == src else None
+        if bound == "hbm":
+            ach = amount / avg_s / 1e9
+            return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": tval, "peak_kind": f"{peak_kind} copy bandwidth",
+                    "algorithmic_bytes_per_launch": amount, "avg_launch_ms": avg_s * 1e3,
+                    "launches_per_step": cnt / args.steps}
+        ach = amount / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": tval, "peak_kind": "GB300 nominal FP64",
+                "algorithmic_flops_per_launch": amount, "avg_launch_ms": avg_s * 1e3,
+                "launches_per_step": cnt / args.steps}
+
+    sk_ms = sum(prof[k][0] for k in ("cs_sort_blocks", "cs_gather_dense") if k in prof)
+    sk_n = prof.get("cs_gather_dense", (0, 0))[1]
+    sketch = None
+    if sk_n:
+        gbs = M * (N + 1) * 4.0 / (sk_ms / sk_n / 1e3) / 1e9
+        sketch = {"kernels": ["cs_sort_blocks", "cs_gather_dense"], "bound": "hbm", "achieved": gbs,
+                  "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "avg_apply_ms": sk_ms / sk_n}
+
+    # end to end: host-resident inputs, copied in every step through the public API
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A_h).pin_memory()
+        bh = torch.from_numpy(b_h).pin_memory()
+        xh = torch.empty(N, dtype=torch.float64).pin_memory()
+        Ad = torch.empty_like(A)
+        bd = torch.empty_like(b)
+        for _ in range(2):
+            Ad.copy_(Ah, non_blocking=True)
+            bd.copy_(bh, non_blocking=True)
+            xx, _ = ctx.lstsq(Ad, bd, D, seed=SKETCH_SEED, tol=TOL, ws=ws)
+            xh.copy_(xx, non_blocking=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ke = max(3, args.steps // 2)
+        barrier()
+        e0.record(stream)
+        for _ in range(ke):
+            Ad.copy_(Ah, non_blocking=True)
+            bd.copy_(bh, non_blocking=True)
+            xx, _ = ctx.lstsq(Ad, bd, D, seed=SKETCH_SEED, tol=TOL, ws=ws)
+            xh.copy_(xx, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ke * world / (ems / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(A.numel() * 4 + b.numel() * 4), "d2h_bytes_per_step": int(N * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A_h, b_h)
+
+    if rank == 0:
+        st = sorted(step_ms)
+        p = lambda q: st[min(len(st) - 1, int(math.ceil(q * len(st))) - 1)]
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 passes + f64 QR/solves", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "d": D, "kappa": KAPPA, "tol_eta": TOL,
+                       "sketch": "countsketch", "parallelism": f"replicas x{world}",
+                       "l2": "A is 1.08 GB > 129 MB L2 and is streamed every pass; no flush needed"},
+            "p50_ms": p(0.50), "p99_ms": p(0.99),
+            "roofline": roof(dom) if dom else None,
+            "sketch_apply": sketch,
+            "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "solve": {"status": [i[0] for i in infos][-1], "iters": infos[-1][1], "outer": infos[-1][2],
+                      "eta": infos[-1][3]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "source": src,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return
+    A, b = make_inputs(0, None)
+    warm = max(3, args.warmup)
+    frac = 16
+    rows = M // frac
+    for _ in range(min(warm, 1)):
+        oracle_solve_sample(A, b, rows)
+    ts = []
+    its = 0
+    for _ in range(args.steps):
+        t_sk, t_qr, t_it, its = oracle_solve_sample(A, b, rows)
+        ts.append(t_sk * frac + t_qr + t_it * frac)
+    tot = float(np.sum(ts))
+    val = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": warm, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "d": D, "kappa": KAPPA, "tol_eta": TOL},
+            "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "value": val, "unit": "solves/s",
+                             "sample": f"first {rows} rows per step, row-proportional phases x{frac} "
+                                       f"({its} LSQR iterations)"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -43,6 +43,19 @@ sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64
  * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array. */
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host);
 
+/* ---- Measurement ----------------------------------------------------------
+ * Number of kernel launches this library has issued in this process. */
+uint64_t snsolve_launch_count(void);
+/* Per-kernel timing: with snsolve_profile(1), every launch is bracketed by a
+ * CUDA event pair recorded on its own stream.  snsolve_profile_read
+ * synchronizes those events, writes total milliseconds and launch counts per
+ * kernel class (nid >= snsolve_profile_num_kernels() entries, HOST arrays) and
+ * clears the records.  Kernel classes are named by snsolve_profile_kernel_name. */
+sns_status snsolve_profile(int enable);
+int snsolve_profile_num_kernels(void);
+const char* snsolve_profile_kernel_name(int id);
+sns_status snsolve_profile_read(double* ms, uint64_t* count, int nid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,11 @@ SIGNATURES = [
     ("snsolve_debug_srht_sample_ws", C.c_int, [i64, i64, P(sz)]),
     ("snsolve_debug_srht_sample", C.c_int, [i64, i64, C.c_uint64, vp, vp, sz, vp]),
     ("snsolve_debug_gaussian_table", C.c_int, [P(C.c_uint16)]),
+    ("snsolve_launch_count", C.c_uint64, []),
+    ("snsolve_profile", C.c_int, [C.c_int]),
+    ("snsolve_profile_num_kernels", C.c_int, []),
+    ("snsolve_profile_kernel_name", C.c_char_p, [C.c_int]),
+    ("snsolve_profile_read", C.c_int, [P(C.c_double), P(C.c_uint64), C.c_int]),
 ]
 
 _lib = None

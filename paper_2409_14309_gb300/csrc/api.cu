@@ -116,7 +116,7 @@ static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, vo
 
 // Workspace of snsolve_lstsq.
 struct LsLayout {
-  size_t off_saug, off_sk, sk_bytes, off_w, off_dev, off_iter, bytes;
+  size_t off_saug, off_sk, sk_bytes, off_w, off_dev, off_qr, off_iter, bytes;
   int grid;
 };
 static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
@@ -129,6 +129,7 @@ static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
   L.off_sk = off; off += al(L.sk_bytes);
   L.off_w = off; off += al((size_t)d * q * 8);
   L.off_dev = off; off += al(64);
+  L.off_qr = off; off += al(qr_coop_ws_bytes(q));
   L.grid = iter_grid();
   L.off_iter = off;
   if (o->tol > 0) off += al(iter_ws_bytes(p->n, L.grid));
@@ -278,13 +279,23 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     s = qr_load_colmajor(SA, q, f64, d, q, W, st);
     if (s != SNS_OK) return s;
     QrOut o{W, d, q, x, dstatus, dsres};
-    s = qr_solve_one(o, st);
+    const bool coop = q >= 32;
+    s = coop ? qr_solve_coop(o, w + L.off_qr, st) : qr_solve_one(o, st);
     if (s != SNS_OK) return s;
     SNS_CUDA_TRY(cudaMemcpyAsync(hp + 16, w + L.off_dev, 16, cudaMemcpyDeviceToHost, st));
+    if (coop) {
+      const size_t eoff = L.off_qr + (((size_t)q * 8 + 255) & ~(size_t)255) + (size_t)q * 4;
+      SNS_CUDA_TRY(cudaMemcpyAsync(hp + 18, w + eoff, 4, cudaMemcpyDeviceToHost, st));
+    }
     SNS_CUDA_TRY(cudaStreamSynchronize(st));
-    int32_t qs;
+    int32_t qs, qerr = 0;
     memcpy(&qs, hp + 16, 4);
+    if (coop) memcpy(&qerr, hp + 18, 4);
     sres = hp[17];
+    if (qerr) {
+      info_fill(info, SNS_ETIMEOUT, 0, 0, 0.0, 0.0, 0.0);
+      return SNS_ETIMEOUT;
+    }
     if (qs != SNS_OK) {
       info_fill(info, qs, 0, 0, 0.0, 0.0, sres);
       return (sns_status)qs;

@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sns {
 
@@ -488,10 +489,13 @@ static size_t sort_smem(int64_t d) { return (size_t)kSortWarps * d * 2 + (size_t
 sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, cudaStream_t st) {
   const size_t smem = sort_smem(d);
   SNS_CUDA_TRY(cudaFuncSetAttribute(cs_sort_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    SNS_PROF(K_CS_SORT, st);
   cs_sort_blocks<<<(unsigned)L.nblk, kSortWarps * 32, smem, st>>>(
       m, (uint32_t)d, stream_state(seed, kStreamCountSketch), L.nblk, reinterpret_cast<uint32_t*>(ws + L.off_sorted),
       reinterpret_cast<uint32_t*>(ws + L.off_seg), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
       d * L.ntile);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -508,11 +512,14 @@ static sns_status launch_gather(const DenseArgs& a, int64_t d, const CsLayout& L
   if (occ < 1) occ = 1;
   const int64_t items = d * L.parts * L.ntile;
   const int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * occ);
+  {
+    SNS_PROF(K_CS_GATHER, st);
   kern<<<(unsigned)grid, kGatherWarps * 32, smem, st>>>(
       static_cast<const T*>(a.A), a.lda, static_cast<const T*>(a.b), a.n, (uint32_t)d, L.nblk, L.spi, L.parts,
       L.ntile, reinterpret_cast<const uint32_t*>(ws + L.off_sorted), reinterpret_cast<const uint32_t*>(ws + L.off_seg),
       reinterpret_cast<uint32_t*>(ws + L.off_ticket), reinterpret_cast<T*>(ws + L.off_part), static_cast<T*>(SA), ldsa,
       static_cast<T*>(Sb), sbs);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -556,13 +563,19 @@ sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, v
   const uint64_t s0 = stream_state(seed, kStreamCountSketch);
   const int grid = num_sms() * 8;
   if (v4)
+    {
+      SNS_PROF(K_CS_STREAM, st);
     cs_stream_dense<4><<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b),
                                              a.m, a.n, (uint32_t)d, s0, static_cast<float*>(SA), ldsa,
                                              static_cast<float*>(Sb), sbs);
+    }
   else
+    {
+      SNS_PROF(K_CS_STREAM, st);
     cs_stream_dense<1><<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b),
                                              a.m, a.n, (uint32_t)d, s0, static_cast<float*>(SA), ldsa,
                                              static_cast<float*>(Sb), sbs);
+    }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -581,10 +594,13 @@ sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, i
   if (occ < 1) occ = 1;
   const int64_t items = d * L.parts;
   const int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * occ);
+  {
+    SNS_PROF(K_CS_CSR, st);
   cs_gather_csr<<<(unsigned)grid, kGatherWarps * 32, smem, st>>>(
       a.rowptr, a.col, a.val, a.b, a.n, (uint32_t)d, L.nblk, L.spi, L.parts,
       reinterpret_cast<const uint32_t*>(w + L.off_sorted), reinterpret_cast<const uint32_t*>(w + L.off_seg),
       reinterpret_cast<uint32_t*>(w + L.off_ticket), reinterpret_cast<float*>(w + L.off_part), SA, ldsa, Sb, sbs);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -605,12 +621,18 @@ __global__ void stream_keys_dump(uint64_t s0, int64_t start, int64_t count, uint
 }
 
 sns_status debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s, cudaStream_t st) {
+  {
+    SNS_PROF(K_MISC, st);
   cs_hash_dump<<<num_sms() * 4, 256, 0, st>>>(m, (uint32_t)d, stream_state(seed, kStreamCountSketch), h, s);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
 sns_status debug_stream_keys(uint64_t seed, int stream, int64_t start, int64_t count, uint64_t* out, cudaStream_t st) {
+  {
+    SNS_PROF(K_MISC, st);
   stream_keys_dump<<<num_sms() * 4, 256, 0, st>>>(stream_state(seed, (uint64_t)stream), start, count, out);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sns {
 
@@ -155,9 +156,12 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   kchunk = ((kchunk + kGKc - 1) / kGKc) * kGKc;
   ksplit = (a.m + kchunk - 1) / kchunk;
   dim3 grid((unsigned)tiles, (unsigned)ksplit);
+  {
+    SNS_PROF(K_GAUSS, st);
   gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
                                    stream_state(seed, kStreamGaussian), dtab, kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }

@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sns {
 
@@ -489,13 +490,19 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
     const size_t smem = (size_t)kPassWarps * a.n * 8;
     auto k = resid_pass_f32<VEC, NCH>;
     SNS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_RESID, st);
     k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket,
                                           W.g, W.scal, want_anorm ? 1 : 0);
+    }
   } else {
     const size_t smem = (size_t)kPassWarps * a.n * 4;
     auto k = normal_pass_f32<VEC, NCH>;
     SNS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_NORMAL, st);
     k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.w);
+    }
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -525,14 +532,20 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
   if (da) {
     const size_t smem = (size_t)da->n * 16;
     SNS_CUDA_TRY(cudaFuncSetAttribute(resid_pass_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_RESID, st);
     resid_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda,
                                                        static_cast<const double*>(da->b), da->m, da->n, x, W.partd,
                                                        W.ticket, W.g, W.scal, want_anorm ? 1 : 0);
+    }
   } else {
     const size_t smem = (size_t)ca->n * 16;
     SNS_CUDA_TRY(cudaFuncSetAttribute(resid_pass_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_RESID, st);
     resid_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->b, ca->m, ca->n, x, W.partd,
                                                        W.ticket, W.g, W.scal, want_anorm ? 1 : 0);
+    }
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -543,13 +556,19 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
   if (da) {
     const size_t smem = (size_t)da->n * 16;
     SNS_CUDA_TRY(cudaFuncSetAttribute(normal_pass_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_NORMAL, st);
     normal_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda, da->m, da->n,
                                                         W.z, W.partd, W.ticket, W.w);
+    }
   } else {
     const size_t smem = (size_t)ca->n * 8;
     SNS_CUDA_TRY(cudaFuncSetAttribute(normal_pass_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      SNS_PROF(K_NORMAL, st);
     normal_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->m, ca->n, W.z32, W.part,
                                                         W.ticket, W.w);
+    }
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -578,7 +597,10 @@ __global__ void small_matvec_kernel(const double* __restrict__ M, const double* 
 sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
                         double* accum, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)num_sms()));
+  {
+    SNS_PROF(K_MATVEC, st);
   small_matvec_kernel<<<grid, 256, 0, st>>>(M, v, n, out, out32, alpha, accum);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -623,12 +645,18 @@ __global__ void cg_step_kernel(int64_t n, const double* __restrict__ qv, double*
 }
 
 sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st) {
+  {
+    SNS_PROF(K_CG, st);
   cg_init_kernel<<<1, 512, 0, st>>>(W.rhs, n, W.y, W.res, W.p, W.scal);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
 sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st) {
+  {
+    SNS_PROF(K_CG, st);
   cg_step_kernel<<<1, 512, 0, st>>>(n, W.qv, W.y, W.res, W.p, W.scal);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -654,7 +682,10 @@ __global__ void eta_kernel(const double* __restrict__ g, int64_t n, double* scal
   }
 }
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st) {
+  {
+    SNS_PROF(K_ETA, st);
   eta_kernel<<<1, 512, 0, st>>>(W.g, n, W.scal);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   SNS_CUDA_TRY(cudaMemcpyAsync(host_out, W.scal + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
   return SNS_OK;

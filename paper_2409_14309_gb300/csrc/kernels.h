@@ -65,6 +65,10 @@ struct QrOut {
 };
 sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, int64_t q, double* W, cudaStream_t st);
 sns_status qr_solve_one(const QrOut& o, cudaStream_t st);
+// Multi-CTA factorisation of one large problem; ws holds qr_coop_ws_bytes(q)
+// bytes (tau values, flags, error word).  The error word is set if a wait gave up.
+size_t qr_coop_ws_bytes(int64_t q);
+sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st);
 sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st);
 sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
                       cudaStream_t st);

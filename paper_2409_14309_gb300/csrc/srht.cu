@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sns {
 
@@ -130,7 +131,10 @@ static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sam
   while (dp < d) dp <<= 1;
   const size_t smem = (size_t)(cap + dp) * 4;
   SNS_CUDA_TRY(cudaFuncSetAttribute(srht_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    SNS_PROF(K_SRHT_SAMPLE, st);
   srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, m2);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -257,12 +261,18 @@ static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, 
   const int64_t ntile = (L.q + kSrhtCT - 1) / kSrhtCT;
   const size_t smem = ((size_t)kSrhtCT * (L.m2 + 1) + L.m2) * sizeof(T);
   SNS_CUDA_TRY(cudaFuncSetAttribute(srht_pass1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    SNS_PROF(K_SRHT_PASS1, st);
   srht_pass1<T><<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(static_cast<const T*>(a.A), a.lda,
                                                               static_cast<const T*>(a.b), a.m, a.n, L.m2, ntile,
                                                               stream_state(seed, kStreamSrhtSign), need, Y, L.q);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
+  {
+    SNS_PROF(K_SRHT_PASS2, st);
   srht_pass2<T><<<(unsigned)d, 256, 0, st>>>(Y, L.q, L.q, L.m1, L.m2, sample, (T)(1.0 / std::sqrt((double)d)), SA,
                                              ldsa, Sb, sbs);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
@@ -293,7 +303,10 @@ sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out,
   uint8_t* nd = static_cast<uint8_t*>(ws) + ((size_t)d * 4 + 255) / 256 * 256;
   sns_status s = srht_sample(mp, d, seed, sample, nd, m2, st);
   if (s != SNS_OK) return s;
+  {
+    SNS_PROF(K_MISC, st);
   widen_i32<<<64, 256, 0, st>>>(sample, d, out);
+  }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
