@@ -197,6 +197,34 @@ sns_status snsolve_submit(sns_server* srv, const sns_problem* prob, const sns_op
  * timeout_us microseconds (0 = do not wait). */
 sns_status snsolve_poll(sns_server* srv, uint64_t req_id, int64_t timeout_us, sns_info* info);
 
+/* ---- CountSketch without any allocation ------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory at the time they need a sketch (for example
+ * code inside a host callback or another library's critical section, or a
+ * process whose device memory is fully reserved up front), and so cannot
+ * provide the workspace snsolve_sketch asks for.
+ *
+ * Computes SA = S A (d x n FP32, row-major, leading dimension ldsa >= n) and
+ * Sb = S b (d floats) for a dense FP32 problem with the deterministic
+ * bucket-sorted CountSketch (the same kernels and results as snsolve_sketch
+ * with kind SNS_COUNTSKETCH and variant SNS_CS_SORTED).  Its scratch is a fixed
+ * 8 MiB array inside the library's device image, held by every GPU that loads
+ * the library until the process exits; no memory is allocated or freed.
+ * Problems whose scratch need exceeds 8 MiB (roughly 4 bytes per row of A plus
+ * 4*d bytes per 4096 rows, plus partial rows when buckets are split) are
+ * rejected with SNS_ENOMEM before anything is launched.  SNS_EINVAL for other
+ * invalid arguments (non-FP32 input, d < n, d > 8192, null pointers).
+ *
+ * The first call on a device looks up the scratch's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * in the process share the one array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race and corrupt each
+ * other's results, so serialize them.  The array keeps the last call's
+ * contents; the kernels rewrite everything they read, so no clearing is
+ * needed between calls.  Asynchronous on `stream`. */
+sns_status snsolve_sketch_countsketch_static(const sns_problem* prob, int64_t d, uint64_t seed, float* SA,
+                                             int64_t ldsa, float* Sb, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
