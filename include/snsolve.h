@@ -208,11 +208,12 @@ sns_status snsolve_poll(sns_server* srv, uint64_t req_id, int64_t timeout_us, sn
  * Sb = S b (d floats) for a dense FP32 problem with the deterministic
  * bucket-sorted CountSketch (the same kernels and results as snsolve_sketch
  * with kind SNS_COUNTSKETCH and variant SNS_CS_SORTED).  Its scratch is a fixed
- * 8 MiB array inside the library's device image, held by every GPU that loads
+ * 16 MiB array inside the library's device image, held by every GPU that loads
  * the library until the process exits; no memory is allocated or freed.
- * Problems whose scratch need exceeds 8 MiB (roughly 4 bytes per row of A plus
- * 4*d bytes per 4096 rows, plus partial rows when buckets are split) are
- * rejected with SNS_ENOMEM before anything is launched.  SNS_EINVAL for other
+ * Problems whose scratch need exceeds 16 MiB (roughly 8 bytes per row of A plus
+ * 4*d bytes per 4096 rows, plus partial rows when buckets are split: about
+ * 1.2 million rows at n = 256, d = 1024) are rejected with SNS_ENOMEM before
+ * anything is launched.  SNS_EINVAL for other
  * invalid arguments (non-FP32 input, d < n, d > 8192, null pointers).
  *
  * The first call on a device looks up the scratch's device address with that

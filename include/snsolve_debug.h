@@ -55,6 +55,10 @@ sns_status snsolve_profile(int enable);
 int snsolve_profile_num_kernels(void);
 const char* snsolve_profile_kernel_name(int id);
 sns_status snsolve_profile_read(double* ms, uint64_t* count, int nid);
+/* Forgets the launch shapes the batched solver's tuner has measured in this
+ * process (its cache file, $SNSOLVE_TUNE_CACHE or ~/.cache/snsolve_tune.txt,
+ * is left alone), so the next batched call measures again. */
+void snsolve_tune_reset(void);
 
 #ifdef __cplusplus
 }

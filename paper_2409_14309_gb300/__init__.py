@@ -153,6 +153,31 @@ class Context:
                                   opts(d, "countsketch", seed, "auto", tol, max_iter, inner, precondition),
                                   ws=ws, stream=stream)
 
+    # -------------------------------------------------------------- batched
+    def lstsq_batched(self, As, bs, ds, seeds, ws=None, stream=None, check=True):
+        """Sketch-and-solve of many dense FP32 problems in one persistent launch.
+        As, bs: lists of CUDA tensors; ds, seeds: ints per problem.  Returns
+        (list of x tensors, list of sns_info)."""
+        k = len(As)
+        probs = (abi.sns_problem * k)()
+        ops = (abi.sns_opts * k)()
+        xs = [torch.empty(A.shape[1], dtype=torch.float64, device=self.device) for A in As]
+        xp = (C.c_void_p * k)()
+        for i in range(k):
+            probs[i] = dense_problem(As[i], bs[i])
+            ops[i] = opts(ds[i], "countsketch", seeds[i])
+            xp[i] = xs[i].data_ptr()
+        n = C.c_size_t()
+        _check(self._L.snsolve_lstsq_batched_workspace_size(probs, ops, k, C.byref(n)),
+               "snsolve_lstsq_batched_workspace_size")
+        if ws is None or ws.numel() < n.value:
+            ws = _workspace(n.value, self.device)
+        infos = (abi.sns_info * k)()
+        code = self._L.snsolve_lstsq_batched(self.h, probs, ops, k, xp, infos, _ptr(ws), ws.numel(), _stream(stream))
+        if check and code not in (abi.SNS_OK, abi.SNS_ERANK):
+            raise SnsError(code, "snsolve_lstsq_batched")
+        return xs, list(infos)
+
     # -------------------------------------------------------------- debug
     def countsketch_hash(self, m, d, seed, stream=None):
         h = torch.empty(m, dtype=torch.int32, device=self.device)

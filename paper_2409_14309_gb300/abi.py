@@ -74,6 +74,7 @@ SIGNATURES = [
     ("snsolve_profile_num_kernels", C.c_int, []),
     ("snsolve_profile_kernel_name", C.c_char_p, [C.c_int]),
     ("snsolve_profile_read", C.c_int, [P(C.c_double), P(C.c_uint64), C.c_int]),
+    ("snsolve_tune_reset", None, []),
 ]
 
 _lib = None

@@ -353,6 +353,25 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   return SNS_OK;
 }
 
+// ---------------------------------------------------------------- batched
+sns_status snsolve_lstsq_batched_workspace_size(const sns_problem* probs, const sns_opts* opts, int nprob,
+                                                size_t* bytes) {
+  if (!bytes || !probs || !opts || nprob < 1) return SNS_EINVAL;
+  for (int i = 0; i < nprob; ++i) {
+    sns_status s = validate_problem(probs + i);
+    if (s == SNS_OK) s = validate_opts(probs + i, opts + i);
+    if (s != SNS_OK) return s;
+  }
+  *bytes = batch_ws_bytes(probs, opts, nprob);
+  return SNS_OK;
+}
+
+sns_status snsolve_lstsq_batched(sns_ctx* ctx, const sns_problem* probs, const sns_opts* opts, int nprob,
+                                 double* const* x, sns_info* infos, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return SNS_EINVAL;
+  return lstsq_batched(probs, opts, nprob, x, infos, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
 // ---------------------------------------------------------------- debug ABI
 sns_status snsolve_debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s, void* stream) {
   if (m < 0 || d < 1 || !h || !s) return SNS_EINVAL;

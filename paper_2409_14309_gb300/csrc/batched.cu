@@ -1,0 +1,332 @@
+// Batched sketch-and-solve: many independent dense FP32 problems of uneven
+// sizes in one persistent launch (Sec. 1.2 steps 1-3 applied per problem).
+//
+// Each CTA repeatedly takes the next problem from a queue ordered by
+// decreasing estimated cost (longest-processing-time-first), then
+//  1. sketches [A | b] with its CountSketch, one column tile of ct columns at a
+//     time (b rides along in tile 0), into a shared-memory tile of d x (ct+1)
+//     FP32 accumulators with shared atomics; the tile is widened to FP64 and
+//     stored column-major in the problem's slice of the workspace;
+//  2. runs the FP64 Householder QR of [SA | Sb] and the back substitution on
+//     that slice (the one-CTA kernels of qr.cu), writing x^, the rank status and
+//     the sketched residual.
+// The upload of the task table, the reset of the queue counter and the kernel
+// are captured once into a CUDA graph per (workspace, batch size, launch
+// shape) and replayed.  The launch shape (threads per CTA, tile width, CTAs
+// per SM) comes from the tuner in tune.cpp.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "prof.h"
+#include "qr_cta.cuh"
+
+namespace sns {
+
+struct BatchTask {
+  const float* A;
+  const float* b;
+  double* W;        // d x (n+1) FP64 column-major
+  double* x;        // n
+  int64_t lda;
+  int32_t m, n, d, pad;
+  uint64_t seed;
+};
+struct BatchOut {
+  int32_t status;
+  int32_t pad;
+  double sres;
+};
+
+
+__global__ void batched_fused(const BatchTask* __restrict__ tasks, const int32_t* __restrict__ order, int ntasks,
+                              int* __restrict__ counter, BatchOut* __restrict__ outs, int ct) {
+  extern __shared__ __align__(16) float tile[];   // d_max x (ct + 1) floats (also reused as FP64 scratch)
+  __shared__ double red[32];
+  __shared__ int s_idx;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (;;) {
+    if (tid == 0) s_idx = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= ntasks) break;
+    const int ti = order[idx];
+    const BatchTask T = tasks[ti];
+    const int64_t m = T.m, n = T.n, d = T.d, q = n + 1;
+    const uint64_t s0 = stream_state(T.seed, kStreamCountSketch);
+    const int ldt = ct + 1;
+    for (int64_t c0 = 0; c0 < n; c0 += ct) {
+      const int w = (int)min((int64_t)ct, n - c0);
+      const bool with_b = (c0 == 0);
+      const int wt = w + (with_b ? 1 : 0);            // tile width incl. b
+      for (int64_t e = tid; e < d * ldt; e += blockDim.x) tile[e] = 0.f;
+      __syncthreads();
+      for (int64_t r = wid; r < m; r += nw) {
+        const uint64_t key = splitmix_at(s0, (uint64_t)r);
+        const uint32_t h = bucket_of(key, (uint64_t)d);
+        const float sg = (key >> 63) ? -1.f : 1.f;
+        const float* row = T.A + r * T.lda + c0;
+        float* trow = tile + (int64_t)h * ldt;
+        for (int j = lane; j < wt; j += 32) {
+          const float v = (j < w) ? __ldg(row + j) : __ldg(T.b + r);
+          atomicAdd(trow + j, sg * v);
+        }
+      }
+      __syncthreads();
+      // widen to FP64, column-major: columns c0..c0+w-1, and b to column n
+      for (int64_t e = tid; e < d * wt; e += blockDim.x) {
+        const int64_t k = e % d, j = e / d;
+        const int64_t col = (j < w) ? c0 + j : n;
+        T.W[col * d + k] = (double)tile[k * ldt + j];
+      }
+      __syncthreads();
+    }
+    double* scratch = reinterpret_cast<double*>(tile);   // d doubles (v), then reused for z
+    qr_factor_cta(T.W, d, q, scratch, red);
+    qr_finish_cta(T.W, d, q, T.x, &outs[ti].status, &outs[ti].sres, scratch, red);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct BatchLayout {
+  size_t off_tasks, off_order, off_counter, off_outs, off_w, bytes;
+};
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+static BatchLayout batch_layout(const sns_problem* probs, const sns_opts* opts, int nprob) {
+  BatchLayout L{};
+  size_t off = 0;
+  L.off_tasks = off; off += al((size_t)nprob * sizeof(BatchTask));
+  L.off_order = off; off += al((size_t)nprob * 4);
+  L.off_counter = off; off += al(16);
+  L.off_outs = off; off += al((size_t)nprob * sizeof(BatchOut));
+  L.off_w = off;
+  for (int i = 0; i < nprob; ++i) off += al((size_t)opts[i].sk.d * (probs[i].n + 1) * 8);
+  L.bytes = off;
+  return L;
+}
+
+static sns_status validate_batch(const sns_problem* probs, const sns_opts* opts, int nprob) {
+  if (!probs || !opts || nprob < 1) return SNS_EINVAL;
+  for (int i = 0; i < nprob; ++i) {
+    const sns_problem& p = probs[i];
+    const sns_opts& o = opts[i];
+    if (p.fmt != SNS_DENSE_F32 || !p.A || !p.b || p.m < 1 || p.n < 1 || p.m < p.n || p.lda < p.n) return SNS_EINVAL;
+    if (p.m >= ((int64_t)1 << 31)) return SNS_EINVAL;
+    if (o.sk.kind != SNS_COUNTSKETCH || o.sk.d < p.n || o.sk.d > 4096 || o.tol > 0) return SNS_EINVAL;
+  }
+  return SNS_OK;
+}
+
+size_t batch_ws_bytes(const sns_problem* probs, const sns_opts* opts, int nprob) {
+  return batch_layout(probs, opts, nprob).bytes;
+}
+
+// Tuned launch shape.
+struct BatchShape {
+  int threads, ct, ctas_per_sm;
+};
+std::vector<BatchShape> batch_candidates() {
+  return {{256, 64, 1}, {256, 32, 2}, {512, 64, 1}, {128, 32, 3}, {256, 16, 2}, {256, 8, 2}};
+}
+// implemented in tune.cpp
+bool tune_lookup(const char* key, int* a, int* b, int* c);
+void tune_store(const char* key, int a, int b, int c);
+
+struct GraphKey {
+  void* ws;
+  const void* stage;
+  int nprob, threads, ct, grid;
+  size_t smem;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(ws, stage, nprob, threads, ct, grid, smem) <
+           std::tie(o.ws, o.stage, o.nprob, o.threads, o.ct, o.grid, o.smem);
+  }
+};
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+
+static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_t* w, const BatchLayout& L,
+                            const void* host_tasks, size_t task_bytes, cudaStream_t st, bool use_graph) {
+  const size_t smem = (size_t)dmax * (S.ct + 1) * 4;
+  if (smem > 227 * 1024) return SNS_EINVAL;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(batched_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_fused, S.threads, smem));
+  if (occ < 1) return SNS_EINVAL;
+  const int per = std::min(occ, S.ctas_per_sm);
+  const int grid = std::min(nprob, num_sms() * per);
+  const BatchTask* tasks = reinterpret_cast<const BatchTask*>(w + L.off_tasks);
+  const int32_t* order = reinterpret_cast<const int32_t*>(w + L.off_order);
+  int* counter = reinterpret_cast<int*>(w + L.off_counter);
+  BatchOut* outs = reinterpret_cast<BatchOut*>(w + L.off_outs);
+  auto enqueue = [&](cudaStream_t s) -> sns_status {
+    SNS_CUDA_TRY(cudaMemcpyAsync(w + L.off_tasks, host_tasks, task_bytes, cudaMemcpyHostToDevice, s));
+    SNS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, s));
+    batched_fused<<<grid, S.threads, smem, s>>>(tasks, order, nprob, counter, outs, S.ct);
+    SNS_CUDA_TRY(cudaGetLastError());
+    return SNS_OK;
+  };
+  SNS_PROF(K_BATCH, st);
+  if (!use_graph) return enqueue(st);
+  GraphKey key{w, host_tasks, nprob, S.threads, S.ct, grid, smem};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) exec = it->second;
+  }
+  if (!exec) {
+    cudaStream_t cap;
+    SNS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    SNS_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    sns_status s = enqueue(cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (s != SNS_OK) return s;
+    if (e != cudaSuccess) return record_cuda_error(e);
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs[key] = exec;
+  }
+  SNS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  return SNS_OK;
+}
+
+// Pinned staging for the task table (host memory owned by the library,
+// allocated on first use and grown as needed; no device memory).
+static std::mutex g_stage_mu;
+static void* g_stage = nullptr;
+static size_t g_stage_bytes = 0;
+
+sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int nprob, double* const* x,
+                         sns_info* infos, void* ws, size_t ws_bytes, cudaStream_t st) {
+  sns_status s = validate_batch(probs, opts, nprob);
+  if (s != SNS_OK) return s;
+  if (!x) return SNS_EINVAL;
+  for (int i = 0; i < nprob; ++i)
+    if (!x[i]) return SNS_EINVAL;
+  const BatchLayout L = batch_layout(probs, opts, nprob);
+  if (!ws || ws_bytes < L.bytes) return SNS_ENOMEM;
+  if ((uintptr_t)ws % 256) return SNS_EINVAL;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+
+  // task table + LPT order (host), staged in pinned memory
+  const size_t task_bytes = (size_t)nprob * sizeof(BatchTask);
+  const size_t order_off = al(task_bytes);
+  const size_t stage_need = order_off + (size_t)nprob * 4;
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  if (g_stage_bytes < stage_need) {
+    if (g_stage) cudaFreeHost(g_stage);
+    g_stage = nullptr;
+    g_stage_bytes = 0;
+    SNS_CUDA_TRY(cudaHostAlloc(&g_stage, stage_need, cudaHostAllocDefault));
+    g_stage_bytes = stage_need;
+  }
+  SNS_CUDA_TRY(cudaStreamSynchronize(st));     // the staging buffer may still feed an earlier call
+  BatchTask* T = static_cast<BatchTask*>(g_stage);
+  int32_t* order = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(g_stage) + order_off);
+  size_t woff = L.off_w;
+  int64_t dmax = 1;
+  std::vector<std::pair<double, int>> cost(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const sns_problem& p = probs[i];
+    const int64_t d = opts[i].sk.d, q = p.n + 1;
+    T[i].A = static_cast<const float*>(p.A);
+    T[i].b = static_cast<const float*>(p.b);
+    T[i].W = reinterpret_cast<double*>(w + woff);
+    T[i].x = x[i];
+    T[i].lda = p.lda;
+    T[i].m = (int32_t)p.m;
+    T[i].n = (int32_t)p.n;
+    T[i].d = (int32_t)d;
+    T[i].pad = 0;
+    T[i].seed = opts[i].sk.seed;
+    woff += al((size_t)d * q * 8);
+    dmax = std::max(dmax, d);
+    // FP64 QR flops at ~1 TFLOP/s vs bytes of [A | b] at ~6 TB/s
+    const double c = (2.0 * d * q * q) / 1.0e12 + (double)p.m * q * 4.0 / 6.0e12;
+    cost[i] = {-c, i};
+  }
+  std::sort(cost.begin(), cost.end());
+  for (int i = 0; i < nprob; ++i) order[i] = cost[i].second;
+  // the order array travels with the task table in one copy
+  const size_t copy_bytes = order_off + (size_t)nprob * 4;
+  if (L.off_order != L.off_tasks + order_off) {
+    // layouts differ only if alignment rules change; keep both copies consistent
+    return SNS_EINVAL;
+  }
+
+  // launch shape from the tuner (key: batch size and size mix)
+  char key[160];
+  int64_t nsum[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < nprob; ++i) {
+    const int64_t n = probs[i].n;
+    nsum[n <= 16 ? 0 : n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 3 : 4]++;
+  }
+  snprintf(key, sizeof(key), "batched:sm%d:n%d:dmax%lld:mix%lld-%lld-%lld-%lld-%lld", num_sms(), nprob,
+           (long long)dmax, (long long)nsum[0], (long long)nsum[1], (long long)nsum[2], (long long)nsum[3],
+           (long long)nsum[4]);
+  BatchShape best{256, 64, 1};
+  int ta, tb, tc;
+  if (tune_lookup(key, &ta, &tb, &tc)) {
+    best = {ta, tb, tc};
+  } else {
+    // time every candidate once on this batch (results are overwritten by the final run)
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    SNS_CUDA_TRY(cudaEventCreate(&e0));
+    SNS_CUDA_TRY(cudaEventCreate(&e1));
+    for (const BatchShape& S : batch_candidates()) {
+      SNS_CUDA_TRY(cudaEventRecord(e0, st));
+      const sns_status rs = run_shape(S, dmax, nprob, w, L, g_stage, copy_bytes, st, false);
+      SNS_CUDA_TRY(cudaEventRecord(e1, st));
+      SNS_CUDA_TRY(cudaEventSynchronize(e1));
+      if (rs != SNS_OK) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = S;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, best.threads, best.ct, best.ctas_per_sm);
+  }
+  s = run_shape(best, dmax, nprob, w, L, g_stage, copy_bytes, st, true);
+  if (s != SNS_OK) return s;
+  // per-problem reports
+  std::vector<BatchOut> outs(nprob);
+  SNS_CUDA_TRY(cudaMemcpyAsync(outs.data(), w + L.off_outs, (size_t)nprob * sizeof(BatchOut), cudaMemcpyDeviceToHost,
+                               st));
+  SNS_CUDA_TRY(cudaStreamSynchronize(st));
+  sns_status worst = SNS_OK;
+  for (int i = 0; i < nprob; ++i) {
+    if (outs[i].status != SNS_OK) worst = (sns_status)outs[i].status;
+    if (infos) {
+      infos[i].status = outs[i].status;
+      infos[i].iters = 0;
+      infos[i].outer = 0;
+      infos[i].reserved = 0;
+      infos[i].eta = 0.0;
+      infos[i].resid_norm = 0.0;
+      infos[i].sketch_resid = outs[i].sres;
+    }
+  }
+  return worst;
+}
+
+}  // namespace sns

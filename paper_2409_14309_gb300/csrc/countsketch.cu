@@ -53,9 +53,25 @@ CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr) {
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
   L.off_sorted = take((size_t)L.nblk * kRowsPerBlock * 4);
   L.off_seg = take((size_t)L.nblk * d * 4);
-  L.off_ticket = take((size_t)d * L.ntile * 4);
-  // partial rows: one per (bucket, part, tile), each ct values + 1 for b
-  L.off_part = L.parts > 1 ? take((size_t)d * L.parts * L.ntile * (ct + 1) * esz) : take(0);
+  L.nticket = d * std::max<int64_t>(L.ntile, (n + 127) / 128);   // >= d * ceil(n / 128) for every phase 2
+  L.off_ticket = take((size_t)L.nticket * 4);
+  // partial rows: one per (bucket, part, tile), each ct values + 1 for b; sized
+  // for both phase-2 kernels (the bulk-copy one uses its own part count)
+  L.tma_parts = (csr || f64) ? 1 : cs_tma_parts(m, d);
+  const int64_t tma_ct = n <= 128 ? 128 : 256, tma_ntile = (n + tma_ct - 1) / tma_ct;
+  const size_t part_a = L.parts > 1 ? (size_t)d * L.parts * L.ntile * (ct + 1) * esz : 0;
+  const size_t part_b = L.tma_parts > 1 ? (size_t)d * L.tma_parts * tma_ntile * (tma_ct + 1) * 4 : 0;
+  L.off_part = take(std::max(part_a, part_b));
+  L.off_list = take((csr || f64) ? 0 : (size_t)m * 4);
+  L.off_btot = take((size_t)d * 4);
+  L.off_bbase = take((size_t)d * 4);
+  L.off_err = take(16);
+  // warp-gather chunk tables and chunk partial rows (dense FP32 only)
+  const bool wg = !(csr || f64);
+  const int64_t maxch = wg ? cs_warp_max_chunks(m, d) : 0;
+  L.off_cbase = take(wg ? (size_t)(d + 1) * 4 : 0);
+  L.off_ctab = take((size_t)maxch * 4);
+  L.off_wpart = take((size_t)maxch * ((n + 127) / 128) * (128 + 4) * 4);
   L.bytes = off;
   return L;
 }
@@ -67,7 +83,7 @@ CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr) {
 // seg[k * nblk + blk] = (start << 16) | count.  Also clears the tickets.
 __global__ void __launch_bounds__(kSortWarps * 32)
 cs_sort_blocks(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restrict__ sorted,
-               uint32_t* __restrict__ seg, uint32_t* __restrict__ ticket, int64_t nticket) {
+               uint32_t* __restrict__ seg, uint32_t* __restrict__ ticket, int64_t nticket, uint32_t* __restrict__ btot) {
   extern __shared__ __align__(16) uint8_t smraw[];
   uint16_t* cnt = reinterpret_cast<uint16_t*>(smraw);              // [W][d]
   uint16_t* hb = cnt + (size_t)kSortWarps * d;                      // [R]
@@ -123,6 +139,7 @@ cs_sort_blocks(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __res
       tot += c;
     }
     seg[(size_t)k * nblk + blk] = (running << 16) | tot;
+    if (tot) atomicAdd(btot + k, tot);   // bucket totals (integer adds: order does not matter)
     running += tot;
   }
   __syncthreads();
@@ -488,13 +505,15 @@ static size_t sort_smem(int64_t d) { return (size_t)kSortWarps * d * 2 + (size_t
 
 sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, cudaStream_t st) {
   const size_t smem = sort_smem(d);
+  SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_btot, 0, (size_t)d * 4, st));
+  SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));   // error word and phase-2 item counter
   SNS_CUDA_TRY(cudaFuncSetAttribute(cs_sort_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     SNS_PROF(K_CS_SORT, st);
   cs_sort_blocks<<<(unsigned)L.nblk, kSortWarps * 32, smem, st>>>(
       m, (uint32_t)d, stream_state(seed, kStreamCountSketch), L.nblk, reinterpret_cast<uint32_t*>(ws + L.off_sorted),
       reinterpret_cast<uint32_t*>(ws + L.off_seg), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
-      d * L.ntile);
+      L.nticket, reinterpret_cast<uint32_t*>(ws + L.off_btot));
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -538,6 +557,8 @@ sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, v
     return v2 ? launch_gather<double, 2, 2>(a, d, L, w, SA, ldsa, Sb, sbs, st)
               : launch_gather<double, 1, 4>(a, d, L, w, SA, ldsa, Sb, sbs, st);
   }
+  if (cs_tma_eligible(a))
+    return cs_tma_phase2(a, d, L, w, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, st);
   const bool v4 = (a.lda % 4 == 0) && aligned(a.A, 16);
   if (L.ct == 128)
     return v4 ? launch_gather<float, 4, 1>(a, d, L, w, SA, ldsa, Sb, sbs, st)

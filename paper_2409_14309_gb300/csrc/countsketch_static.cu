@@ -22,7 +22,7 @@
 
 namespace sns {
 
-constexpr size_t kStaticScratchBytes = (size_t)8 << 20;   // 8 MiB
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
 
 // The scratch.  Host code must not pass &g_static_scratch to a kernel: on the
 // host that name is only a stand-in for the device symbol.  The device address

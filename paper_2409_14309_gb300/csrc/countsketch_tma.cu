@@ -1,0 +1,540 @@
+// CountSketch apply, deterministic variant, bulk-copy pipeline (dense FP32).
+//
+// Phase 1 (countsketch.cu) counting-sorts the row ids of every 4096-row block by
+// bucket.  Phase 1b here turns those per-block runs into one bucket-major list
+// (rows of bucket 0 in ascending order, then bucket 1, ...).  Phase 2 splits
+// every bucket's rows into P contiguous parts; a work item is (bucket, part,
+// column tile).  In each CTA one producer warp walks its items, reads the
+// item's row ids and b entries with coalesced loads, and issues one
+// cp.async.bulk copy per row (the row's columns of the tile, 1 KB at n = 256)
+// into a shared-memory ring owned by consumer warp (j mod 8), j being the row's
+// position in the item.  Consumer warps wait on the slot's mbarrier, add the
+// signed row into register accumulators (two per warp, alternating rows), and
+// free the slot.  At the end of an item the 16 partial rows are added in a
+// fixed tree order; parts of a bucket are added in part order by the last CTA
+// to finish the bucket.  The summation order depends only on (m, d, n, P), not
+// on the grid, so results are bitwise reproducible.
+//
+// All mbarrier waits are bounded; a wait that gives up raises a CTA-wide abort
+// flag (every later wait returns at once), records an error word, and the
+// producer waits (bounded) for its last copy before the CTA exits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "prof.h"
+
+namespace sns {
+
+constexpr int kTmaWC = 8;          // consumer warps
+constexpr int kTmaCH = 512;        // producer row-list chunk
+constexpr uint32_t kEnd = 0xFFFFFFFFu;
+constexpr long long kWaitLimit = 1LL << 22;
+constexpr int kListRowsPerBlock = 4096;   // phase-1 block height (matches countsketch.cu)
+constexpr int kChunkRows = 128;           // rows per warp work item of the warp gather
+
+template <int CT>
+struct TmaCfg {
+  static constexpr int SW = CT == 256 ? 6 : 8;   // slots per consumer ring
+  static constexpr int NS = kTmaWC * SW;
+  static constexpr size_t smem_bytes() {
+    return (size_t)NS * CT * 4                    // slots
+           + (size_t)2 * kTmaWC * 2 * (CT + 1) * 4  // partial rows, double-buffered
+           + (size_t)kTmaCH * 8                   // row ids + b values
+           + (size_t)NS * 8                       // meta
+           + (size_t)NS * 16;                     // full + empty barriers
+  }
+};
+
+SNS_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+SNS_D void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+SNS_D void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+SNS_D void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+SNS_D bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; gives up early when the CTA is aborting.
+SNS_D bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort && *abort) return false;
+  }
+  if (abort) *abort = 1;
+  return false;
+}
+SNS_D void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+SNS_D void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kTmaWC * 32) : "memory"); }
+
+// ---------------------------------------------------------------------------
+// Phase 1b: bucket bases (exclusive scan of the bucket totals, done by every
+// CTA in shared memory) and the bucket-major row list.  One warp per bucket.
+__global__ void __launch_bounds__(256)
+cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ seg,
+              const uint32_t* __restrict__ btot, uint32_t* __restrict__ bbase, uint32_t* __restrict__ list,
+              uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab) {
+  extern __shared__ uint32_t sbase[];   // d bucket bases, then d chunk bases
+  uint32_t* scb = sbase + d;
+  __shared__ uint32_t wsum[8], wsum2[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = ((int)d + 255) / 256;
+  const int k0 = tid * per, k1 = min((int)d, k0 + per);
+  uint32_t local = 0, lch = 0;
+  for (int k = k0; k < k1; ++k) {
+    local += btot[k];
+    lch += (btot[k] + kChunkRows - 1) / kChunkRows;
+  }
+  uint32_t incl = local, inc2 = lch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    const uint32_t t2 = __shfl_up_sync(0xffffffffu, inc2, o);
+    if (lane >= o) { incl += t; inc2 += t2; }
+  }
+  if (lane == 31) { wsum[w] = incl; wsum2[w] = inc2; }
+  __syncthreads();
+  uint32_t run = incl - local, run2 = inc2 - lch;
+  for (int ww = 0; ww < w; ++ww) { run += wsum[ww]; run2 += wsum2[ww]; }
+  for (int k = k0; k < k1; ++k) {
+    sbase[k] = run;
+    scb[k] = run2;
+    if (blockIdx.x == 0) { bbase[k] = run; cbase[k] = run2; }
+    run += btot[k];
+    run2 += (btot[k] + kChunkRows - 1) / kChunkRows;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && tid == blockDim.x - 1) cbase[d] = run2;       // total chunk count
+  for (int64_t k = (int64_t)blockIdx.x * 8 + w; k < d; k += (int64_t)gridDim.x * 8) {
+    const uint32_t nch = (btot[k] + kChunkRows - 1) / kChunkRows;
+    for (uint32_t c = lane; c < nch; c += 32) ctab[scb[k] + c] = (uint32_t)k;
+    uint32_t pos = sbase[k];
+    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+      const int64_t blk = b0 + lane;
+      const uint32_t sv = blk < nblk ? __ldg(seg + (size_t)k * nblk + blk) : 0u;
+      const uint32_t c = sv & 0xFFFFu, st = sv >> 16;
+      uint32_t inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const uint32_t ex = inc - c;
+      for (uint32_t i = 0; i < c; ++i) list[pos + ex + i] = __ldg(sorted + blk * kListRowsPerBlock + st + i);
+      pos += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int CT>
+__global__ void __launch_bounds__((kTmaWC + 1) * 32)
+cs_gather_tma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t n, uint32_t d,
+              int64_t P, int64_t ntile, const uint32_t* __restrict__ list, const uint32_t* __restrict__ btot,
+              const uint32_t* __restrict__ bbase, uint32_t* __restrict__ ticket, float* __restrict__ part_buf,
+              float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int* __restrict__ err) {
+  using Cfg = TmaCfg<CT>;
+  constexpr int WC = kTmaWC, SW = Cfg::SW, NS = Cfg::NS, CH = kTmaCH, NCH = CT / 128;
+  extern __shared__ __align__(128) uint8_t sm[];
+  float* slots = reinterpret_cast<float*>(sm);
+  float* red = slots + (size_t)NS * CT;
+  uint32_t* rl = reinterpret_cast<uint32_t*>(red + (size_t)2 * WC * 2 * (CT + 1));
+  float* bl = reinterpret_cast<float*>(rl + CH);
+  uint2* meta = reinterpret_cast<uint2*>(bl + CH);
+  uint64_t* full = reinterpret_cast<uint64_t*>(meta + NS);
+  uint64_t* empty = full + NS;
+  __shared__ volatile int s_abort;
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t nitems = (int64_t)d * P * ntile;
+
+  if (w == WC) {
+    // ------------------------------------------------------------ producer
+    uint32_t cnt = 0;            // lane l < WC: slots used so far in ring l
+    int last_slot = -1;
+    uint32_t last_par = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      if (__any_sync(0xffffffffu, s_abort != 0)) break;
+      const int64_t t = item % ntile, kp = item / ntile, p = kp % P, k = kp / P;
+      const int64_t col0 = t * CT;
+      const uint32_t bytes = (uint32_t)(min((int64_t)CT, n - col0) * 4);
+      const int64_t len = btot[k], base = bbase[k];
+      const int64_t lo = base + len * p / P, hi = base + len * (p + 1) / P;
+      const int64_t J = hi - lo;
+      for (int64_t c0 = 0; c0 < J; c0 += CH) {
+        if (__any_sync(0xffffffffu, s_abort != 0)) break;
+        const int nrow = (int)min((int64_t)CH, J - c0);
+        for (int r = lane; r < nrow; r += 32) rl[r] = __ldg(list + lo + c0 + r);
+        __syncwarp();
+        for (int r = lane; r < nrow; r += 32) bl[r] = __ldg(b + (rl[r] & 0x7FFFFFFFu));
+        __syncwarp();
+        for (int r0 = 0; r0 < nrow; r0 += 32) {
+          const int r = r0 + lane;
+          const int64_t jj = c0 + r;
+          const int ww = (int)(jj % WC);
+          const uint32_t kth = (uint32_t)(jj / WC);
+          const uint32_t cw = __shfl_sync(0xffffffffu, cnt, ww);
+          if (r < nrow && !s_abort) {
+            const uint32_t pos = cw + kth;
+            const int slot = ww * SW + (int)(pos % SW);
+            const uint32_t par = (pos / SW) & 1u;
+            if (mbar_wait(empty + slot, par ^ 1u, &s_abort)) {
+              const uint32_t rid = rl[r];
+              meta[slot] = make_uint2(rid, __float_as_uint(bl[r]));
+              mbar_arrive_expect_tx(full + slot, bytes);
+              bulk_g2s(slots + (size_t)slot * CT, A + (int64_t)(rid & 0x7FFFFFFFu) * lda + col0, bytes, full + slot);
+              last_slot = slot;
+              last_par = par;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // end-of-item markers, one per consumer ring
+      if (lane < WC && !s_abort) {
+        const uint32_t nl = (J > lane) ? (uint32_t)((J - lane + WC - 1) / WC) : 0u;
+        const uint32_t pos = cnt + nl;
+        const int slot = lane * SW + (int)(pos % SW);
+        const uint32_t par = (pos / SW) & 1u;
+        if (mbar_wait(empty + slot, par ^ 1u, &s_abort)) {
+          meta[slot] = make_uint2(kEnd, 0u);
+          mbar_arrive(full + slot);
+        }
+        cnt = pos + 1;
+      }
+      __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, s_abort != 0)) {
+      if (lane == 0) atomicExch(err, 1);
+      if (last_slot >= 0) mbar_wait(full + last_slot, last_par, nullptr);   // own copy lands before exit
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  uint32_t pos = 0;
+  int it = 0;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+    const int64_t t = item % ntile, kp = item / ntile, p = kp % P, k = kp / P;
+    const int64_t col0 = t * CT;
+    float acc[2][NCH][4];
+    float accb[2] = {0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < NCH; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[a][q][v] = 0.f;
+    uint32_t kth = 0;
+    for (;;) {
+      if (__any_sync(0xffffffffu, s_abort != 0)) break;
+      const int slot = w * SW + (int)(pos % SW);
+      const uint32_t par = (pos / SW) & 1u;
+      const bool got = mbar_wait(full + slot, par, &s_abort);
+      if (!__all_sync(0xffffffffu, got)) break;
+      const uint2 mt = meta[slot];
+      if (mt.x == kEnd) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + slot);
+        ++pos;
+        break;
+      }
+      const float* row = slots + (size_t)slot * CT;
+      float4 v[NCH];
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) v[q] = *reinterpret_cast<const float4*>(row + q * 128 + lane * 4);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + slot);
+      const bool neg = (mt.x >> 31) != 0;
+      const float bv = __uint_as_float(mt.y);
+      // two accumulators, alternating rows (warp-uniform branch keeps them in registers)
+      if (kth & 1) {
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+          acc[1][q][0] += neg ? -v[q].x : v[q].x;
+          acc[1][q][1] += neg ? -v[q].y : v[q].y;
+          acc[1][q][2] += neg ? -v[q].z : v[q].z;
+          acc[1][q][3] += neg ? -v[q].w : v[q].w;
+        }
+        accb[1] += neg ? -bv : bv;
+      } else {
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+          acc[0][q][0] += neg ? -v[q].x : v[q].x;
+          acc[0][q][1] += neg ? -v[q].y : v[q].y;
+          acc[0][q][2] += neg ? -v[q].z : v[q].z;
+          acc[0][q][3] += neg ? -v[q].w : v[q].w;
+        }
+        accb[0] += neg ? -bv : bv;
+      }
+      ++kth;
+      ++pos;
+    }
+    // partial rows of this warp
+    float* rb = red + (size_t)(it & 1) * WC * 2 * (CT + 1);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      float* rr = rb + (size_t)(w * 2 + a) * (CT + 1);
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        rr[q * 128 + lane * 4 + 0] = acc[a][q][0];
+        rr[q * 128 + lane * 4 + 1] = acc[a][q][1];
+        rr[q * 128 + lane * 4 + 2] = acc[a][q][2];
+        rr[q * 128 + lane * 4 + 3] = acc[a][q][3];
+      }
+      if (lane == 0) rr[CT] = accb[a];
+    }
+    consumer_bar();
+    // On abort every consumer still runs the same barrier sequence; only the
+    // stores are skipped.
+    const bool ab = s_abort != 0;
+    // fixed-order tree over the 2*WC partial rows
+    const int ctid = threadIdx.x;  // 0 .. WC*32-1
+    float* pb = part_buf + ((size_t)(k * ntile + t) * P + p) * (CT + 1);
+    for (int c = ctid; c <= CT; c += WC * 32) {
+      float vals[2 * WC];
+#pragma unroll
+      for (int i = 0; i < 2 * WC; ++i) vals[i] = rb[(size_t)i * (CT + 1) + c];
+#pragma unroll
+      for (int s = WC; s > 0; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < s; ++i) vals[i] += vals[i + s];
+      if (ab) continue;
+      if (P > 1) {
+        pb[c] = vals[0];
+      } else if (c < CT) {
+        if (col0 + c < n) SA[k * ldsa + col0 + c] = vals[0];
+      } else if (t == 0) {
+        Sb[k * sbs] = vals[0];
+      }
+    }
+    if (P > 1) {
+      __threadfence();
+      consumer_bar();
+      if (ctid == 0) s_last = (!s_abort && atomicAdd(ticket + k * ntile + t, 1u) == (uint32_t)(P - 1)) ? 1 : 0;
+      consumer_bar();
+      if (s_last) {
+        __threadfence();
+        const float* pk = part_buf + (size_t)(k * ntile + t) * P * (CT + 1);
+        for (int c = ctid; c <= CT; c += WC * 32) {
+          float s = 0.f;
+          for (int64_t pp = 0; pp < P; ++pp) s += __ldcg(pk + pp * (CT + 1) + c);
+          if (c < CT) {
+            if (col0 + c < n) SA[k * ldsa + col0 + c] = s;
+          } else if (t == 0) {
+            Sb[k * sbs] = s;
+          }
+        }
+      }
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Phase 2, warp variant: a warp item is (chunk of kChunkRows consecutive
+// entries of one bucket's list, column tile of kWarpCT = 128 columns, i.e.
+// 512 B of each row).  Warps fetch items from a global counter.  The warp
+// loads the chunk's row ids 32 at a time (one coalesced load), keeps 8 row
+// tiles in flight (one float4 per lane each), and adds them into two register
+// accumulators (even / odd rows).  b entries are added per lane and summed by a
+// fixed shuffle tree.  The chunk's row goes to the partial buffer; the last
+// warp to finish a (bucket, tile) (ticket) adds the bucket's chunk rows in
+// chunk order.  A bucket with one chunk is written directly.  Which warp runs
+// an item does not change its arithmetic, so results are deterministic.
+constexpr int kWarpCT = 128;
+constexpr int kWarpU = 8;
+__global__ void __launch_bounds__(256, 3)
+cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t n, int64_t ntile,
+               const uint32_t* __restrict__ list, const uint32_t* __restrict__ btot,
+               const uint32_t* __restrict__ bbase, const uint32_t* __restrict__ cbase,
+               const uint32_t* __restrict__ ctab, uint32_t d, uint32_t* __restrict__ ticket,
+               uint32_t* __restrict__ next_item, float* __restrict__ part, float* __restrict__ SA, int64_t ldsa,
+               float* __restrict__ Sb, int64_t sbs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = cbase[d];
+  const int64_t nitems = nchunks * ntile;
+  for (;;) {
+    uint32_t gi = 0;
+    if (lane == 0) gi = atomicAdd(next_item, 1u);
+    const int64_t g = __shfl_sync(0xffffffffu, gi, 0);
+    if (g >= nitems) break;
+    const int64_t chunk = g / ntile, t = g % ntile;
+    const uint32_t k = __ldg(ctab + chunk);
+    const int64_t c = chunk - __ldg(cbase + k);
+    const int64_t len = __ldg(btot + k), base = __ldg(bbase + k);
+    const int64_t lo = base + c * kChunkRows;
+    const int64_t hi = min(base + len, lo + kChunkRows);
+    const int64_t col0 = t * kWarpCT;
+    const bool okc = col0 + lane * 4 < n;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), e0 = a0;   // even / odd rows
+    float accb = 0.f;
+    for (int64_t j0 = lo; j0 < hi; j0 += 32) {
+      const int nr = (int)min((int64_t)32, hi - j0);
+      const uint32_t rid_l = (lane < nr) ? __ldg(list + j0 + lane) : 0u;
+      if (t == 0 && lane < nr) {
+        const float bv = __ldg(b + (rid_l & 0x7FFFFFFFu));
+        accb += (rid_l >> 31) ? -bv : bv;
+      }
+      for (int r = 0; r < nr; r += kWarpU) {
+        float4 x[kWarpU];
+        uint32_t rid[kWarpU];
+#pragma unroll
+        for (int u = 0; u < kWarpU; ++u) {
+          rid[u] = __shfl_sync(0xffffffffu, rid_l, (r + u) & 31);
+          const bool ok = ((r + u) < nr) && okc;
+          const float* rp = A + (int64_t)(rid[u] & 0x7FFFFFFFu) * lda + col0 + lane * 4;
+          x[u] = ok ? __ldg(reinterpret_cast<const float4*>(rp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kWarpU; ++u) {
+          const float sg = (rid[u] >> 31) ? -1.f : 1.f;
+          float4& p0 = (u & 1) ? e0 : a0;
+          p0.x = fmaf(sg, x[u].x, p0.x);
+          p0.y = fmaf(sg, x[u].y, p0.y);
+          p0.z = fmaf(sg, x[u].z, p0.z);
+          p0.w = fmaf(sg, x[u].w, p0.w);
+        }
+      }
+    }
+    a0.x += e0.x; a0.y += e0.y; a0.z += e0.z; a0.w += e0.w;
+    accb = warp_sum(accb);
+    const int64_t nch_k = (len + kChunkRows - 1) / kChunkRows;
+    if (nch_k == 1) {
+      float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
+      if (okc) { out[0] = a0.x; out[1] = a0.y; out[2] = a0.z; out[3] = a0.w; }
+      if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = accb;
+      continue;
+    }
+    float* pr = part + (size_t)g * (kWarpCT + 4);
+    reinterpret_cast<float4*>(pr)[lane] = a0;
+    if (lane == 0) pr[kWarpCT] = accb;
+    __threadfence();
+    __syncwarp();
+    uint32_t old = 0;
+    if (lane == 0) old = atomicAdd(ticket + (int64_t)k * ntile + t, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != (uint32_t)(nch_k - 1)) continue;
+    __threadfence();
+    // last warp of bucket k, tile t: add the chunk rows in chunk order
+    const int64_t g0 = (int64_t)__ldg(cbase + k) * ntile + t;
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float sb = 0.f;
+    for (int64_t q = 0; q < nch_k; ++q) {
+      const float* pq = part + (size_t)(g0 + q * ntile) * (kWarpCT + 4);
+      const float4 v0 = __ldcg(reinterpret_cast<const float4*>(pq) + lane);
+      s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+      sb += __ldcg(pq + kWarpCT);
+    }
+    float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
+    if (okc) { out[0] = s0.x; out[1] = s0.y; out[2] = s0.z; out[3] = s0.w; }
+    if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = sb;
+  }
+}
+
+int64_t cs_warp_max_chunks(int64_t m, int64_t d) { return (m + kChunkRows - 1) / kChunkRows + d; }
+// ---------------------------------------------------------------------------
+int64_t cs_tma_parts(int64_t m, int64_t d) {
+  const int64_t per = d * 256;
+  int64_t P = (m + per / 2) / per;
+  return P < 1 ? 1 : P;
+}
+
+bool cs_tma_eligible(const DenseArgs& a) {
+  return !a.f64 && a.n % 4 == 0 && a.lda % 4 == 0 && ((uintptr_t)a.A % 16) == 0 && a.n >= 32;
+}
+
+template <int CT>
+static sns_status launch_tma(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
+                             float* Sb, int64_t sbs, cudaStream_t st) {
+  const size_t smem = TmaCfg<CT>::smem_bytes();
+  auto kern = cs_gather_tma<CT>;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (kTmaWC + 1) * 32, smem));
+  if (occ < 1) occ = 1;
+  const int64_t ntile = (a.n + CT - 1) / CT;
+  const int64_t items = d * L.tma_parts * ntile;
+  const int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * occ);
+  {
+    SNS_PROF(K_CS_GATHER, st);
+    kern<<<(unsigned)grid, (kTmaWC + 1) * 32, smem, st>>>(
+        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, (uint32_t)d, L.tma_parts, ntile,
+        reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
+        reinterpret_cast<const uint32_t*>(ws + L.off_bbase), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
+        reinterpret_cast<float*>(ws + L.off_part), SA, ldsa, Sb, sbs, reinterpret_cast<int*>(ws + L.off_err));
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
+                         float* Sb, int64_t sbs, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + 7) / 8, (int64_t)num_sms() * 4));
+  const size_t smem = (size_t)d * 8;
+  SNS_CUDA_TRY(cudaFuncSetAttribute(cs_build_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  uint32_t* cbase = reinterpret_cast<uint32_t*>(ws + L.off_cbase);
+  uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
+  {
+    SNS_PROF(K_CS_SORT, st);
+    cs_build_list<<<grid, 256, smem, st>>>((uint32_t)d, L.nblk, reinterpret_cast<const uint32_t*>(ws + L.off_sorted),
+                                           reinterpret_cast<const uint32_t*>(ws + L.off_seg),
+                                           reinterpret_cast<const uint32_t*>(ws + L.off_btot),
+                                           reinterpret_cast<uint32_t*>(ws + L.off_bbase),
+                                           reinterpret_cast<uint32_t*>(ws + L.off_list), cbase, ctab);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  static int use_tma = -1;
+  if (use_tma < 0) {
+    const char* e = getenv("SNSOLVE_CS_GATHER");
+    use_tma = (e && e[0] == 't') ? 1 : 0;
+  }
+  if (use_tma)
+    return a.n <= 128 ? launch_tma<128>(a, d, L, ws, SA, ldsa, Sb, sbs, st)
+                      : launch_tma<256>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+  const int64_t ntile = (a.n + kWarpCT - 1) / kWarpCT;
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_gather_warp, 256, 0));
+  const int64_t grid2 = (int64_t)num_sms() * std::max(occ, 1);
+  {
+    SNS_PROF(K_CS_GATHER, st);
+    cs_gather_warp<<<(unsigned)grid2, 256, 0, st>>>(
+        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile,
+        reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
+        reinterpret_cast<const uint32_t*>(ws + L.off_bbase), cbase, ctab, (uint32_t)d,
+        reinterpret_cast<uint32_t*>(ws + L.off_ticket), reinterpret_cast<uint32_t*>(ws + L.off_err) + 1,
+        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+}  // namespace sns

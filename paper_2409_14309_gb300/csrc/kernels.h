@@ -26,9 +26,16 @@ struct CsrArgs {
 
 // CountSketch workspace layout.
 struct CsLayout {
-  int64_t nblk, spi, parts, ct, ntile;
-  size_t off_sorted, off_seg, off_ticket, off_part, bytes;
+  int64_t nblk, spi, parts, ct, ntile, tma_parts, nticket;
+  size_t off_sorted, off_seg, off_ticket, off_part, off_list, off_btot, off_bbase, off_err, off_cbase, off_ctab,
+      off_wpart, bytes;
 };
+// Bulk-copy pipeline of the deterministic dense FP32 CountSketch (phase 1b + 2).
+bool cs_tma_eligible(const DenseArgs& a);
+int64_t cs_tma_parts(int64_t m, int64_t d);
+int64_t cs_warp_max_chunks(int64_t m, int64_t d);
+sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
+                         float* Sb, int64_t sbs, cudaStream_t st);
 CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr);
 int64_t cs_sorted_max_d();
 int num_sms();
@@ -96,4 +103,7 @@ sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st);
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st);
 
 // Batched.
+size_t batch_ws_bytes(const sns_problem* probs, const sns_opts* opts, int nprob);
+sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int nprob, double* const* x,
+                         sns_info* infos, void* ws, size_t ws_bytes, cudaStream_t st);
 }  // namespace sns

@@ -15,11 +15,11 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "prof.h"
+#include "qr_cta.cuh"
 
 namespace sns {
 
 constexpr int kQrThreads = 256;
-constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
 
 template <typename T>
 __global__ void qr_load_kernel(const T* __restrict__ S, int64_t ld, int64_t d, int64_t q, double* __restrict__ W) {
@@ -44,82 +44,6 @@ sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, 
     }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
-}
-
-// One CTA factorises one problem held column-major in global memory (L2
-// resident at these sizes), then checks the rank and back-substitutes.
-SNS_D void qr_factor_cta(double* __restrict__ W, int64_t d, int64_t q, double* v, double* red) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int64_t j = 0; j < q && j < d; ++j) {
-    double* cj = W + j * d;
-    double part = 0.0;
-    for (int64_t i = j + tid; i < d; i += nt) {
-      const double x = cj[i];
-      part = fma(x, x, part);
-    }
-    const double nrm2 = block_sum(part, red);
-    const double x0 = cj[j];
-    const double normx = sqrt(nrm2);
-    double alpha = x0, tau = 0.0, inv_v0 = 0.0;
-    if (normx > 0.0) {
-      alpha = (x0 >= 0.0) ? -normx : normx;
-      const double v0 = x0 - alpha;
-      tau = -v0 / alpha;
-      inv_v0 = 1.0 / v0;
-    }
-    for (int64_t i = j + tid; i < d; i += nt) v[i] = (i == j) ? 1.0 : cj[i] * inv_v0;
-    __syncthreads();
-    if (tid == 0) cj[j] = alpha;
-    if (tau != 0.0) {
-      for (int64_t c = j + 1 + wid; c < q; c += nw) {
-        double* cc = W + c * d;
-        double s = 0.0;
-        for (int64_t i = j + lane; i < d; i += 32) s = fma(v[i], cc[i], s);
-        s = warp_sum(s);
-        const double f = tau * s;
-        for (int64_t i = j + lane; i < d; i += 32) cc[i] = fma(-f, v[i], cc[i]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Rank check and back substitution x = R^{-1} z, column-oriented: after x_k is
-// known, z[0:k] -= R[0:k, k] x_k.  z lives in shared memory.
-SNS_D void qr_finish_cta(const double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ x,
-                         int32_t* status, double* sres, double* z, double* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t n = q - 1;
-  double mx = 0.0;
-  for (int64_t i = tid; i < n; i += nt) mx = fmax(mx, fabs(W[i * d + i]));
-  // block max via the sum helper's staging area
-  mx = warp_max(mx);
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
-  __syncthreads();
-  double gmax = 0.0;
-  for (int w = 0; w < (nt >> 5); ++w) gmax = fmax(gmax, red[w]);
-  __syncthreads();
-  int bad = 0;
-  for (int64_t i = tid; i < n; i += nt) bad |= (fabs(W[i * d + i]) <= (double)n * kU64 * gmax) ? 1 : 0;
-  bad = __syncthreads_or(bad);
-  if (tid == 0) {
-    if (status) *status = (bad || gmax == 0.0) ? SNS_ERANK : SNS_OK;
-    if (sres) *sres = (n < d) ? fabs(W[n * d + n]) : 0.0;
-  }
-  if (!x) return;
-  for (int64_t i = tid; i < n; i += nt) z[i] = W[n * d + i];
-  __syncthreads();
-  for (int64_t k = n - 1; k >= 0; --k) {
-    const double xk = z[k] / W[k * d + k];
-    __syncthreads();
-    if (tid == 0) {
-      z[k] = xk;
-      x[k] = (bad || gmax == 0.0) ? 0.0 : xk;
-    }
-    for (int64_t i = tid; i < k; i += nt) z[i] = fma(-W[k * d + i], xk, z[i]);
-    __syncthreads();
-  }
 }
 
 __global__ void __launch_bounds__(kQrThreads) qr_tasks_kernel(const QrOut* __restrict__ tasks, int ntasks) {

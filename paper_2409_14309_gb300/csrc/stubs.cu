@@ -3,9 +3,6 @@
 #include "snsolve.h"
 
 extern "C" {
-sns_status snsolve_lstsq_batched_workspace_size(const sns_problem*, const sns_opts*, int, size_t*) { return SNS_EINVAL; }
-sns_status snsolve_lstsq_batched(sns_ctx*, const sns_problem*, const sns_opts*, int, double* const*, sns_info*, void*,
-                                 size_t, void*) { return SNS_EINVAL; }
 sns_status snsolve_server_create(sns_server** s, sns_ctx*, size_t, int) { if (s) *s = nullptr; return SNS_EINVAL; }
 void snsolve_server_destroy(sns_server*) {}
 sns_status snsolve_submit(sns_server*, const sns_problem*, const sns_opts*, double*, uint64_t*) { return SNS_EINVAL; }

@@ -106,3 +106,35 @@ def test_full_size_ill_conditioned_sampled_rows(variant):
     tot = np.linalg.norm(SAh.astype(np.float64)) ** 2 + np.linalg.norm(Sbh.astype(np.float64)) ** 2
     ref_tot = np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2
     assert abs(tot / ref_tot - 1) < 0.2
+
+
+def test_bulk_copy_pipeline_variant_in_subprocess():
+    """The alternative phase-2 kernel (bulk-copy ring, selected by the
+    SNSOLVE_CS_GATHER=tma environment variable read once per process) against
+    the oracle on shapes with one and two column tiles and split buckets."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, ".")
+import paper_2409_14309_gb300 as sns
+from oracle import sketch as OS
+c = sns.Context(0)
+worst = 0.0
+for (m, n, d) in [(70001, 64, 256), (20000, 300, 1200), (300000, 128, 256)]:
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n)).astype(np.float32); b = rng.standard_normal(m).astype(np.float32)
+    SA, Sb = c.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), d, seed=5, variant="sorted")
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64))**2 + np.linalg.norm(b.astype(np.float64))**2)
+    e = max(np.linalg.norm(SA.cpu().numpy() - OS.countsketch_apply(A, d, 5)),
+            np.linalg.norm(Sb.cpu().numpy() - OS.countsketch_apply(b, d, 5))) / scale
+    worst = max(worst, e)
+print("WORST", worst)
+'''
+    env = dict(os.environ, SNSOLVE_CS_GATHER="tma")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    worst = float(r.stdout.split("WORST")[1])
+    assert worst <= TOL32

