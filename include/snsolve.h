@@ -179,23 +179,35 @@ sns_status snsolve_lstsq_batched(sns_ctx* ctx, const sns_problem* probs, const s
                                  int nprob, double* const* x, sns_info* infos,
                                  void* ws, size_t ws_bytes, void* stream);
 
-/* ---- Serving: continuous batching over a fixed device pool -----------------
- * A server owns one worker thread and `hbm_budget_bytes` of device memory
- * (allocated once here; never during serving).  Requests are admitted while
- * their footprint fits the free budget and a slot is free; admitted requests'
- * work overlaps on the device.  Problem pointers given to submit must stay
- * valid until the request is polled done. */
+/* ---- Serving: continuous batching of requests on one GPU --------------------
+ * A server owns a device workspace arena (a quarter of hbm_budget_bytes, at
+ * most 32 GiB, allocated here once; nothing is allocated while serving) and
+ * max_slots worker threads, each with its own stream.  A request's footprint
+ * is the bytes of its inputs (A and b, resident on the device and owned by the
+ * caller) plus its solver workspace.  Requests are admitted in arrival order
+ * while a slot is free, the admitted footprints sum to at most the budget and
+ * the arena has room; admitted requests run concurrently (their kernels
+ * overlap on the device) and each starts as soon as a slot and memory free up.
+ * Each request is solved exactly as snsolve_lstsq would solve it.  Problem
+ * pointers given to submit must stay valid until the request is polled done. */
 typedef struct sns_server sns_server;
 sns_status snsolve_server_create(sns_server** srv, sns_ctx* ctx, size_t hbm_budget_bytes,
                                  int max_slots);
+/* Waits for running requests, then frees the arena; pending ones are dropped. */
 void snsolve_server_destroy(sns_server* srv);
-/* Queue a request; x is a device pointer to n doubles.  SNS_EBUDGET when the
- * request's footprint alone exceeds the budget. */
+/* Queue a request; x is a device pointer to n doubles.  Returns at once.
+ * SNS_EBUDGET when the request's footprint alone exceeds the budget (or its
+ * workspace exceeds the arena); SNS_EINVAL for invalid arguments. */
 sns_status snsolve_submit(sns_server* srv, const sns_problem* prob, const sns_opts* opts,
                           double* x, uint64_t* req_id);
-/* SNS_OK with *info filled once done; SNS_EAGAIN if still pending after
- * timeout_us microseconds (0 = do not wait). */
+/* SNS_OK with *info filled (info->status is the solve's status) once the
+ * request is done; the id is then forgotten.  If it is not done: SNS_EAGAIN
+ * when timeout_us == 0, otherwise SNS_ETIMEOUT after waiting timeout_us
+ * microseconds.  SNS_EINVAL for an unknown or already collected id. */
 sns_status snsolve_poll(sns_server* srv, uint64_t req_id, int64_t timeout_us, sns_info* info);
+/* Requests running now, requests waiting for admission, and the footprint
+ * bytes admitted (any pointer may be NULL). */
+sns_status snsolve_server_stats(sns_server* srv, int* running, int* pending, size_t* used_bytes);
 
 /* ---- CountSketch without any allocation ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

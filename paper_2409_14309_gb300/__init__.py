@@ -202,6 +202,64 @@ class Context:
         return idx
 
 
+class Server:
+    """Continuous-batching request server over one Context (snsolve_server_*)."""
+
+    def __init__(self, ctx, hbm_budget_bytes, max_slots):
+        self.ctx = ctx
+        self._L = ctx._L
+        h = C.c_void_p()
+        _check(self._L.snsolve_server_create(C.byref(h), ctx.h, int(hbm_budget_bytes), int(max_slots)),
+               "snsolve_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit_problem(self, prob, op, x, keep=()):
+        rid = C.c_uint64()
+        code = self._L.snsolve_submit(self.h, C.byref(prob), C.byref(op), _ptr(x), C.byref(rid))
+        if code != abi.SNS_OK:
+            raise SnsError(code, "snsolve_submit")
+        self._keep[rid.value] = (x,) + tuple(keep)       # tensors must outlive the request
+        return rid.value
+
+    def submit(self, A, b, d, seed=0, tol=0.0, kind="countsketch", max_iter=0, inner=0):
+        x = torch.empty(A.shape[1], dtype=torch.float64, device=self.ctx.device)
+        return self.submit_problem(dense_problem(A, b), opts(d, kind, seed, "auto", tol, max_iter, inner), x,
+                                   keep=(A, b)), x
+
+    def submit_csr(self, rowptr, col, val, b, n, d, seed=0, tol=0.0, max_iter=0):
+        x = torch.empty(n, dtype=torch.float64, device=self.ctx.device)
+        return self.submit_problem(csr_problem(rowptr, col, val, b, n),
+                                   opts(d, "countsketch", seed, "auto", tol, max_iter), x,
+                                   keep=(rowptr, col, val, b)), x
+
+    def poll(self, rid, timeout_us=0):
+        """(status code of the poll, sns_info or None)."""
+        info = abi.sns_info()
+        code = self._L.snsolve_poll(self.h, rid, int(timeout_us), C.byref(info))
+        if code == abi.SNS_OK:
+            self._keep.pop(rid, None)
+            return code, info
+        return code, None
+
+    def stats(self):
+        r, p, u = C.c_int(), C.c_int(), C.c_size_t()
+        _check(self._L.snsolve_server_stats(self.h, C.byref(r), C.byref(p), C.byref(u)), "snsolve_server_stats")
+        return r.value, p.value, u.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.snsolve_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def gaussian_table_bits():
     """The library's BF16 normal-quantile table as 4096 raw uint16 values (host call)."""
     buf = (C.c_uint16 * 4096)()

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("snsolve_server_destroy", None, [vp]),
     ("snsolve_submit", C.c_int, [vp, P(sns_problem), P(sns_opts), vp, P(C.c_uint64)]),
     ("snsolve_poll", C.c_int, [vp, C.c_uint64, i64, P(sns_info)]),
+    ("snsolve_server_stats", C.c_int, [vp, P(C.c_int), P(C.c_int), P(sz)]),
     ("snsolve_sketch_countsketch_static", C.c_int, [P(sns_problem), i64, C.c_uint64, vp, i64, vp, vp]),
     # debug ABI
     ("snsolve_debug_countsketch_hash", C.c_int, [i64, i64, C.c_uint64, vp, vp, vp]),

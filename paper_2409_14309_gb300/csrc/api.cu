@@ -28,6 +28,22 @@ sns_status record_cuda_error(cudaError_t e) {
 
 static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Pinned host scalars for the convergence checks of snsolve_lstsq, one block
+// per host thread, so concurrent calls on one context do not share them.
+struct PinnedScalars {
+  double* p = nullptr;
+  ~PinnedScalars() {
+    if (p) cudaFreeHost(p);
+  }
+};
+static thread_local PinnedScalars t_pinned;
+static double* thread_pinned() {
+  if (!t_pinned.p) {
+    if (cudaHostAlloc(&t_pinned.p, 4096, cudaHostAllocDefault) != cudaSuccess) t_pinned.p = nullptr;
+  }
+  return t_pinned.p;
+}
+
 static bool is_f64(const sns_problem* p) { return p->fmt == SNS_DENSE_F64; }
 
 static sns_status validate_problem(const sns_problem* p) {
@@ -265,7 +281,8 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   double* W = reinterpret_cast<double*>(w + L.off_w);
   int32_t* dstatus = reinterpret_cast<int32_t*>(w + L.off_dev);
   double* dsres = reinterpret_cast<double*>(w + L.off_dev + 8);
-  double* hp = ctx->pinned;
+  double* hp = thread_pinned();
+  if (!hp) return SNS_ENOMEM;
   const bool precond = opts->precondition != 0 || opts->tol <= 0;
 
   double sres = 0.0;
