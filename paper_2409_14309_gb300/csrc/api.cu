@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
+#include <set>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -27,6 +29,25 @@ sns_status record_cuda_error(cudaError_t e) {
 }
 
 static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+cudaError_t raise_smem_limit(const void* func) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, func})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes attr;
+  e = cudaFuncGetAttributes(&attr, func);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)attr.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({dev, func});
+  return e;
+}
 
 // Pinned host scalars for the convergence checks of snsolve_lstsq, one block
 // per host thread, so concurrent calls on one context do not share them.

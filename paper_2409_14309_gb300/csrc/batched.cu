@@ -70,15 +70,36 @@ __global__ void batched_fused(const BatchTask* __restrict__ tasks, const int32_t
       const int wt = w + (with_b ? 1 : 0);            // tile width incl. b
       for (int64_t e = tid; e < d * ldt; e += blockDim.x) tile[e] = 0.f;
       __syncthreads();
-      for (int64_t r = wid; r < m; r += nw) {
-        const uint64_t key = splitmix_at(s0, (uint64_t)r);
-        const uint32_t h = bucket_of(key, (uint64_t)d);
-        const float sg = (key >> 63) ? -1.f : 1.f;
-        const float* row = T.A + r * T.lda + c0;
-        float* trow = tile + (int64_t)h * ldt;
-        for (int j = lane; j < wt; j += 32) {
-          const float v = (j < w) ? __ldg(row + j) : __ldg(T.b + r);
-          atomicAdd(trow + j, sg * v);
+      // kRowsInFlight rows per warp iteration: all loads first, then the
+      // shared-memory atomics (tile widths are at most 3 x 32 + 1 columns)
+      constexpr int kR = 8;
+      for (int64_t r0 = (int64_t)wid * kR; r0 < m; r0 += (int64_t)nw * kR) {
+        float v[kR][3];
+        uint32_t hh[kR];
+        float sg[kR];
+#pragma unroll
+        for (int u = 0; u < kR; ++u) {
+          const int64_t r = r0 + u;
+          const bool ok = r < m;
+          const uint64_t key = splitmix_at(s0, (uint64_t)(ok ? r : 0));
+          hh[u] = bucket_of(key, (uint64_t)d);
+          sg[u] = (key >> 63) ? -1.f : 1.f;
+          const float* row = T.A + (ok ? r : 0) * T.lda + c0;
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) {
+            const int j = lane + 32 * q2;
+            v[u][q2] = (ok && j < wt) ? ((j < w) ? __ldg(row + j) : __ldg(T.b + r)) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kR; ++u) {
+          if (r0 + u >= m) break;
+          float* trow = tile + (int64_t)hh[u] * ldt;
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) {
+            const int j = lane + 32 * q2;
+            if (j < wt) atomicAdd(trow + j, sg[u] * v[u][q2]);
+          }
         }
       }
       __syncthreads();
@@ -158,8 +179,8 @@ static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_t* w, const BatchLayout& L,
                             const void* host_tasks, size_t task_bytes, cudaStream_t st, bool use_graph) {
   const size_t smem = (size_t)dmax * (S.ct + 1) * 4;
-  if (smem > 227 * 1024) return SNS_EINVAL;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(batched_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 227 * 1024 || S.ct > 95) return SNS_EINVAL;   // the row loop covers 3 x 32 tile columns
+  SNS_CUDA_TRY(raise_smem_limit((const void*)batched_fused));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_fused, S.threads, smem));
   if (occ < 1) return SNS_EINVAL;

@@ -124,4 +124,9 @@ SNS_D bool spin_until_ge(const volatile int* flag, int target, long long limit) 
 
 namespace sns {
 sns_status record_cuda_error(cudaError_t e);
+// Raises a kernel's dynamic shared-memory limit to the device maximum, once per
+// (device, kernel).  Kernels are launched with varying dynamic sizes from
+// several host threads; setting the limit per call would let one thread lower
+// it between another thread's set and launch.
+cudaError_t raise_smem_limit(const void* func);
 }

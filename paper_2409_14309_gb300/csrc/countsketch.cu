@@ -507,7 +507,7 @@ sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, const CsLayout& L, uin
   const size_t smem = sort_smem(d);
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_btot, 0, (size_t)d * 4, st));
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));   // error word and phase-2 item counter
-  SNS_CUDA_TRY(cudaFuncSetAttribute(cs_sort_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)cs_sort_blocks));
   {
     SNS_PROF(K_CS_SORT, st);
   cs_sort_blocks<<<(unsigned)L.nblk, kSortWarps * 32, smem, st>>>(
@@ -525,7 +525,7 @@ static sns_status launch_gather(const DenseArgs& a, int64_t d, const CsLayout& L
   constexpr int CT = 32 * VEC * NCH;
   const size_t smem = (size_t)kGatherWarps * kGatherU * (CT + 1) * sizeof(T);
   auto kern = cs_gather_dense<T, VEC, NCH>;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGatherWarps * 32, smem));
   if (occ < 1) occ = 1;
@@ -609,7 +609,7 @@ sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, i
   sns_status s = cs_phase1(a.m, d, seed, L, w, st);
   if (s != SNS_OK) return s;
   const size_t smem = (size_t)(a.n + 1) * 4;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(cs_gather_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)cs_gather_csr));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_gather_csr, kGatherWarps * 32, smem));
   if (occ < 1) occ = 1;

@@ -92,7 +92,8 @@ SNS_D void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kTmaWC * 32) : 
 __global__ void __launch_bounds__(256)
 cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ seg,
               const uint32_t* __restrict__ btot, uint32_t* __restrict__ bbase, uint32_t* __restrict__ list,
-              uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab) {
+              uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab, float* __restrict__ SA, int64_t ldsa,
+              float* __restrict__ Sb, int64_t sbs, int64_t n) {
   extern __shared__ uint32_t sbase[];   // d bucket bases, then d chunk bases
   uint32_t* scb = sbase + d;
   __shared__ uint32_t wsum[8], wsum2[8];
@@ -127,6 +128,11 @@ cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, con
   for (int64_t k = (int64_t)blockIdx.x * 8 + w; k < d; k += (int64_t)gridDim.x * 8) {
     const uint32_t nch = (btot[k] + kChunkRows - 1) / kChunkRows;
     for (uint32_t c = lane; c < nch; c += 32) ctab[scb[k] + c] = (uint32_t)k;
+    if (SA && btot[k] == 0) {
+      // a bucket no row hashed to has no work item in phase 2: its rows are zero
+      for (int64_t c = lane; c < n; c += 32) SA[k * ldsa + c] = 0.f;
+      if (lane == 0) Sb[k * sbs] = 0.f;
+    }
     uint32_t pos = sbase[k];
     for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
       const int64_t blk = b0 + lane;
@@ -477,7 +483,7 @@ static sns_status launch_tma(const DenseArgs& a, int64_t d, const CsLayout& L, u
                              float* Sb, int64_t sbs, cudaStream_t st) {
   const size_t smem = TmaCfg<CT>::smem_bytes();
   auto kern = cs_gather_tma<CT>;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (kTmaWC + 1) * 32, smem));
   if (occ < 1) occ = 1;
@@ -500,23 +506,24 @@ sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8
                          float* Sb, int64_t sbs, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + 7) / 8, (int64_t)num_sms() * 4));
   const size_t smem = (size_t)d * 8;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(cs_build_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)cs_build_list));
   uint32_t* cbase = reinterpret_cast<uint32_t*>(ws + L.off_cbase);
   uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
+  static int use_tma = -1;
+  if (use_tma < 0) {
+    const char* e = getenv("SNSOLVE_CS_GATHER");
+    use_tma = (e && e[0] == 't') ? 1 : 0;
+  }
   {
     SNS_PROF(K_CS_SORT, st);
     cs_build_list<<<grid, 256, smem, st>>>((uint32_t)d, L.nblk, reinterpret_cast<const uint32_t*>(ws + L.off_sorted),
                                            reinterpret_cast<const uint32_t*>(ws + L.off_seg),
                                            reinterpret_cast<const uint32_t*>(ws + L.off_btot),
                                            reinterpret_cast<uint32_t*>(ws + L.off_bbase),
-                                           reinterpret_cast<uint32_t*>(ws + L.off_list), cbase, ctab);
+                                           reinterpret_cast<uint32_t*>(ws + L.off_list), cbase, ctab,
+                                           use_tma ? nullptr : SA, ldsa, Sb, sbs, a.n);
   }
   SNS_CUDA_TRY(cudaGetLastError());
-  static int use_tma = -1;
-  if (use_tma < 0) {
-    const char* e = getenv("SNSOLVE_CS_GATHER");
-    use_tma = (e && e[0] == 't') ? 1 : 0;
-  }
   if (use_tma)
     return a.n <= 128 ? launch_tma<128>(a, d, L, ws, SA, ldsa, Sb, sbs, st)
                       : launch_tma<256>(a, d, L, ws, SA, ldsa, Sb, sbs, st);

@@ -489,7 +489,7 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
   if (resid) {
     const size_t smem = (size_t)kPassWarps * a.n * 8;
     auto k = resid_pass_f32<VEC, NCH>;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     {
       SNS_PROF(K_RESID, st);
     k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket,
@@ -498,7 +498,7 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
   } else {
     const size_t smem = (size_t)kPassWarps * a.n * 4;
     auto k = normal_pass_f32<VEC, NCH>;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     {
       SNS_PROF(K_NORMAL, st);
     k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.w);
@@ -531,7 +531,7 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
   if (da && !da->f64) return dense_f32_dispatch(*da, W, x, true, want_anorm, st);
   if (da) {
     const size_t smem = (size_t)da->n * 16;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(resid_pass_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)resid_pass_f64));
     {
       SNS_PROF(K_RESID, st);
     resid_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda,
@@ -540,7 +540,7 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
     }
   } else {
     const size_t smem = (size_t)ca->n * 16;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(resid_pass_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)resid_pass_csr));
     {
       SNS_PROF(K_RESID, st);
     resid_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->b, ca->m, ca->n, x, W.partd,
@@ -555,7 +555,7 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
   if (da && !da->f64) return dense_f32_dispatch(*da, W, nullptr, false, false, st);
   if (da) {
     const size_t smem = (size_t)da->n * 16;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(normal_pass_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)normal_pass_f64));
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda, da->m, da->n,
@@ -563,7 +563,7 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
     }
   } else {
     const size_t smem = (size_t)ca->n * 8;
-    SNS_CUDA_TRY(cudaFuncSetAttribute(normal_pass_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SNS_CUDA_TRY(raise_smem_limit((const void*)normal_pass_csr));
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->m, ca->n, W.z32, W.part,

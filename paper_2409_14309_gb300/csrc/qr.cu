@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_one_kernel(QrOut o) {
 
 sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
   const size_t smem = (size_t)std::max<int64_t>(o.d, o.q) * 8;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)qr_one_kernel));
   {
     SNS_PROF(K_QR, st);
   qr_one_kernel<<<1, kQrThreads, smem, st>>>(o);
@@ -78,7 +78,7 @@ sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
 
 sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st) {
   const size_t smem = (size_t)max_d * 8;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)qr_tasks_kernel));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_tasks_kernel, kQrThreads, smem));
   const int grid = std::min(ntasks, num_sms() * std::max(occ, 1));
@@ -224,7 +224,7 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
   int* err = flags + o.q;
   SNS_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)o.q * 4 + 4, st));
   const size_t smem = (size_t)o.d * 8;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)qr_coop_kernel));
   const int grid = qr_coop_grid(o.q);
   double* W = o.W;
   int64_t d = o.d, q = o.q;
@@ -235,7 +235,7 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
                                              st));
   }
   const size_t zs = (size_t)std::max<int64_t>(o.q, 1) * 8;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(qr_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)qr_finish_kernel));
   {
     SNS_PROF(K_QR, st);
     qr_finish_kernel<<<1, kQrThreads, zs, st>>>(o);
@@ -245,41 +245,47 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
 }
 
 // Explicit R^{-1} (upper triangular, FP64) for the preconditioner applications
-// of the iterative phase: one warp per column j solves R y = e_j by
-// column-oriented back substitution.  Writes Rinv (row-major) and its
-// transpose RinvT (row-major), zeros below/above the diagonal.  With
-// `identity`, writes the identity (unpreconditioned iteration).
-__global__ void rinv_kernel(const double* __restrict__ W, int64_t ldw, int64_t n, double* __restrict__ Rinv,
-                            double* __restrict__ RinvT, int identity) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = gw; j < n; j += nw) {
-    // y[0..j] kept in the output column (Rinv[i*n + j]); start from e_j
-    for (int64_t i = lane; i < n; i += 32) {
-      Rinv[i * n + j] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncwarp();
+// of the iterative phase.  One CTA per column j solves R y = e_j by
+// column-oriented back substitution with the running column in shared memory:
+// at step k every thread reads y_k = y[k] / R[k, k] (final, since step k only
+// updates rows i < k), the owner of row k records it, and all threads update
+// their rows i < k; one barrier per step.  Writes Rinv (row-major) and its
+// transpose RinvT (row-major).  With `identity`, writes the identity
+// (unpreconditioned iteration).
+__global__ void __launch_bounds__(256) rinv_kernel(const double* __restrict__ W, int64_t ldw, int64_t n,
+                                                   double* __restrict__ Rinv, double* __restrict__ RinvT,
+                                                   int identity) {
+  extern __shared__ double ycol[];   // n
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ycol[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
     if (!identity) {
       for (int64_t k = j; k >= 0; --k) {
-        const double yk = Rinv[k * n + j] / W[k * ldw + k];
-        __syncwarp();
-        if (lane == 0) Rinv[k * n + j] = yk;
-        for (int64_t i = lane; i < k; i += 32) Rinv[i * n + j] = fma(-W[k * ldw + i], yk, Rinv[i * n + j]);
-        __syncwarp();
+        const double yk = ycol[k] / W[k * ldw + k];
+        const double* rk = W + k * ldw;          // column k of R: rows 0..k
+        __syncthreads();                         // everyone has read y[k]
+        if (threadIdx.x == 0) ycol[k] = yk;
+        for (int64_t i = threadIdx.x; i < k; i += blockDim.x) ycol[i] = fma(-rk[i], yk, ycol[i]);
+        __syncthreads();
       }
     }
-    for (int64_t i = lane; i < n; i += 32) RinvT[j * n + i] = Rinv[i * n + j];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = (i <= j) ? ycol[i] : 0.0;
+      Rinv[i * n + j] = v;
+      RinvT[j * n + i] = v;
+    }
+    __syncthreads();
   }
 }
 
 sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
                       cudaStream_t st) {
-  const int warps = 8;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + warps - 1) / warps, (int64_t)num_sms() * 4));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms() * 4));
+  const size_t smem = (size_t)n * 8;
+  SNS_CUDA_TRY(raise_smem_limit((const void*)rinv_kernel));
   {
     SNS_PROF(K_RINV, st);
-  rinv_kernel<<<grid, warps * 32, 0, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
+    rinv_kernel<<<grid, 256, smem, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;

@@ -130,7 +130,7 @@ static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sam
   int dp = 1;
   while (dp < d) dp <<= 1;
   const size_t smem = (size_t)(cap + dp) * 4;
-  SNS_CUDA_TRY(cudaFuncSetAttribute(srht_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)srht_sample_kernel));
   {
     SNS_PROF(K_SRHT_SAMPLE, st);
   srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, m2);
@@ -260,7 +260,7 @@ static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, 
   constexpr int kSrhtCT = srht_ct<T>();
   const int64_t ntile = (L.q + kSrhtCT - 1) / kSrhtCT;
   const size_t smem = ((size_t)kSrhtCT * (L.m2 + 1) + L.m2) * sizeof(T);
-  SNS_CUDA_TRY(cudaFuncSetAttribute(srht_pass1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)srht_pass1<T>));
   {
     SNS_PROF(K_SRHT_PASS1, st);
   srht_pass1<T><<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(static_cast<const T*>(a.A), a.lda,

@@ -138,3 +138,32 @@ print("WORST", worst)
     assert r.returncode == 0, r.stderr[-2000:]
     worst = float(r.stdout.split("WORST")[1])
     assert worst <= TOL32
+
+
+@pytest.mark.parametrize("variant", ["sorted", "stream"])
+@pytest.mark.parametrize("m,n,d", [(100, 64, 1000), (22271, 128, 4096), (5000, 300, 8192)])
+def test_empty_buckets_are_written_as_zero(variant, m, n, d):
+    """d comparable to or above m leaves buckets no row hashes to: their SA rows
+    and Sb entries must come out as zeros, whatever the output buffers held."""
+    import ctypes as C
+    import paper_2409_14309_gb300 as sns
+    c = ctx()
+    rng = np.random.default_rng(m + d)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    Ad, bd = dev(A), dev(b)
+    prob = sns.dense_problem(Ad, bd)
+    sk = sns.sketch_desc(d, "countsketch", 9, variant)
+    SA = torch.full((d, n), float("nan"), device="cuda")
+    Sb = torch.full((d,), float("nan"), device="cuda")
+    ws = torch.empty(max(c.sketch_workspace(prob, sk), 256), dtype=torch.uint8, device="cuda")
+    code = c._L.snsolve_sketch(c.h, C.byref(prob), C.byref(sk), C.c_void_p(SA.data_ptr()), n,
+                               C.c_void_p(Sb.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(), None)
+    assert code == 0
+    torch.cuda.synchronize()
+    h, _ = OH.countsketch_hash(9, m, d)
+    assert len(set(range(d)) - set(h.tolist())) > 0            # there are empty buckets
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
+    assert np.isfinite(SA.cpu().numpy()).all() and np.isfinite(Sb.cpu().numpy()).all()
+    assert rel_fro(SA.cpu().numpy(), OS.countsketch_apply(A, d, 9), scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 9), scale) <= TOL32
