@@ -167,3 +167,21 @@ def test_empty_buckets_are_written_as_zero(variant, m, n, d):
     assert np.isfinite(SA.cpu().numpy()).all() and np.isfinite(Sb.cpu().numpy()).all()
     assert rel_fro(SA.cpu().numpy(), OS.countsketch_apply(A, d, 9), scale) <= TOL32
     assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 9), scale) <= TOL32
+
+
+@pytest.mark.parametrize("m,n,d", [(777, 1, 5), (3000, 20, 80), (20000, 100, 333), (50000, 256, 1024),
+                                   (10000, 300, 1200)])
+def test_gaussian_sketch_tensor_core(m, n, d):
+    """Gaussian sketch on the tensor cores (BF16 G and BF16-rounded [A | b],
+    FP32 accumulation) against the oracle's FP64 product of the same BF16
+    operands."""
+    c = ctx()
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    SA, Sb = c.sketch(dev(A), dev(b), d, kind="gaussian", seed=13)
+    ref = OS.gaussian_apply(A, d, 13, bf16_operand=True)
+    refb = OS.gaussian_apply(b, d, 13, bf16_operand=True)
+    scale = np.sqrt(np.linalg.norm(ref) ** 2 + np.linalg.norm(refb) ** 2)
+    assert rel_fro(SA.cpu().numpy(), ref, scale) <= 1e-5
+    assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-5
