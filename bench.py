@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cs-variant", default="auto", choices=["auto", "sorted", "stream"])
-    ap.add_argument("--workload", default="solve", choices=["solve", "batched", "served"])
+    ap.add_argument("--workload", default="solve", choices=["solve", "batched", "served", "sketches"])
     ap.add_argument("--requests", type=int, default=400)
     args = ap.parse_args()
     warm = max(3, args.warmup)
@@ -214,6 +214,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "sketches":
+        return run_sketches(args)
 
     import torch
     import torch.distributed as dist
@@ -556,6 +558,54 @@ def run_served(args):
                        "budget_bytes": 150 << 30, "slots": 8},
             "served": served, "plain_one_slot": plain, "plain_capacity_solves_per_s": plain_cap["solves_per_s"]}
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ sketch kinds
+def run_sketches(args):
+    """snsolve_sketch alone on the 1048576 x 256 workload for every sketch kind:
+    HBM GB/s (A and b read once) and, for the Gaussian GEMM, tensor TFLOP/s."""
+    import torch
+    import paper_2409_14309_gb300 as sns
+    from paper_2409_14309_gb300 import abi
+    dev = torch.device("cuda", 0)
+    ctx = sns.Context(0)
+    L = abi.lib()
+    A_h, b_h = make_inputs(0, dev)
+    A = torch.from_numpy(A_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    hbm_peak, bf16_peak, kind_peak = peaks()
+    out = {}
+    for name, kind, variant in [("countsketch_sorted", "countsketch", "sorted"),
+                                ("countsketch_stream", "countsketch", "stream"),
+                                ("gaussian_tcgen05", "gaussian", "auto"), ("srht", "srht", "auto")]:
+        prob = sns.dense_problem(A, b)
+        sk = sns.sketch_desc(D, kind, SKETCH_SEED, variant)
+        ws = torch.empty(max(ctx.sketch_workspace(prob, sk), 256), dtype=torch.uint8, device=dev)
+        for _ in range(max(3, args.warmup)):
+            ctx.sketch_problem(prob, sk, torch.float32, ws=ws)
+        torch.cuda.synchronize()
+        L.snsolve_profile(1)
+        kernel_profile(L)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            ctx.sketch_problem(prob, sk, torch.float32, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = kernel_profile(L)
+        L.snsolve_profile(0)
+        ms = e0.elapsed_time(e1) / args.steps
+        byts = M * (N + 1) * 4.0
+        r = {"ms": ms, "GBps": byts / (ms / 1e3) / 1e9, "frac_hbm": byts / (ms / 1e3) / 1e9 / hbm_peak,
+             "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()}}
+        if kind == "gaussian":
+            fl = 2.0 * D * M * (N + 1)
+            r["TFLOPs"] = fl / (ms / 1e3) / 1e12
+            r["frac_bf16"] = r["TFLOPs"] / bf16_peak
+        out[name] = r
+    print(json.dumps({"metric": METRIC, "workload": "sketches", "config": {"m": M, "n": N, "d": D},
+                      "peaks": {"hbm_GBps": hbm_peak, "bf16_TFLOPs": bf16_peak, "kind": kind_peak},
+                      "sketches": out}))
 
 
 def run_reference(args, rank, world):

@@ -79,7 +79,8 @@ typedef enum {
  * Flood 2014): output i of stream t is mix64((seed ^ (t << 56)) + (i+1)*gamma).
  * CountSketch (t = 0): h(i) = ((k mod 2^32) * d) >> 32, s(i) = bit 63 ? -1 : +1.
  * SRHT: signs from t = 1, d distinct rows of [0, m') by Floyd's algorithm on t = 2.
- * Gaussian: G[k, i] = T[12-bit field (k mod 4) of output i*ceil(d/4) + k/4 of t = 3],
+ * Gaussian: G[k, i] = T[top 12 bits of 16-bit field (k div 8) mod 4 of output
+ * i*G + 8*(k div 32) + (k mod 8) of t = 3], G = 8*ceil(d/32),
  * T[j] = BF16(Phi^-1((j + 1/2)/4096)). */
 typedef struct {
   int32_t kind;        /* sns_sketch_kind */

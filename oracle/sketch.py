@@ -8,11 +8,12 @@ Three families, as the paper lists them:
   and a common scale does not change the minimiser).
 * Gaussian (Sec. 1.2.1): S = G / sqrt(d) with G iid Gaussian.  Reading (the paper
   fixes no generator): G[k, i] = T[j], j a 12-bit index drawn from the hash
-  stream, T[j] the BF16-rounded normal quantile Phi^{-1}((j + 1/2) / 4096).  Row
-  k of G uses 16-bit field (k mod 4) of SplitMix64 output i * ceil(d/4) + k // 4
-  of stream 3, and j is the top 12 bits of that field.  The tensor-core path
-  multiplies BF16 operands, so the oracle offers SA for both the exact A and the
-  BF16-rounded A.
+  stream, T[j] the BF16-rounded normal quantile Phi^{-1}((j + 1/2) / 4096).  One
+  SplitMix64 output of stream 3 serves the four rows k = 32 b + l + 8 q
+  (q = 0..3) of group g = 8 b + l (l = k mod 8, b = k div 32): row k uses 16-bit
+  field q = (k div 8) mod 4 of output i * G + g, G = 8 ceil(d / 32), and j is the
+  top 12 bits of that field.  The tensor-core path multiplies BF16 operands, so
+  the oracle offers SA for both the exact A and the BF16-rounded A.
 * Subsampled randomized Hadamard (Sec. 1.2.1): S = (1/sqrt(d)) P H D with
   m' = 2^ceil(log2 m) (rows m..m'-1 of [A | b] are zero), H the unnormalised
   Sylvester-Hadamard matrix H[p, i] = (-1)^popcount(p & i) applied by the fast
@@ -98,14 +99,21 @@ def gaussian_table():
     return round_to_bf16(q)
 
 
+def gaussian_groups(d):
+    """Number of hash groups per column of G: 8 per block of 32 rows."""
+    return 8 * ((d + 31) // 32)
+
+
 def gaussian_indices(m, d, seed):
     """Table index j[k, i] (d x m, int64) of every entry of G."""
-    groups = (d + 3) // 4
+    groups = gaussian_groups(d)
     i = np.arange(m, dtype=np.uint64)[None, :]
     k = np.arange(d, dtype=np.uint64)[:, None]
-    counter = i * np.uint64(groups) + (k >> np.uint64(2))
+    g = (k // np.uint64(32)) * np.uint64(8) + (k % np.uint64(8))
+    q = (k // np.uint64(8)) % np.uint64(4)
+    counter = i * np.uint64(groups) + g
     key = H.splitmix64_at(H.stream_state(seed, H.STREAM_GAUSSIAN), counter)
-    field = (key >> (np.uint64(16) * (k & np.uint64(3)))) & np.uint64(0xFFFF)
+    field = (key >> (np.uint64(16) * q)) & np.uint64(0xFFFF)
     return (field >> np.uint64(4)).astype(np.int64)
 
 

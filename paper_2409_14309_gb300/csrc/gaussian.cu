@@ -1,7 +1,9 @@
 // Gaussian sketch (Sec. 1.2.1: dense sketch with iid Gaussian entries):
 //   S [A | b] = (1/sqrt(d)) G [A | b],
-// G[k, i] = T[j], j = top 12 bits of 16-bit field (k mod 4) of SplitMix64
-// output i * ceil(d/4) + k/4 of stream 3, T[j] = BF16(Phi^-1((j + 1/2)/4096)).
+// G[k, i] = T[j], j = top 12 bits of 16-bit field q = (k div 8) mod 4 of
+// SplitMix64 output i * Gn + g of stream 3, g = 8 (k div 32) + (k mod 8),
+// Gn = 8 ceil(d / 32) (one output serves rows k, k + 8, k + 16, k + 24), and
+// T[j] = BF16(Phi^-1((j + 1/2)/4096)).
 // G is never stored: tiles are generated where they are consumed.  The operand
 // [A | b] is rounded to BF16 (round to nearest even) and products accumulate in
 // FP32, the precision of a BF16 tensor-core contraction.
@@ -81,23 +83,24 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   const int64_t k0 = tm * kGMt, j0 = tn * kGNt;
   const int64_t i_begin = (int64_t)blockIdx.y * kchunk;
   const int64_t i_end = std::min<int64_t>(m, i_begin + kchunk);
-  const int64_t groups = (d + 3) / 4;
+  const int64_t groups = 8 * ((d + 31) / 32);
   const int tx = tid % 16, ty = tid / 16;
   float acc[4][4] = {};
   __syncthreads();
   for (int64_t i0 = i_begin; i0 < i_end; i0 += kGKc) {
-    // G tile: kGKc rows of A (i) x kGMt rows of G (k); one hash per 4 k
+    // G tile: kGKc rows of A (i) x kGMt rows of G (k); one hash per 4 rows
+    // (k, k + 8, k + 16, k + 24) of a 32-row block
     for (int e = tid; e < kGKc * (kGMt / 4); e += blockDim.x) {
-      const int il = e / (kGMt / 4), g4 = e % (kGMt / 4);
+      const int il = e / (kGMt / 4), gl = e % (kGMt / 4);
       const int64_t i = i0 + il;
-      const int64_t kg = (k0 >> 2) + g4;
+      const int64_t g = (k0 / 32) * 8 + gl;
       uint64_t key = 0;
-      if (i < i_end && kg < groups) key = splitmix_at(s0, (uint64_t)i * (uint64_t)groups + (uint64_t)kg);
+      if (i < i_end) key = splitmix_at(s0, (uint64_t)i * (uint64_t)groups + (uint64_t)g);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int64_t k = kg * 4 + t;
+        const int kl = 32 * (gl / 8) + (gl % 8) + 8 * t;
         const uint32_t idx = (uint32_t)((key >> (16 * t + 4)) & 0xFFFu);
-        Gs[il][g4 * 4 + t] = (i < i_end && k < d) ? T[idx] : 0.f;
+        Gs[il][kl] = (i < i_end && k0 + kl < d) ? T[idx] : 0.f;
       }
     }
     // operand tile: BF16-rounded [A | b]
@@ -157,6 +160,7 @@ constexpr int kUN = 256;          // max columns per CTA
 constexpr int kUKC = kUKT / 8;    // core matrices along K
 constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 32 KB
 constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB
+constexpr uint32_t kUStaging = kUKT * kUN * 4;  // 64 KB of FP32 rows of A
 constexpr long long kUWait = 1LL << 24;
 
 SNS_D uint32_t u_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -186,6 +190,28 @@ SNS_D uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// Issues the bulk copies of rows [i0, i0 + rows) of A's column tile into the
+// staging buffer (row k at staging + k * ncols floats); warp 0 only.
+SNS_D void stage_rows(float* staging, const float* A, int64_t lda, int64_t col0, int ncols, int64_t i0, int rows,
+                      uint64_t* bar) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t rbytes = (uint32_t)ncols * 4u;
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(u_smem(bar)),
+                 "r"(rbytes * (uint32_t)rows)
+                 : "memory");
+  __syncwarp();
+  for (int k = lane; k < rows; k += 32)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            u_smem(staging + (size_t)k * ncols)),
+        "l"(A + (i0 + k) * lda + col0), "r"(rbytes), "r"(u_smem(bar))
+        : "memory");
+}
+
+// BULK: rows of A arrive by cp.async.bulk one chunk ahead (needs 16-byte
+// aligned rows and ncols % 4 == 0); otherwise each thread loads its elements.
+template <bool BULK>
 __global__ void __launch_bounds__(256, 1)
 gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
            uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
@@ -193,9 +219,11 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   extern __shared__ __align__(1024) uint8_t usm[];
   uint8_t* stA[2] = {usm, usm + kUStageA + kUStageB};
   uint8_t* stB[2] = {usm + kUStageA, usm + 2 * kUStageA + kUStageB};
-  uint16_t* T = reinterpret_cast<uint16_t*>(usm + 2 * (kUStageA + kUStageB));   // 4096 entries
+  float* staging = reinterpret_cast<float*>(usm + 2 * (kUStageA + kUStageB));
+  uint16_t* T = reinterpret_cast<uint16_t*>(usm + 2 * (kUStageA + kUStageB) + (BULK ? kUStaging : 0));
   float* bst = reinterpret_cast<float*>(T + 4096);                                 // [2][kUKT]
   __shared__ __align__(8) uint64_t mma_done[2];
+  __shared__ __align__(8) uint64_t rows_ready;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -206,11 +234,12 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   const bool with_b = (blockIdx.z == 0);
   const int64_t i_begin = (int64_t)blockIdx.y * kchunk;
   const int64_t i_end = min(m, i_begin + kchunk);
-  const int64_t groups = (d + 3) / 4;
+  const int64_t groups = 8 * ((d + 31) / 32);
   for (int j = tid; j < 4096; j += blockDim.x) T[j] = table[j];
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&rows_ready)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -229,51 +258,86 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   float sb_acc = 0.f;                                            // b column, row r_base + tid
   const int64_t nchunks = (i_end - i_begin + kUKT - 1) / kUKT;
   int64_t issued = 0;                                            // chunks whose MMAs were issued
+  if (BULK && nchunks > 0 && warp == 0)
+    stage_rows(staging, A, lda, col0, ncols, i_begin, (int)min((int64_t)kUKT, i_end - i_begin), &rows_ready);
   for (int64_t c = 0; c < nchunks; ++c) {
     const int s = (int)(c & 1);
     const int64_t u = c >> 1;                                    // use index of stage s
+    const int64_t i0 = i_begin + c * kUKT;
+    const int rows = (int)min((int64_t)kUKT, i_end - i0);
     if (u >= 1 && !u_wait(&mma_done[s], (uint32_t)((u - 1) & 1))) {
+      if (lane == 0) atomicExch(&s_fail, 1);
+    }
+    if (BULK && !u_wait(&rows_ready, (uint32_t)(c & 1))) {
       if (lane == 0) atomicExch(&s_fail, 1);
     }
     __syncthreads();
     if (s_fail) break;
-    const int64_t i0 = i_begin + c * kUKT;
     uint8_t* sA = stA[s];
     uint8_t* sB = stB[s];
-    // G tile: task (k pair, group of 4 rows): 32 x 64 tasks
-    for (int t = tid; t < (kUKT / 2) * (kUG / 4); t += blockDim.x) {
-      const int kp = t % (kUKT / 2), rg = t / (kUKT / 2);
-      const int k0 = 2 * kp;
-      const int64_t ia = i0 + k0, ib = ia + 1;
-      const int64_t g = r_base / 4 + rg;
-      uint64_t ka = 0, kb = 0;
-      const bool oka = ia < i_end && g < groups, okb = ib < i_end && g < groups;
-      if (oka) ka = splitmix_at(s0, (uint64_t)ia * (uint64_t)groups + (uint64_t)g);
-      if (okb) kb = splitmix_at(s0, (uint64_t)ib * (uint64_t)groups + (uint64_t)g);
+    // A chunk -> BF16, K-major: task (column nn, 8 consecutive k): one 16-byte
+    // store per task; consecutive threads take consecutive columns (distinct
+    // 16-byte bank groups)
+    for (int t = tid; t < kUKC * npad; t += blockDim.x) {
+      const int nn = t % npad, k8 = t / npad;
+      float f[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = 4 * rg + q;
-        const bool rowok = r_base + r < d;
-        const uint16_t va = (oka && rowok) ? T[(ka >> (16 * q + 4)) & 0xFFF] : (uint16_t)0;
-        const uint16_t vb = (okb && rowok) ? T[(kb >> (16 * q + 4)) & 0xFFF] : (uint16_t)0;
-        *reinterpret_cast<uint32_t*>(sA + kmaj_off(r, k0)) = (uint32_t)va | ((uint32_t)vb << 16);
+      for (int j = 0; j < 8; ++j) {
+        const int k = 8 * k8 + j;
+        float v = 0.f;
+        if (nn < ncols && k < rows) {
+          if (BULK) v = staging[(size_t)k * ncols + nn];
+          else v = __ldg(A + (i0 + k) * lda + col0 + nn);
+        }
+        f[j] = v;
       }
-    }
-    // A chunk: task (k pair, column) -> BF16 pair, K-major
-    for (int t = tid; t < (kUKT / 2) * npad; t += blockDim.x) {
-      const int nn = t % npad, kp = t / npad;
-      const int k0 = 2 * kp;
-      const int64_t ia = i0 + k0, ib = ia + 1;
-      float fa = 0.f, fb = 0.f;
-      if (nn < ncols) {
-        if (ia < i_end) fa = __ldg(A + ia * lda + col0 + nn);
-        if (ib < i_end) fb = __ldg(A + ib * lda + col0 + nn);
-      }
-      *reinterpret_cast<uint32_t*>(sB + kmaj_off(nn, k0)) = pack_bf16(fa, fb);
+      uint4 w;
+      w.x = pack_bf16(f[0], f[1]);
+      w.y = pack_bf16(f[2], f[3]);
+      w.z = pack_bf16(f[4], f[5]);
+      w.w = pack_bf16(f[6], f[7]);
+      *reinterpret_cast<uint4*>(sB + kmaj_off(nn, 8 * k8)) = w;
     }
     if (with_b && tid < kUKT) {
       const int64_t i = i0 + tid;
-      bst[s * kUKT + tid] = (i < i_end) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + i))) : 0.f;
+      bst[s * kUKT + tid] = (tid < rows) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + i))) : 0.f;
+    }
+    __syncthreads();                                             // staging consumed
+    if (BULK && c + 1 < nchunks && warp == 0)
+      stage_rows(staging, A, lda, col0, ncols, i0 + kUKT, (int)min((int64_t)kUKT, i_end - i0 - kUKT), &rows_ready);
+    // G tile: task (hash group gl, 8 consecutive k): 8 hashes give the 4 rows
+    // r = 32 (gl / 8) + gl % 8 + 8 q, q = 0..3 (field q) x 8 values.  The 8
+    // threads of a store phase take consecutive gl, hence 8 distinct r mod 8:
+    // 8 distinct 16-byte bank groups.
+    for (int t = tid; t < (kUG / 4) * kUKC; t += blockDim.x) {
+      const int gl = t % (kUG / 4), k8 = t / (kUG / 4);
+      const int64_t g = (r_base / 32) * 8 + gl;
+      const int rows_here = min(kUKT - 8 * k8, rows);
+      uint64_t ctr = (uint64_t)(i0 + 8 * k8) * (uint64_t)groups + (uint64_t)g;
+      uint64_t key[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        key[j] = (j < rows_here - 0 && 8 * k8 + j < rows) ? splitmix_at(s0, ctr) : 0ull;
+        ctr += (uint64_t)groups;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = 32 * (gl >> 3) + (gl & 7) + 8 * q;
+        const bool rowok = r_base + r < d;
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t word = (q < 2) ? (uint32_t)key[j] : (uint32_t)(key[j] >> 32);
+          const uint32_t idx = (word >> ((q & 1) * 16 + 4)) & 0xFFFu;
+          h[j] = (rowok && 8 * k8 + j < rows) ? (uint32_t)T[idx] : 0u;
+        }
+        uint4 w;
+        w.x = h[0] | (h[1] << 16);
+        w.y = h[2] | (h[3] << 16);
+        w.z = h[4] | (h[5] << 16);
+        w.w = h[6] | (h[7] << 16);
+        *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * k8)) = w;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -319,6 +383,8 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     const int64_t cl = issued - 1;
     ok = u_wait(&mma_done[cl & 1], (uint32_t)((cl >> 1) & 1));
   }
+  // a staged chunk that was never consumed (failure path) must land before exit
+  if (BULK && s_fail && issued < nchunks) u_wait(&rows_ready, (uint32_t)(issued & 1));
   __syncthreads();
   if (!ok || s_fail) {
     if (tid == 0) atomicExch(err, 1);
@@ -336,10 +402,18 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
           : "r"(a));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < d) {
+        float* dst = SA + row * ldsa + col0 + c0;
+        if (c0 + 16 <= ncols && ((uintptr_t)dst & 15) == 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          if (col < ncols) atomicAdd(SA + row * ldsa + col0 + col, __uint_as_float(v[j]) * scale);
+          for (int j = 0; j < 16; j += 4)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j),
+                         "f"(__uint_as_float(v[j]) * scale), "f"(__uint_as_float(v[j + 1]) * scale),
+                         "f"(__uint_as_float(v[j + 2]) * scale), "f"(__uint_as_float(v[j + 3]) * scale)
+                         : "memory");
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < ncols) atomicAdd(dst + j, __uint_as_float(v[j]) * scale);
         }
       }
     }
@@ -350,7 +424,9 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
 }
 
-size_t gauss_umma_smem() { return 2 * (size_t)(kUStageA + kUStageB) + 4096 * 2 + 2 * kUKT * 4; }
+size_t gauss_umma_smem(bool bulk) {
+  return 2 * (size_t)(kUStageA + kUStageB) + (bulk ? kUStaging : 0) + 4096 * 2 + 2 * kUKT * 4;
+}
 
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
                              int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
@@ -381,11 +457,13 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
     int64_t kchunk = (a.m + ksplit - 1) / ksplit;
     kchunk = ((kchunk + kUKT - 1) / kUKT) * kUKT;
     ksplit = (a.m + kchunk - 1) / kchunk;
-    SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
+    const bool bulk = (a.n % 4 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.A % 16 == 0);
+    auto kern = bulk ? gauss_umma<true> : gauss_umma<false>;
+    SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
     dim3 grid((unsigned)mtiles, (unsigned)ksplit, (unsigned)ntiles);
     {
       SNS_PROF(K_GAUSS, st);
-      gauss_umma<<<grid, 256, gauss_umma_smem(), st>>>(
+      kern<<<grid, 256, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
           stream_state(seed, kStreamGaussian), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
           err);

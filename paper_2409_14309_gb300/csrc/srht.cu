@@ -24,7 +24,7 @@ namespace sns {
 
 constexpr int kM2 = 1024;
 template <typename T>
-constexpr int srht_ct() { return sizeof(T) == 4 ? 32 : 16; }   // columns per pass-1 tile
+constexpr int srht_ct() { return sizeof(T) == 4 ? 16 : 8; }   // columns per pass-1 tile (3 CTAs per SM)
 constexpr int kSrhtMaxD = 16384;
 
 static int64_t np2(int64_t m) {
@@ -160,17 +160,30 @@ srht_pass1(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, int64_
     sgn[rl] = (row < m) ? ((splitmix_at(s_sign, (uint64_t)row) >> 63) ? T(-1) : T(1)) : T(0);
   }
   __syncthreads();
-  // load D [A | b] (rows coalesced along columns)
-  for (int64_t e = threadIdx.x; e < m2 * kSrhtCT; e += blockDim.x) {
-    const int64_t rl = e / kSrhtCT;
-    const int c = (int)(e % kSrhtCT);
-    const int64_t row = r0 + rl;
-    T v = T(0);
-    if (row < m && c < ncol) {
+  // load D [A | b] (rows coalesced along columns), 16 independent loads in
+  // flight per thread before they are stored
+  constexpr int kL = 16;
+  for (int64_t e0 = threadIdx.x; e0 < m2 * kSrhtCT; e0 += (int64_t)blockDim.x * kL) {
+    T v[kL];
+#pragma unroll
+    for (int u = 0; u < kL; ++u) {
+      const int64_t e = e0 + (int64_t)u * blockDim.x;
+      const int64_t rl = e / kSrhtCT;
+      const int c = (int)(e % kSrhtCT);
+      const int64_t row = r0 + rl;
       const int64_t col = c0 + c;
-      v = sgn[rl] * ((col < n) ? A[row * lda + col] : b[row]);
+      v[u] = T(0);
+      if (e < m2 * kSrhtCT && row < m && c < ncol) v[u] = (col < n) ? __ldg(A + row * lda + col) : __ldg(b + row);
     }
-    tile[(int64_t)c * ldt + rl] = v;
+#pragma unroll
+    for (int u = 0; u < kL; ++u) {
+      const int64_t e = e0 + (int64_t)u * blockDim.x;
+      if (e < m2 * kSrhtCT) {
+        const int64_t rl = e / kSrhtCT;
+        const int c = (int)(e % kSrhtCT);
+        tile[(int64_t)c * ldt + rl] = sgn[rl] * v[u];
+      }
+    }
   }
   __syncthreads();
   // transform: one warp per column; lane holds x[k] = tile[32 k + lane]
@@ -233,15 +246,25 @@ srht_pass2(const T* __restrict__ Y, int64_t ldy, int64_t q, int64_t m1, int64_t 
   const int64_t p = sample[k];
   const int64_t p1 = p / m2, p2 = p % m2;
   for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
-    // compensated (Kahan-Babuska) summation of the m1 signed terms
+    // compensated (Kahan-Babuska) summation of the m1 signed terms; 16 rows of
+    // Y are loaded before they are added, so 16 loads are in flight
+    constexpr int kL = 16;
     T acc = T(0), err = T(0);
-#pragma unroll 8
-    for (int64_t i1 = 0; i1 < m1; ++i1) {
-      T v = Y[(i1 * m2 + p2) * ldy + c];
-      v = (__popcll((unsigned long long)(p1 & i1)) & 1) ? -v : v;
-      const T s = acc + v;
-      err += (fabs(acc) >= fabs(v)) ? ((acc - s) + v) : ((v - s) + acc);
-      acc = s;
+    for (int64_t i0 = 0; i0 < m1; i0 += kL) {
+      T v[kL];
+#pragma unroll
+      for (int u = 0; u < kL; ++u) {
+        const int64_t i1 = i0 + u;
+        v[u] = (i1 < m1) ? __ldg(Y + (i1 * m2 + p2) * ldy + c) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kL; ++u) {
+        const int64_t i1 = i0 + u;
+        const T w = (__popcll((unsigned long long)(p1 & i1)) & 1) ? -v[u] : v[u];
+        const T s = acc + w;
+        err += (fabs(acc) >= fabs(w)) ? ((acc - s) + w) : ((w - s) + acc);
+        acc = s;
+      }
     }
     acc = (acc + err) * scale;
     if (c < q - 1) SA[k * ldsa + c] = acc;

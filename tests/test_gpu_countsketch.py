@@ -185,3 +185,32 @@ def test_gaussian_sketch_tensor_core(m, n, d):
     scale = np.sqrt(np.linalg.norm(ref) ** 2 + np.linalg.norm(refb) ** 2)
     assert rel_fro(SA.cpu().numpy(), ref, scale) <= 1e-5
     assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-5
+
+
+def test_gaussian_simt_variant_in_subprocess():
+    """The CUDA-core Gaussian kernel (SNSOLVE_GAUSS=simt) follows the same
+    definition of G as the tensor-core kernel."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, ".")
+import paper_2409_14309_gb300 as sns
+from oracle import sketch as OS
+c = sns.Context(0)
+worst = 0.0
+for (m, n, d) in [(3000, 20, 80), (20000, 100, 333)]:
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32); b = rng.standard_normal(m).astype(np.float32)
+    SA, Sb = c.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), d, kind="gaussian", seed=13)
+    ref = OS.gaussian_apply(A, d, 13); refb = OS.gaussian_apply(b, d, 13)
+    scale = np.sqrt(np.linalg.norm(ref)**2 + np.linalg.norm(refb)**2)
+    worst = max(worst, np.linalg.norm(SA.cpu().numpy() - ref) / scale, np.linalg.norm(Sb.cpu().numpy() - refb) / scale)
+print("WORST", worst)
+'''
+    env = dict(os.environ, SNSOLVE_GAUSS="simt")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert float(r.stdout.split("WORST")[1]) <= 1e-5

@@ -75,9 +75,15 @@ def test_gaussian_indices_uniform_and_field_layout():
     counts = np.bincount(j.ravel() >> 6, minlength=64)          # 64 coarse bins
     e = j.size / 64
     assert ((counts - e) ** 2 / e).sum() < 64 + 6 * math.sqrt(128)
-    # row k uses the top 12 bits of 16-bit field k % 4 of output i*ceil(d/4) + k//4
-    key = H.splitmix64_at(H.stream_state(5, 3), np.array([7 * 3 + 2], dtype=np.uint64))
+    # row k = 32 b + l + 8 q uses the top 12 bits of 16-bit field q of output
+    # i * G + (8 b + l), G = 8 * ceil(d / 32); d = 10: G = 8, row 9 -> l = 1, q = 1
+    key = H.splitmix64_at(H.stream_state(5, 3), np.array([7 * 8 + 1], dtype=np.uint64))
     assert j[9, 7] == (int(key[0]) >> (16 * 1 + 4)) & 0xFFF
+    # every output feeds four rows 8 apart: rows 1, 9 (and 17, 25 when present)
+    jj = S.gaussian_indices(40, 64, seed=5)
+    key = H.splitmix64_at(H.stream_state(5, 3), np.array([3 * 16 + 8 + 2], dtype=np.uint64))   # i=3, b=1, l=2
+    for q in range(4):
+        assert jj[32 + 2 + 8 * q, 3] == (int(key[0]) >> (16 * q + 4)) & 0xFFF
 
 
 def test_gaussian_sketch_and_solve_expected_residual():
