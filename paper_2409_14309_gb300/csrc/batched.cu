@@ -178,7 +178,8 @@ static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 
 static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_t* w, const BatchLayout& L,
                             const void* host_tasks, size_t task_bytes, cudaStream_t st, bool use_graph) {
-  const size_t smem = (size_t)dmax * (S.ct + 1) * 4;
+  // sketch tile; reused as QR scratch (d doubles) and back-substitution scratch (2 q <= 2 d + 2 doubles)
+  const size_t smem = std::max((size_t)dmax * (S.ct + 1) * 4, (size_t)(2 * dmax + 2) * 8);
   if (smem > 227 * 1024 || S.ct > 95) return SNS_EINVAL;   // the row loop covers 3 x 32 tile columns
   SNS_CUDA_TRY(raise_smem_limit((const void*)batched_fused));
   int occ = 0;

@@ -108,7 +108,7 @@ SNS_D double ff_to_double(ff v) { return (double)v.hi + (double)v.lo; }
 SNS_D bool spin_until_ge(const volatile int* flag, int target, long long limit) {
   for (long long it = 0; it < limit; ++it) {
     if (*flag >= target) return true;
-    __nanosleep(64);
+    if (it >= 4096) __nanosleep(32);   // tight polling first: the flags of the QR flip within microseconds
   }
   return *flag >= target;
 }

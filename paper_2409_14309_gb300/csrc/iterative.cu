@@ -33,9 +33,9 @@ namespace sns {
 
 constexpr int kPassThreads = 256;
 constexpr int kPassWarps = kPassThreads / 32;
-constexpr int kPassU = 2;       // rows in flight per warp
+constexpr int kNormU = 4;       // rows in flight per warp (normal pass)
 
-int iter_grid() { return num_sms() * 2; }
+int iter_grid() { return num_sms() * 4; }
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -47,7 +47,8 @@ size_t iter_ws_bytes(int64_t n, int grid) {
   s += 3 * al256((size_t)n * 4);              // xhi xlo z32
   s += al256((size_t)grid * n * 4);           // part
   s += al256((size_t)grid * (n + 4) * 8);     // partd
-  s += al256(64);                             // ticket
+  s += al256(64 * 4);                         // tickets (groups + top)
+  s += al256((size_t)64 * (n + 4) * 8);       // level-2 partials
   return s;
 }
 
@@ -72,7 +73,8 @@ IterWs iter_ws_carve(void* base, int64_t n, int grid) {
   W.z32 = (float*)take(n * 4);
   W.part = (float*)take((size_t)grid * n * 4);
   W.partd = (double*)take((size_t)grid * (n + 4) * 8);
-  W.ticket = (uint32_t*)take(64);
+  W.ticket = (uint32_t*)take(64 * 4);
+  W.lvl2 = (double*)take((size_t)64 * (n + 4) * 8);
   W.grid = grid;
   return W;
 }
@@ -80,15 +82,47 @@ IterWs iter_ws_carve(void* base, int64_t n, int grid) {
 // Scalar slots in W.scal.
 enum { kRR = 0, kRnorm2 = 1, kAnorm2 = 2, kEta = 3, kGnorm2 = 4, kRnorm = 5, kPQ = 6 };
 
-// Last-CTA detection: returns true in every thread of the CTA that finished last.
-SNS_D bool last_cta(uint32_t* ticket) {
+// Deterministic two-level reduction of per-CTA partial rows.  CTA b has
+// written its row part[b * stride + c], c < nc.  CTAs form groups of 32; the
+// last CTA of a group (ticket) adds the group's rows in CTA order (FP64) into
+// lvl2[group]; the last group to finish adds the group sums in group order and
+// calls emit(c, value).  Tickets are reset by the CTAs that consume them.
+constexpr int kRedGroup = 32;
+template <typename PT, typename F>
+SNS_D void tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, uint32_t* __restrict__ tickets,
+                       double* __restrict__ lvl2, F&& emit) {
   __shared__ int s_last;
+  const int64_t G = gridDim.x;
+  const int64_t ngroups = (G + kRedGroup - 1) / kRedGroup;
+  const int64_t grp = blockIdx.x / kRedGroup;
+  const int64_t gsize = min((int64_t)kRedGroup, G - grp * kRedGroup);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) s_last = (atomicAdd(tickets + grp, 1u) == (uint32_t)(gsize - 1));
   __syncthreads();
-  if (s_last) __threadfence();
-  return s_last != 0;
+  if (!s_last) return;
+  __threadfence();
+  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
+    double acc = 0.0;
+    const PT* pc = part + grp * kRedGroup * stride + c;
+#pragma unroll 8
+    for (int64_t k = 0; k < gsize; ++k) acc += (double)__ldcg(pc + k * stride);
+    lvl2[grp * stride + c] = acc;
+  }
+  if (threadIdx.x == 0) tickets[grp] = 0;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(tickets + ngroups, 1u) == (uint32_t)(ngroups - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int64_t q = 0; q < ngroups; ++q) acc += __ldcg(lvl2 + q * stride + c);
+    emit(c, acc);
+  }
+  if (threadIdx.x == 0) tickets[ngroups] = 0;
 }
 
 // ------------------------------------------------------------------ dense FP32
@@ -123,11 +157,34 @@ SNS_D void ldv(const float* p, float (&v)[VEC]) {
   }
 }
 
-template <int VEC, int NCH>
+SNS_D Comp comp_plus(Comp a, Comp b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return {s, (a.lo + b.lo) + e};
+}
+SNS_D Comp comp_shfl_xor(Comp c, int o) {
+  return {__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o)};
+}
+
+// Residual pass, dense FP32: r = b - A x in FP64-class accuracy, g = A^T r,
+// ||r||^2 (and ||A||_F^2 when ANORM).  Each warp takes U rows (4 or 2) at a time.
+// Row dots use exact products (TwoProdFMA) and compensated sums, since b - A x
+// cancels; a U-row reduce-scatter butterfly leaves row u's total in lanes
+// u*32/U .. (u+1)*32/U - 1.  For g, EXACT adds every product exactly (TwoProdFMA,
+// compensated sum, plus the a * r_lo term).  Without EXACT, per column the U
+// rows' products a * r_hi are summed in FP32 and that partial is added with a
+// compensated sum: the accumulation stays error-free to float-float accuracy
+// and only per-term rounding remains, so ||dg|| <~ eps32 * max_i ||a_i|| * ||r||,
+// i.e. an eta floor of at most ~3e-8 even when one row carries all of ||A||_F
+// (below 1e-9 for incoherent rows at m >= 1e4).
+template <int VEC, int NCH, int U, bool ANORM, bool EXACT>
 __global__ void __launch_bounds__(kPassThreads)
 resid_pass_f32(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
-               const double* __restrict__ x, double* __restrict__ partd, uint32_t* __restrict__ ticket,
-               double* __restrict__ g, double* __restrict__ scal, int want_anorm) {
+               const double* __restrict__ x, double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2,
+               double* __restrict__ g, double* __restrict__ scal) {
+  static_assert(U == 4 || U == 2, "reduce-scatter over 4 or 2 rows");
+  constexpr int kLpr = 32 / U;                        // lanes per row after the butterfly
   __shared__ double sred[kPassWarps][3];
   extern __shared__ __align__(16) double dsm[];      // [kPassWarps][n] doubles
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -146,15 +203,18 @@ resid_pass_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
       gacc[q][v] = {0.f, 0.f};
     }
   }
-  double rr = 0.0;
+  const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+  const int urow = lane / kLpr;                       // row of the lane group after the butterfly
+  // ||r||^2 of the rows this lane group finishes (the group's first lane counts)
+  Comp rrc = {0.f, 0.f};
   float an = 0.f;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r0 = gw * kPassU; r0 < m; r0 += nw * kPassU) {
-    float a[kPassU][NCH][VEC];
-    float bv[kPassU];
+  for (int64_t r0 = gw * U; r0 < m; r0 += nw * U) {
+    float a[U][NCH][VEC];
+    float bv[U];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < U; ++u) {
       const bool rok = r0 + u < m;
       const float* rp = A + (r0 + u) * lda + lane * VEC;
 #pragma unroll
@@ -166,62 +226,102 @@ resid_pass_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
       }
       bv[u] = rok ? __ldg(b + r0 + u) : 0.f;
     }
+    Comp s[U];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
-      Comp s = {0.f, 0.f};
+    for (int u = 0; u < U; ++u) {
+      s[u] = {0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-          comp_fma(s, a[u][q][v], xh[q][v]);
-          s.lo = fmaf(a[u][q][v], xl[q][v], s.lo);
-          an = fmaf(a[u][q][v], a[u][q][v], an);
+          comp_fma(s[u], a[u][q][v], xh[q][v]);
+          s[u].lo = fmaf(a[u][q][v], xl[q][v], s[u].lo);
+          if (ANORM) an = fmaf(a[u][q][v], a[u][q][v], an);
         }
-      // warp sum of the compensated dot
-      float hi = s.hi, lo = s.lo;
+    }
+    // reduce-scatter: xor 16 splits rows {0,1} | {2,3}, xor 8 splits the pair,
+    // xor 4, 2, 1 finish the row's sum
+    Comp kk;
+    float bme;
+    if constexpr (U == 4) {
+      Comp k0 = up16 ? s[2] : s[0], k1 = up16 ? s[3] : s[1];
+      const Comp g0 = up16 ? s[0] : s[2], g1 = up16 ? s[1] : s[3];
+      k0 = comp_plus(k0, comp_shfl_xor(g0, 16));
+      k1 = comp_plus(k1, comp_shfl_xor(g1, 16));
+      kk = up8 ? k1 : k0;
+      kk = comp_plus(kk, comp_shfl_xor(up8 ? k0 : k1, 8));
+      bme = urow == 0 ? bv[0] : urow == 1 ? bv[1] : urow == 2 ? bv[2] : bv[3];
+    } else {
+      kk = up16 ? s[1] : s[0];
+      kk = comp_plus(kk, comp_shfl_xor(up16 ? s[0] : s[1], 16));
+      kk = comp_plus(kk, comp_shfl_xor(kk, 8));
+      bme = up16 ? bv[1] : bv[0];
+    }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-        Comp c = {hi, lo + ol};
-        comp_add(c, oh);
-        hi = c.hi;
-        lo = c.lo;
-      }
-      // r = b - dot (as hi + lo)
-      Comp r = {bv[u], 0.f};
-      comp_add(r, -hi);
-      r.lo -= lo;
-      const float rh = r.hi + r.lo;
-      const float rl = r.lo - (rh - r.hi);
-      if (lane == 0 && r0 + u < m) rr = fma((double)rh + rl, (double)rh + rl, rr);
+    for (int o = 4; o > 0; o >>= 1) kk = comp_plus(kk, comp_shfl_xor(kk, o));
+    // r = b - dot for this lane's row
+    Comp r = {bme, 0.f};
+    comp_add(r, -kk.hi);
+    r.lo -= kk.lo;
+    const float rh = r.hi + r.lo;
+    const float rl = r.lo - (rh - r.hi);
+    if (lane % kLpr == 0 && r0 + urow < m) {
+      comp_fma(rrc, rh, rh);
+      rrc.lo = fmaf(2.f * rh, rl, rrc.lo);
+    }
+    float rhu[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) rhu[u] = __shfl_sync(0xffffffffu, rh, kLpr * u);
+    if constexpr (EXACT) {
+      float rlu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) rlu[u] = __shfl_sync(0xffffffffu, rl, kLpr * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < NCH; ++q)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            comp_fma(gacc[q][v], a[u][q][v], rhu[u]);
+            gacc[q][v].lo = fmaf(a[u][q][v], rlu[u], gacc[q][v].lo);
+          }
+    } else {
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-          comp_fma(gacc[q][v], a[u][q][v], rh);
-          gacc[q][v].lo = fmaf(a[u][q][v], rl, gacc[q][v].lo);
+          float t = a[0][q][v] * rhu[0];
+#pragma unroll
+          for (int u = 1; u < U; ++u) t = fmaf(a[u][q][v], rhu[u], t);
+          comp_add(gacc[q][v], t);
         }
     }
   }
-  // CTA reduction in FP64, fixed order
-  double* myrow = dsm + (size_t)w * n;
+  // CTA reduction in float-float (fixed order), one conversion to FP64 per
+  // column: FP64 instructions are scarce on this part
+  float2* myrow = reinterpret_cast<float2*>(dsm) + (size_t)w * n;
 #pragma unroll
   for (int q = 0; q < NCH; ++q)
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
       const int64_t c = (int64_t)q * 32 * VEC + lane * VEC + v;
-      if (c < n) myrow[c] = (double)gacc[q][v].hi + (double)gacc[q][v].lo;
+      if (c < n) myrow[c] = make_float2(gacc[q][v].hi, gacc[q][v].lo);
     }
-  const double rrw = warp_sum(rr);
-  const double anw = warp_sum((double)an);
+  const double rrw = warp_sum(lane % kLpr == 0 ? (double)rrc.hi + (double)rrc.lo : 0.0);
+  const double anw = ANORM ? warp_sum((double)an) : 0.0;
   if (lane == 0) { sred[w][0] = rrw; sred[w][1] = anw; }
   __syncthreads();
   double* out = partd + (size_t)blockIdx.x * (n + 4);
+  const float2* rows = reinterpret_cast<const float2*>(dsm);
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-    double s = 0.0;
-    for (int ww = 0; ww < kPassWarps; ++ww) s += dsm[(size_t)ww * n + c];
-    out[c] = s;
+    const float2 f0 = rows[c];
+    Comp acc = {f0.x, f0.y};
+#pragma unroll
+    for (int ww = 1; ww < kPassWarps; ++ww) {
+      const float2 f = rows[(size_t)ww * n + c];
+      acc = comp_plus(acc, Comp{f.x, f.y});
+    }
+    out[c] = (double)acc.hi + (double)acc.lo;
   }
   if (threadIdx.x == 0) {
     double a0 = 0.0, a1 = 0.0;
@@ -229,22 +329,17 @@ resid_pass_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
     out[n] = a0;
     out[n + 1] = a1;
   }
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n + 2; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partd + (size_t)k * (n + 4) + c);
-      if (c < n) g[c] = s;
-      else if (c == n) scal[kRnorm2] = s;
-      else if (want_anorm) scal[kAnorm2] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(partd, n + 4, n + 2, ticket, lvl2, [&](int64_t c, double s) {
+    if (c < n) g[c] = s;
+    else if (c == n) scal[kRnorm2] = s;
+    else if (ANORM) scal[kAnorm2] = s;
+  });
 }
 
 template <int VEC, int NCH>
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ z32,
-                float* __restrict__ part, uint32_t* __restrict__ ticket, double* __restrict__ wout) {
+                float* __restrict__ part, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
   extern __shared__ __align__(16) float fsm[];       // [kPassWarps][n]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float zr[NCH][VEC], acc[NCH][VEC];
@@ -261,10 +356,10 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
   }
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r0 = gw * kPassU; r0 < m; r0 += nw * kPassU) {
-    float a[kPassU][NCH][VEC];
+  for (int64_t r0 = gw * kNormU; r0 < m; r0 += nw * kNormU) {
+    float a[kNormU][NCH][VEC];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kNormU; ++u) {
       const bool rok = r0 + u < m;
       const float* rp = A + (r0 + u) * lda + lane * VEC;
 #pragma unroll
@@ -276,7 +371,7 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
       }
     }
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kNormU; ++u) {
       float t = 0.f;
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
@@ -304,20 +399,13 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
     for (int ww = 0; ww < kPassWarps; ++ww) s += fsm[(size_t)ww * n + c];
     out[c] = s;
   }
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += (double)__ldcg(part + (size_t)k * n + c);
-      wout[c] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
 }
 
 // ------------------------------------------------------------------ FP64 dense
 __global__ void __launch_bounds__(kPassThreads)
 resid_pass_f64(const double* __restrict__ A, int64_t lda, const double* __restrict__ b, int64_t m, int64_t n,
-               const double* __restrict__ x, double* __restrict__ partd, uint32_t* __restrict__ ticket,
+               const double* __restrict__ x, double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2,
                double* __restrict__ g, double* __restrict__ scal, int want_anorm) {
   extern __shared__ __align__(16) double dsm[];      // x[n], gl[n]
   double* xs = dsm;
@@ -350,21 +438,16 @@ resid_pass_f64(const double* __restrict__ A, int64_t lda, const double* __restri
     out[n] = a0;
     out[n + 1] = a1;
   }
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n + 2; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partd + (size_t)k * (n + 4) + c);
-      if (c < n) g[c] = s;
-      else if (c == n) scal[kRnorm2] = s;
-      else if (want_anorm) scal[kAnorm2] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(partd, n + 4, n + 2, ticket, lvl2, [&](int64_t c, double s) {
+    if (c < n) g[c] = s;
+    else if (c == n) scal[kRnorm2] = s;
+    else if (want_anorm) scal[kAnorm2] = s;
+  });
 }
 
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, const double* __restrict__ z,
-                double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ wout) {
+                double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
   extern __shared__ __align__(16) double dsm[];      // z[n], wl[n]
   double* zs = dsm;
   double* wl = dsm + n;
@@ -383,21 +466,14 @@ normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
   __syncthreads();
   double* out = partd + (size_t)blockIdx.x * (n + 4);
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = wl[c];
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partd + (size_t)k * (n + 4) + c);
-      wout[c] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(partd, n + 4, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
 }
 
 // ------------------------------------------------------------------ CSR
 __global__ void __launch_bounds__(kPassThreads)
 resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                const float* __restrict__ b, int64_t m, int64_t n, const double* __restrict__ x,
-               double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ g,
+               double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ g,
                double* __restrict__ scal, int want_anorm) {
   extern __shared__ __align__(16) double dsm[];      // x[n], gl[n]
   double* xs = dsm;
@@ -435,22 +511,17 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
     out[n] = a0;
     out[n + 1] = a1;
   }
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n + 2; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partd + (size_t)k * (n + 4) + c);
-      if (c < n) g[c] = s;
-      else if (c == n) scal[kRnorm2] = s;
-      else if (want_anorm) scal[kAnorm2] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(partd, n + 4, n + 2, ticket, lvl2, [&](int64_t c, double s) {
+    if (c < n) g[c] = s;
+    else if (c == n) scal[kRnorm2] = s;
+    else if (want_anorm) scal[kAnorm2] = s;
+  });
 }
 
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                 int64_t m, int64_t n, const float* __restrict__ z32, float* __restrict__ part,
-                uint32_t* __restrict__ ticket, double* __restrict__ wout) {
+                uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
   extern __shared__ __align__(16) float fsm[];       // z[n], wl[n]
   float* zs = fsm;
   float* wl = fsm + n;
@@ -471,29 +542,24 @@ normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ 
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * n;
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = wl[c];
-  if (last_cta(ticket)) {
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-      double s = 0.0;
-      for (unsigned k = 0; k < gridDim.x; ++k) s += (double)__ldcg(part + (size_t)k * n + c);
-      wout[c] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-  }
+  tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
 }
 
 // ------------------------------------------------------------------ launchers
 template <int VEC, int NCH>
 static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const double* x, bool resid, bool want_anorm,
-                                   cudaStream_t st) {
+                                   bool exact_g, cudaStream_t st) {
   const float* A = static_cast<const float*>(a.A);
   if (resid) {
     const size_t smem = (size_t)kPassWarps * a.n * 8;
-    auto k = resid_pass_f32<VEC, NCH>;
+    constexpr int U = (VEC * NCH <= 8) ? 4 : 2;      // rows per warp step within the register budget
+    auto k = want_anorm ? (exact_g ? resid_pass_f32<VEC, NCH, U, true, true> : resid_pass_f32<VEC, NCH, U, true, false>)
+                        : (exact_g ? resid_pass_f32<VEC, NCH, U, false, true> : resid_pass_f32<VEC, NCH, U, false, false>);
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     {
       SNS_PROF(K_RESID, st);
-    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket,
-                                          W.g, W.scal, want_anorm ? 1 : 0);
+    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket, W.lvl2,
+                                          W.g, W.scal);
     }
   } else {
     const size_t smem = (size_t)kPassWarps * a.n * 4;
@@ -501,7 +567,7 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     {
       SNS_PROF(K_NORMAL, st);
-    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.w);
+    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.lvl2, W.w);
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -509,26 +575,26 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
 }
 
 static sns_status dense_f32_dispatch(const DenseArgs& a, const IterWs& W, const double* x, bool resid,
-                                     bool want_anorm, cudaStream_t st) {
+                                     bool want_anorm, bool exact_g, cudaStream_t st) {
   const bool v4 = (a.lda % 4 == 0) && (a.n % 4 == 0) && ((uintptr_t)a.A % 16 == 0);
   if (v4) {
-    if (a.n <= 128) return launch_dense_f32<4, 1>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 256) return launch_dense_f32<4, 2>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 512) return launch_dense_f32<4, 4>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 1024) return launch_dense_f32<4, 8>(a, W, x, resid, want_anorm, st);
+    if (a.n <= 128) return launch_dense_f32<4, 1>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 256) return launch_dense_f32<4, 2>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 512) return launch_dense_f32<4, 4>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 1024) return launch_dense_f32<4, 8>(a, W, x, resid, want_anorm, exact_g, st);
   } else {
-    if (a.n <= 32) return launch_dense_f32<1, 1>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 128) return launch_dense_f32<1, 4>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 256) return launch_dense_f32<1, 8>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 512) return launch_dense_f32<1, 16>(a, W, x, resid, want_anorm, st);
-    if (a.n <= 1024) return launch_dense_f32<1, 32>(a, W, x, resid, want_anorm, st);
+    if (a.n <= 32) return launch_dense_f32<1, 1>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 128) return launch_dense_f32<1, 4>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 256) return launch_dense_f32<1, 8>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 512) return launch_dense_f32<1, 16>(a, W, x, resid, want_anorm, exact_g, st);
+    if (a.n <= 1024) return launch_dense_f32<1, 32>(a, W, x, resid, want_anorm, exact_g, st);
   }
   return SNS_EINVAL;
 }
 
-sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, const IterWs& W, bool want_anorm,
+sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, const IterWs& W, bool want_anorm, bool exact_g,
                       cudaStream_t st) {
-  if (da && !da->f64) return dense_f32_dispatch(*da, W, x, true, want_anorm, st);
+  if (da && !da->f64) return dense_f32_dispatch(*da, W, x, true, want_anorm, exact_g, st);
   if (da) {
     const size_t smem = (size_t)da->n * 16;
     SNS_CUDA_TRY(raise_smem_limit((const void*)resid_pass_f64));
@@ -536,7 +602,7 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
       SNS_PROF(K_RESID, st);
     resid_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda,
                                                        static_cast<const double*>(da->b), da->m, da->n, x, W.partd,
-                                                       W.ticket, W.g, W.scal, want_anorm ? 1 : 0);
+                                                       W.ticket, W.lvl2, W.g, W.scal, want_anorm ? 1 : 0);
     }
   } else {
     const size_t smem = (size_t)ca->n * 16;
@@ -544,7 +610,7 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
     {
       SNS_PROF(K_RESID, st);
     resid_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->b, ca->m, ca->n, x, W.partd,
-                                                       W.ticket, W.g, W.scal, want_anorm ? 1 : 0);
+                                                       W.ticket, W.lvl2, W.g, W.scal, want_anorm ? 1 : 0);
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -552,14 +618,14 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
 }
 
 sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, cudaStream_t st) {
-  if (da && !da->f64) return dense_f32_dispatch(*da, W, nullptr, false, false, st);
+  if (da && !da->f64) return dense_f32_dispatch(*da, W, nullptr, false, false, false, st);
   if (da) {
     const size_t smem = (size_t)da->n * 16;
     SNS_CUDA_TRY(raise_smem_limit((const void*)normal_pass_f64));
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda, da->m, da->n,
-                                                        W.z, W.partd, W.ticket, W.w);
+                                                        W.z, W.partd, W.ticket, W.lvl2, W.w);
     }
   } else {
     const size_t smem = (size_t)ca->n * 8;
@@ -567,7 +633,7 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->m, ca->n, W.z32, W.part,
-                                                        W.ticket, W.w);
+                                                        W.ticket, W.lvl2, W.w);
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -576,15 +642,30 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
 
 // out_i = sum_k M[i, k] v[k] (row-major n x n); optional FP32 copy and
 // accum += alpha * out.  One warp per row.
-__global__ void small_matvec_kernel(const double* __restrict__ M, const double* __restrict__ v, int64_t n,
-                                    double* __restrict__ out, float* __restrict__ out32, double alpha,
-                                    double* __restrict__ accum) {
+// Small dense FP64 matvec out = M v (n x n, row-major; R^-1 or R^-T): one warp
+// per row, 4 rows per 128-thread CTA, each lane's loads issued together.
+constexpr int kSmallThreads = 128;
+__global__ void __launch_bounds__(kSmallThreads)
+small_matvec_kernel(const double* __restrict__ M, const double* __restrict__ v, int64_t n,
+                    double* __restrict__ out, float* __restrict__ out32, double alpha, double* __restrict__ accum) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n; i += nw) {
+    const double* mr = M + i * n;
     double s = 0.0;
-    for (int64_t k = lane; k < n; k += 32) s = fma(M[i * n + k], v[k], s);
+    int64_t k = lane;
+    for (; k + 224 < n; k += 256) {
+      double mv[8], vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        mv[u] = __ldg(mr + k + 32 * u);
+        vv[u] = __ldg(v + k + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = fma(mv[u], vv[u], s);
+    }
+    for (; k < n; k += 32) s = fma(__ldg(mr + k), __ldg(v + k), s);
     s = warp_sum(s);
     if (lane == 0) {
       if (out) out[i] = s;
@@ -596,19 +677,33 @@ __global__ void small_matvec_kernel(const double* __restrict__ M, const double* 
 
 sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
                         double* accum, cudaStream_t st) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)num_sms()));
+  const int rows_per_cta = kSmallThreads / 32;
+  const int grid = (int)std::max<int64_t>(1, (n + rows_per_cta - 1) / rows_per_cta);
   {
     SNS_PROF(K_MATVEC, st);
-  small_matvec_kernel<<<grid, 256, 0, st>>>(M, v, n, out, out32, alpha, accum);
+  small_matvec_kernel<<<grid, kSmallThreads, 0, st>>>(M, v, n, out, out32, alpha, accum);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
 
+// One-CTA reductions for the O(n) CG and eta kernels: warp sums, then thread 0
+// adds the kSmallThreads / 32 partials (the FP64 pipe is narrow, so no thread
+// repeats work another has done).  Result valid in thread 0 only.
+SNS_D double small_sum0(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kSmallThreads / 32; ++w) t += red[w];
+  return t;
+}
+
 // CG on (R^-T A^T A R^-1) y = rhs.  init: y = 0, res = p = rhs, rr = |res|^2.
-__global__ void cg_init_kernel(const double* __restrict__ rhs, int64_t n, double* y, double* res, double* p,
-                               double* scal) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(kSmallThreads)
+cg_init_kernel(const double* __restrict__ rhs, int64_t n, double* y, double* res, double* p, double* scal) {
+  __shared__ double red[kSmallThreads / 32];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const double r = rhs[i];
@@ -617,19 +712,22 @@ __global__ void cg_init_kernel(const double* __restrict__ rhs, int64_t n, double
     p[i] = r;
     s = fma(r, r, s);
   }
-  s = block_sum(s, red);
+  s = small_sum0(s, red);
   if (threadIdx.x == 0) scal[kRR] = s;
 }
 // step: q = R^-T w (given in qv); alpha = rr / (p.q); y += alpha p;
 // res -= alpha q; rr' = |res|^2; p = res + (rr'/rr) p.
-__global__ void cg_step_kernel(int64_t n, const double* __restrict__ qv, double* y, double* res, double* p,
-                               double* scal) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(kSmallThreads)
+cg_step_kernel(int64_t n, const double* __restrict__ qv, double* y, double* res, double* p, double* scal) {
+  __shared__ double red[2][kSmallThreads / 32];
+  __shared__ double bc[2];
   double pq = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) pq = fma(p[i], qv[i], pq);
-  pq = block_sum(pq, red);
+  pq = small_sum0(pq, red[0]);
   const double rr = scal[kRR];
-  const double alpha = (pq > 0.0 && rr > 0.0) ? rr / pq : 0.0;
+  if (threadIdx.x == 0) bc[0] = (pq > 0.0 && rr > 0.0) ? rr / pq : 0.0;
+  __syncthreads();
+  const double alpha = bc[0];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     y[i] = fma(alpha, p[i], y[i]);
@@ -637,17 +735,20 @@ __global__ void cg_step_kernel(int64_t n, const double* __restrict__ qv, double*
     res[i] = r;
     s = fma(r, r, s);
   }
-  const double rr2 = block_sum(s, red);
-  const double beta = (rr > 0.0) ? rr2 / rr : 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = fma(beta, p[i], res[i]);
+  const double rr2 = small_sum0(s, red[1]);
+  if (threadIdx.x == 0) {
+    bc[1] = (rr > 0.0) ? rr2 / rr : 0.0;
+    scal[kRR] = rr2;      // every thread read the old value before the second barrier
+  }
   __syncthreads();
-  if (threadIdx.x == 0) scal[kRR] = rr2;
+  const double beta = bc[1];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = fma(beta, p[i], res[i]);
 }
 
 sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st) {
   {
     SNS_PROF(K_CG, st);
-  cg_init_kernel<<<1, 512, 0, st>>>(W.rhs, n, W.y, W.res, W.p, W.scal);
+  cg_init_kernel<<<1, kSmallThreads, 0, st>>>(W.rhs, n, W.y, W.res, W.p, W.scal);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -655,7 +756,7 @@ sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st) {
 sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st) {
   {
     SNS_PROF(K_CG, st);
-  cg_step_kernel<<<1, 512, 0, st>>>(n, W.qv, W.y, W.res, W.p, W.scal);
+  cg_step_kernel<<<1, kSmallThreads, 0, st>>>(n, W.qv, W.y, W.res, W.p, W.scal);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -663,11 +764,11 @@ sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st) {
 
 // eta = ||g|| / (||A||_F ||r||) after a resid_pass; copies
 // [eta, ||r||, ||g||, ||A||_F] to host_out (pinned) asynchronously.
-__global__ void eta_kernel(const double* __restrict__ g, int64_t n, double* scal) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(kSmallThreads) eta_kernel(const double* __restrict__ g, int64_t n, double* scal) {
+  __shared__ double red[kSmallThreads / 32];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(g[i], g[i], s);
-  s = block_sum(s, red);
+  s = small_sum0(s, red);
   if (threadIdx.x == 0) {
     const double rn = sqrt(scal[kRnorm2]);
     const double an = sqrt(scal[kAnorm2]);
@@ -684,7 +785,7 @@ __global__ void eta_kernel(const double* __restrict__ g, int64_t n, double* scal
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st) {
   {
     SNS_PROF(K_ETA, st);
-  eta_kernel<<<1, 512, 0, st>>>(W.g, n, W.scal);
+  eta_kernel<<<1, kSmallThreads, 0, st>>>(W.g, n, W.scal);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   SNS_CUDA_TRY(cudaMemcpyAsync(host_out, W.scal + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));

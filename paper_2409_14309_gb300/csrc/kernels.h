@@ -72,9 +72,11 @@ struct QrOut {
 };
 sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, int64_t q, double* W, cudaStream_t st);
 sns_status qr_solve_one(const QrOut& o, cudaStream_t st);
-// Multi-CTA factorisation of one large problem; ws holds qr_coop_ws_bytes(q)
-// bytes (tau values, flags, error word).  The error word is set if a wait gave up.
-size_t qr_coop_ws_bytes(int64_t q);
+// Multi-CTA factorisation of one large problem; ws holds qr_coop_ws_bytes(d, q)
+// bytes (published reflectors and scalars, error word).  The error word is set if a wait gave up.
+size_t qr_coop_ws_bytes(int64_t d, int64_t q);
+// Byte offset, within that workspace, of the int error word (nonzero: a wait timed out).
+size_t qr_coop_err_offset(int64_t d, int64_t q);
 sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st);
 sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st);
 sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
@@ -87,14 +89,17 @@ struct IterWs {
   float *xhi, *xlo, *z32;     // n
   float* part;                // partial n-vectors from passes [grid][n]
   double* partd;              // FP64 partials [grid][n + 4]
-  uint32_t* ticket;           // one counter
+  uint32_t* ticket;           // reduction tickets (group counters + top)
+  double* lvl2;               // level-2 partial rows
   int grid;
 };
 size_t iter_ws_bytes(int64_t n, int grid);
 IterWs iter_ws_carve(void* base, int64_t n, int grid);
 int iter_grid();
+// exact_g: exact FP32 products in g = A^T r (needed for eta targets below
+// about 1e-6; otherwise g's per-term FP32 rounding is negligible).
 sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, const IterWs& W, bool want_anorm,
-                      cudaStream_t st);
+                      bool exact_g, cudaStream_t st);
 sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, cudaStream_t st);
 sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
                         double* accum, cudaStream_t st);

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_one_kernel(QrOut o) {
 }
 
 sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
-  const size_t smem = (size_t)std::max<int64_t>(o.d, o.q) * 8;
+  const size_t smem = (size_t)std::max<int64_t>(o.d, 2 * o.q) * 8;
   SNS_CUDA_TRY(raise_smem_limit((const void*)qr_one_kernel));
   {
     SNS_PROF(K_QR, st);
@@ -77,7 +77,7 @@ sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
 }
 
 sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st) {
-  const size_t smem = (size_t)max_d * 8;
+  const size_t smem = (size_t)(2 * max_d + 2) * 8;     // factor: d doubles; finish: 2 q <= 2 d + 2
   SNS_CUDA_TRY(raise_smem_limit((const void*)qr_tasks_kernel));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_tasks_kernel, kQrThreads, smem));
@@ -92,153 +92,343 @@ sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cud
 
 // ---------------------------------------------------------------------------
 // Multi-CTA Householder QR for one large problem (cooperative launch, all CTAs
-// resident).  Column c belongs to CTA c mod G.  Reflector j is published by the
-// owner of column j: v_j overwrites W[j+1:, j] (v_j[0] = 1 implicit), tau_j and
-// alpha_j = R[j, j] are stored, then flag[j] is raised.  Every CTA applies the
-// reflectors in order to the columns it owns.  Look-ahead: the owner of column
-// j+1 updates that column with reflector j first and publishes reflector j+1
-// before it updates its other columns, so the serial chain per column is one
-// column update plus one reflector construction.  Waits are bounded: after
-// kSpinLimit polls a CTA records an error and returns.
-constexpr long long kSpinLimit = 1LL << 24;
+// resident).  Column c belongs to CTA c mod G and, when the owned columns fit,
+// lives in that CTA's shared memory for the whole factorisation.
+//
+// Reflector j is published unscaled: u_j = x - alpha e_0 over rows j..d-1
+// (u_j[0] = x_0 - alpha = v_0), H_j = I - beta_j u_j u_j^T with
+// beta_j = tau_j / v_0^2 = -1 / (alpha v_0), which is the same H as the
+// (v_0 = 1, tau) form without the scaling pass.  Rows j+1.. of u_j go to
+// U[j, j+1:] and (beta_j, v_0) to pub[j].
+//
+// Hand-off without flags: U and pub are filled with an all-ones bit pattern
+// (a NaN that no arithmetic produces; a computed value with that pattern is
+// published as the canonical NaN) before the launch, and every consumer thread
+// polls exactly the values it needs until they differ from it.  Each value
+// validates itself, so the producer needs no fence and the consumer no flag
+// round trip: one L2 trip per hand-off.
+//
+// GB300's FP64 pipe issues about half a lane per clock per SM sub-partition,
+// so the kernel keeps FP64 instructions off the serial chain: 128 threads (one
+// warp per sub-partition), a fixed row-to-thread map so a thread uses only the
+// reflector rows it loaded itself, scalar work (sqrt, divide) on one thread,
+// and one batched reduction per step for the non-critical columns.
+// Look-ahead: the owner of column j+1 updates it with reflector j, builds and
+// publishes reflector j+1, and only then updates its other columns.  Waits
+// are bounded: after kSpinLimit polls a thread records an error and carries on
+// with zeros; later waits see the error word and stop polling, so a failed
+// factorisation ends quickly and the host reports it.
+constexpr long long kSpinLimit = 1LL << 22;
+constexpr int kCoopThreads = 128;
+constexpr int kCoopWarps = kCoopThreads / 32;
+constexpr int kCoopBatch = 8;                 // non-critical columns per batched reduction
+constexpr long long kSentinel = -1LL;         // all-ones bit pattern: "not yet published"
 
-// Block-wide dot of v (shared, rows j..d-1) with column cc (global).
-SNS_D double block_dot_col(const double* v, const double* cc, int64_t j, int64_t d, double* red) {
-  double s = 0.0;
-  for (int64_t i = j + threadIdx.x; i < d; i += blockDim.x) s = fma(v[i], cc[i], s);
-  return block_sum(s, red);
+SNS_D double ld_relaxed(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+SNS_D int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+SNS_D void st_relaxed(double* p, double v) {
+  if (__double_as_longlong(v) == kSentinel) v = __longlong_as_double(0x7FF8000000000000LL);
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
-// Builds reflector j from column j (already updated by reflectors < j):
-// scales W[j+1:, j] by 1/v0 in place, stores alpha in W[j, j] and tau in taus[j].
-SNS_D void build_reflector(double* W, int64_t d, int64_t j, double* taus, double* red) {
-  double* cj = W + j * d;
-  double part = 0.0;
-  for (int64_t i = j + threadIdx.x; i < d; i += blockDim.x) part = fma(cj[i], cj[i], part);
-  const double nrm2 = block_sum(part, red);
-  const double x0 = cj[j];
-  const double normx = sqrt(nrm2);
-  double alpha = x0, tau = 0.0, inv_v0 = 0.0;
-  if (normx > 0.0) {
-    alpha = (x0 >= 0.0) ? -normx : normx;
-    const double v0 = x0 - alpha;
-    tau = -v0 / alpha;
-    inv_v0 = 1.0 / v0;
+// Polls up to kSlots addresses (null = unused) until none holds the sentinel;
+// bounded as described above.
+template <int kSlots>
+SNS_D void coop_poll(const double* const (&addr)[kSlots], double (&val)[kSlots], int* err) {
+  bool got[kSlots];
+#pragma unroll
+  for (int u = 0; u < kSlots; ++u) got[u] = (addr[u] == nullptr);
+  for (long long it = 0;; ++it) {
+    bool all = true;
+#pragma unroll
+    for (int u = 0; u < kSlots; ++u)
+      if (!got[u]) {
+        val[u] = ld_relaxed(addr[u]);
+        got[u] = __double_as_longlong(val[u]) != kSentinel;
+        all = all && got[u];
+      }
+    if (all) return;
+    const bool give_up = it >= kSpinLimit;
+    if (give_up || ((it & 255) == 255 && ld_relaxed_int(err) != 0)) {
+      if (give_up) atomicExch(err, 1);
+#pragma unroll
+      for (int u = 0; u < kSlots; ++u)
+        if (!got[u]) val[u] = 0.0;
+      return;
+    }
+    if (it >= 4096) __nanosleep(32);
   }
-  for (int64_t i = j + 1 + threadIdx.x; i < d; i += blockDim.x) cj[i] *= inv_v0;
+}
+
+// Sum over the CTA of one value per thread; thread 0 receives the total
+// (other threads receive garbage).  Two reductions in a row are safe: thread 0
+// reads red[] before the barrier that the next writers must pass.
+SNS_D double coop_sum0(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
+  double t = 0.0;
   if (threadIdx.x == 0) {
-    cj[j] = alpha;
-    taus[j] = tau;
+#pragma unroll
+    for (int w = 0; w < kCoopWarps; ++w) t += red[w];
+  }
+  return t;
+}
+
+// Same sum, every thread receives it (one barrier; each thread adds the
+// kCoopWarps partials in the same order).
+SNS_D double coop_sum_all(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kCoopWarps; ++w) t += red[w];
+  return t;
+}
+
+// First row >= j of this thread's fixed residue class (rows i = tid mod T).
+SNS_D int64_t coop_first_row(int64_t j) {
+  return j + (int64_t)((threadIdx.x - (int)(j % kCoopThreads) + kCoopThreads) % kCoopThreads);
+}
+
+// Applies reflector j (rows j.., this thread's rows of vsm; scale beta) to CNT
+// owned columns c0, c0 + cstride, ...: one batched CTA reduction for all dots.
+template <int CNT>
+SNS_D void coop_batch(double* c0, int64_t cstride, int64_t d, int64_t j, double beta, const double* vsm,
+                      double (*red)[kCoopWarps], double* bcast) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double part[CNT];
+#pragma unroll
+  for (int t = 0; t < CNT; ++t) part[t] = 0.0;
+  for (int64_t i = coop_first_row(j); i < d; i += kCoopThreads) {
+    const double vi = vsm[i];
+#pragma unroll
+    for (int t = 0; t < CNT; ++t) part[t] = fma(vi, c0[t * cstride + i], part[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < CNT; ++t) {
+    const double ws = warp_sum(part[t]);
+    if (lane == 0) red[t][wid] = ws;
+  }
+  __syncthreads();
+  if (tid < CNT) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCoopWarps; ++w) s += red[tid][w];
+    bcast[tid] = beta * s;
+  }
+  __syncthreads();
+  double f[CNT];
+#pragma unroll
+  for (int t = 0; t < CNT; ++t) f[t] = bcast[t];
+  for (int64_t i = coop_first_row(j); i < d; i += kCoopThreads) {
+    const double vi = vsm[i];
+#pragma unroll
+    for (int t = 0; t < CNT; ++t) c0[t * cstride + i] = fma(-f[t], vi, c0[t * cstride + i]);
   }
 }
 
-SNS_D void publish(int* flag) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicExch(flag, 1);
-}
-
-// Returns false (and records the error) if the flag never came.
-SNS_D bool wait_flag(int* flag, int* err) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    const bool got = spin_until_ge(reinterpret_cast<volatile int*>(flag), 1, kSpinLimit);
-    if (!got) atomicExch(err, 1);
-    __threadfence();
-    ok = got ? 1 : 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__global__ void __launch_bounds__(kQrThreads)
-qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ taus, int* __restrict__ flags,
+template <bool kSmemCols>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ U, double* __restrict__ pub,
                int* __restrict__ err) {
-  extern __shared__ double vsm[];   // reflector rows j..d-1
-  __shared__ double red[32];
+  extern __shared__ __align__(16) double qsm[];
+  double* vsm = qsm;                                   // reflector rows (fixed row map)
+  double* csm = qsm + d;                               // owned columns (kSmemCols)
+  __shared__ double red[kCoopBatch][kCoopWarps];     // batched reductions
+  __shared__ double redc[2][kCoopWarps];             // the critical column's two reductions
+  __shared__ double bcast[kCoopBatch + 4];
+  const int tid = threadIdx.x;
   const int64_t G = gridDim.x, b = blockIdx.x;
   const int64_t steps = q < d ? q : d;
-  // reflector 0: built by the owner of column 0 before the loop
-  if (b == 0) {
-    build_reflector(W, d, 0, taus, red);
-    publish(flags + 0);
+  if (b >= q) return;
+  const int64_t nown = (q - 1 - b) / G + 1;
+  const int64_t clast = b + (nown - 1) * G;
+  auto col = [&](int64_t k) -> double* { return kSmemCols ? csm + k * d : W + (b + k * G) * d; };
+  const int64_t cstride = kSmemCols ? d : G * d;       // distance between consecutive owned columns
+  if (kSmemCols) {
+    for (int64_t k = 0; k < nown; ++k) {
+      const double* src = W + (b + k * G) * d;
+      for (int64_t i = tid; i < d; i += kCoopThreads) csm[k * d + i] = src[i];
+    }
+    __syncthreads();
   }
-  for (int64_t j = 0; j < steps; ++j) {
-    if (b != j % G) {
-      if (!wait_flag(flags + j, err)) return;
-    }
-    // load v_j and tau_j (through L2: written by another SM)
-    const double* cj = W + j * d;
-    for (int64_t i = j + threadIdx.x; i < d; i += blockDim.x) vsm[i] = (i == j) ? 1.0 : __ldcg(cj + i);
-    __syncthreads();
-    const double tau = __ldcg(taus + j);
-    // look-ahead column j+1
+
+  // Update column cc with reflector j (rows >= j; f = beta * u^T c), then
+  // build reflector c1 = j + 1 from it and publish.  With j < 0 the column is
+  // only reflected (column 0).
+  auto critical = [&](double* cc, int64_t j, double beta) {
     const int64_t c1 = j + 1;
-    if (c1 < q && c1 % G == b) {
-      double* cc = W + c1 * d;
-      if (tau != 0.0) {
-        const double f = tau * block_dot_col(vsm, cc, j, d, red);
-        for (int64_t i = j + threadIdx.x; i < d; i += blockDim.x) cc[i] = fma(-f, vsm[i], cc[i]);
-        __syncthreads();
+    double f = 0.0;
+    if (j >= 0 && beta != 0.0) {
+      double part = 0.0;
+      for (int64_t i = coop_first_row(j); i < d; i += kCoopThreads) part = fma(vsm[i], cc[i], part);
+      f = beta * coop_sum_all(part, redc[0]);
+    }
+    const bool publish = c1 < steps;
+    double* ucol = U + c1 * d;                         // published rows c1+1..
+    double nrm = 0.0;
+    const int64_t i0 = coop_first_row(j >= 0 ? j : 0);
+    for (int64_t i = i0; i < d; i += kCoopThreads) {
+      double c = cc[i];
+      if (f != 0.0) {
+        c = fma(-f, vsm[i], c);
+        cc[i] = c;
       }
-      if (c1 < steps) {
-        build_reflector(W, d, c1, taus, red);
-        publish(flags + c1);
+      if (i >= c1) nrm = fma(c, c, nrm);
+      if (publish && i > c1) st_relaxed(ucol + i, c);
+    }
+    if (!publish) return;                              // no reflector for this column
+    const double nrm2 = coop_sum0(nrm, redc[1]);
+    if (tid == 0) {
+      const double x0 = cc[c1];
+      const double normx = sqrt(nrm2);
+      double alpha = x0, v0 = 0.0, bt = 0.0;
+      if (normx > 0.0) {
+        alpha = (x0 >= 0.0) ? -normx : normx;
+        v0 = x0 - alpha;
+        bt = -1.0 / (alpha * v0);
+      }
+      cc[c1] = alpha;
+      bcast[kCoopBatch + 1] = bt;
+      bcast[kCoopBatch + 2] = v0;
+      st_relaxed(pub + 2 * c1, bt);
+      st_relaxed(pub + 2 * c1 + 1, v0);
+    }
+  };
+
+  if (b == 0) critical(col(0), -1, 0.0);
+  const int64_t jend = clast < steps ? clast : steps;
+  for (int64_t j = 0; j < jend; ++j) {
+    const bool mine = (j % G) == b;
+    __syncthreads();                                   // previous step done; owner's bcast visible
+    // reflector j into this thread's rows of vsm
+    double beta, v0 = 0.0;
+    const bool row_j = coop_first_row(j) == j;         // this thread holds row j (u_j[0] = v_0)
+    if (mine) {
+      beta = bcast[kCoopBatch + 1];
+      v0 = bcast[kCoopBatch + 2];
+      const double* cj = col((j - b) / G);
+      for (int64_t i = coop_first_row(j + 1); i < d; i += kCoopThreads) vsm[i] = cj[i];
+    } else {
+      const double* uj = U + j * d;
+      int64_t i = coop_first_row(j + 1);
+      {   // first 8 rows together with beta and v_0
+        const double* ad[10];
+        double vv[10];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ad[u] = (i + u * kCoopThreads < d) ? uj + i + u * kCoopThreads : nullptr;
+        ad[8] = pub + 2 * j;
+        ad[9] = row_j ? pub + 2 * j + 1 : nullptr;
+        coop_poll<10>(ad, vv, err);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (ad[u]) vsm[i + u * kCoopThreads] = vv[u];
+        beta = vv[8];
+        if (row_j) v0 = vv[9];
+        i += 8 * kCoopThreads;
+      }
+      for (; i < d; i += 8 * kCoopThreads) {
+        const double* ad[8];
+        double vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ad[u] = (i + u * kCoopThreads < d) ? uj + i + u * kCoopThreads : nullptr;
+        coop_poll<8>(ad, vv, err);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (ad[u]) vsm[i + u * kCoopThreads] = vv[u];
       }
     }
-    // remaining owned columns
-    if (tau != 0.0) {
-      int64_t c = c1 + 1;
-      c += ((b - c) % G + G) % G;               // first owned column > j + 1
-      for (; c < q; c += G) {
-        double* cc = W + c * d;
-        const double f = tau * block_dot_col(vsm, cc, j, d, red);
-        for (int64_t i = j + threadIdx.x; i < d; i += blockDim.x) cc[i] = fma(-f, vsm[i], cc[i]);
+    if (row_j) vsm[j] = v0;
+    // look-ahead column j + 1
+    const int64_t c1 = j + 1;
+    if (c1 % G == b) critical(col((c1 - b) / G), j, beta);
+    if (beta == 0.0) continue;
+    // other owned columns > j + 1, up to kCoopBatch per batched reduction
+    int64_t k0 = (c1 + 1 - b + G - 1) / G;               // first owned index with column > j + 1
+    if (c1 + 1 <= b) k0 = 0;
+    for (; k0 < nown; k0 += kCoopBatch) {
+      const int cnt = (int)((nown - k0) < kCoopBatch ? (nown - k0) : kCoopBatch);
+      switch (cnt) {   // compile-time column counts: no predicated-off FP64 instructions
+        case 1: coop_batch<1>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 2: coop_batch<2>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 3: coop_batch<3>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 4: coop_batch<4>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 5: coop_batch<5>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 6: coop_batch<6>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        case 7: coop_batch<7>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
+        default: coop_batch<8>(col(k0), cstride, d, j, beta, vsm, red, bcast); break;
       }
     }
+  }
+  if (kSmemCols) {
     __syncthreads();
+    for (int64_t k = 0; k < nown; ++k) {
+      double* dst = W + (b + k * G) * d;
+      for (int64_t i = tid; i < d; i += kCoopThreads) dst[i] = csm[k * d + i];
+    }
   }
 }
 
 // Rank check + back substitution of a factorised problem on one CTA.
-__global__ void __launch_bounds__(kQrThreads) qr_finish_kernel(QrOut o) {
-  extern __shared__ double zsm[];
+constexpr int kFinishThreads = 128;
+constexpr int kTriRing = 8;
+__global__ void __launch_bounds__(kFinishThreads) qr_finish_kernel(QrOut o) {
+  extern __shared__ __align__(16) double zsm[];
   __shared__ double red[32];
-  qr_finish_cta(o.W, o.d, o.q, o.x, o.status, o.sres, zsm, red);
+  qr_finish_cta<kTriRing>(o.W, o.d, o.q, o.x, o.status, o.sres, zsm, red);
 }
 
-int qr_coop_grid(int64_t q) {
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_coop_kernel, kQrThreads, 0);
-  const int64_t cap = (int64_t)num_sms() * std::max(occ, 1);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(q, cap), num_sms()));
-}
+static int qr_coop_grid(int64_t q) { return (int)std::max<int64_t>(1, std::min<int64_t>(q, num_sms())); }
 
-size_t qr_coop_ws_bytes(int64_t q) { return (size_t)q * 8 + (size_t)q * 4 + 256 + 64; }
+// Workspace: U (q x d doubles) | pub (2 q doubles) | err (int).  U and pub are
+// set to the sentinel and err to 0 by one memset each per factorisation.
+static size_t qr_coop_sent_bytes(int64_t d, int64_t q) { return (size_t)q * d * 8 + (size_t)q * 16; }
+size_t qr_coop_ws_bytes(int64_t d, int64_t q) { return ((qr_coop_sent_bytes(d, q) + 255) & ~(size_t)255) + 256; }
+size_t qr_coop_err_offset(int64_t d, int64_t q) { return (qr_coop_sent_bytes(d, q) + 255) & ~(size_t)255; }
 
 sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
   uint8_t* w = static_cast<uint8_t*>(ws);
-  double* taus = reinterpret_cast<double*>(w);
-  int* flags = reinterpret_cast<int*>(w + (((size_t)o.q * 8 + 255) & ~(size_t)255));
-  int* err = flags + o.q;
-  SNS_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)o.q * 4 + 4, st));
-  const size_t smem = (size_t)o.d * 8;
-  SNS_CUDA_TRY(raise_smem_limit((const void*)qr_coop_kernel));
+  double* U = reinterpret_cast<double*>(w);
+  double* pub = U + (size_t)o.q * o.d;
+  int* err = reinterpret_cast<int*>(w + qr_coop_err_offset(o.d, o.q));
+  SNS_CUDA_TRY(cudaMemsetAsync(U, 0xFF, qr_coop_sent_bytes(o.d, o.q), st));
+  SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
   const int grid = qr_coop_grid(o.q);
+  const int64_t own = (o.q + grid - 1) / grid;
+  int dev = 0, smem_max = 0;
+  SNS_CUDA_TRY(cudaGetDevice(&dev));
+  SNS_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t static_smem = 2048;                     // red, bcast, flag word (upper bound)
+  const size_t smem_cols = (size_t)(1 + own) * o.d * 8;
+  const bool in_smem = smem_cols + static_smem <= (size_t)smem_max;
+  const size_t smem = in_smem ? smem_cols : (size_t)o.d * 8;
+  const void* fn = in_smem ? (const void*)qr_coop_kernel<true> : (const void*)qr_coop_kernel<false>;
+  SNS_CUDA_TRY(raise_smem_limit(fn));
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kCoopThreads, smem));
+  if (occ < 1) return SNS_EINVAL;
   double* W = o.W;
   int64_t d = o.d, q = o.q;
-  void* args[] = {&W, &d, &q, &taus, &flags, &err};
+  void* args[] = {&W, &d, &q, &U, &pub, &err};
   {
     SNS_PROF(K_QR, st);
-    SNS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(grid), dim3(kQrThreads), args, smem,
-                                             st));
+    SNS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, smem, st));
   }
-  const size_t zs = (size_t)std::max<int64_t>(o.q, 1) * 8;
+  const size_t zs = (size_t)std::max<int64_t>(o.q, 1) * 8 * (2 + kTriRing);
   SNS_CUDA_TRY(raise_smem_limit((const void*)qr_finish_kernel));
   {
     SNS_PROF(K_QR, st);
-    qr_finish_kernel<<<1, kQrThreads, zs, st>>>(o);
+    qr_finish_kernel<<<1, kFinishThreads, zs, st>>>(o);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -246,33 +436,37 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
 
 // Explicit R^{-1} (upper triangular, FP64) for the preconditioner applications
 // of the iterative phase.  One CTA per column j solves R y = e_j by
-// column-oriented back substitution with the running column in shared memory:
-// at step k every thread reads y_k = y[k] / R[k, k] (final, since step k only
-// updates rows i < k), the owner of row k records it, and all threads update
-// their rows i < k; one barrier per step.  Writes Rinv (row-major) and its
+// column-oriented back substitution (tri_backsolve_cta: reciprocal diagonal,
+// one barrier per step, R's columns streamed ahead through a cp.async ring);
+// the longest columns are scheduled first.  Writes Rinv (row-major) and its
 // transpose RinvT (row-major).  With `identity`, writes the identity
 // (unpreconditioned iteration).
-__global__ void __launch_bounds__(256) rinv_kernel(const double* __restrict__ W, int64_t ldw, int64_t n,
-                                                   double* __restrict__ Rinv, double* __restrict__ RinvT,
-                                                   int identity) {
-  extern __shared__ double ycol[];   // n
-  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+constexpr int kRinvThreads = 128;
+__global__ void __launch_bounds__(kRinvThreads) rinv_kernel(const double* __restrict__ W, int64_t ldw, int64_t n,
+                                                            double* __restrict__ Rinv, double* __restrict__ RinvT,
+                                                            int identity) {
+  extern __shared__ __align__(16) double rsm[];
+  double* ycol = rsm;                 // n
+  double* rd = rsm + n;               // n: 1 / R[k, k]
+  double* ring = rsm + 2 * n;         // kTriRing columns
+  if (!identity)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) rd[i] = 1.0 / W[i * ldw + i];
+  for (int64_t jj = blockIdx.x; jj < n; jj += gridDim.x) {
+    const int64_t j = n - 1 - jj;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ycol[i] = (i == j) ? 1.0 : 0.0;
     __syncthreads();
     if (!identity) {
-      for (int64_t k = j; k >= 0; --k) {
-        const double yk = ycol[k] / W[k * ldw + k];
-        const double* rk = W + k * ldw;          // column k of R: rows 0..k
-        __syncthreads();                         // everyone has read y[k]
-        if (threadIdx.x == 0) ycol[k] = yk;
-        for (int64_t i = threadIdx.x; i < k; i += blockDim.x) ycol[i] = fma(-rk[i], yk, ycol[i]);
-        __syncthreads();
-      }
+      tri_backsolve_cta<kTriRing>(W, ldw, j, ycol, rd, ring, n, [&](int64_t k, double yk) {
+        Rinv[k * n + j] = yk;
+        RinvT[j * n + k] = yk;
+      });
     }
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const double v = (i <= j) ? ycol[i] : 0.0;
-      Rinv[i * n + j] = v;
-      RinvT[j * n + i] = v;
+      if (identity || i > j) {
+        const double v = (i == j) ? 1.0 : 0.0;
+        Rinv[i * n + j] = v;
+        RinvT[j * n + i] = v;
+      }
     }
     __syncthreads();
   }
@@ -280,12 +474,12 @@ __global__ void __launch_bounds__(256) rinv_kernel(const double* __restrict__ W,
 
 sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
                       cudaStream_t st) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms() * 4));
-  const size_t smem = (size_t)n * 8;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, 4096));
+  const size_t smem = (size_t)n * 8 * (2 + kTriRing);
   SNS_CUDA_TRY(raise_smem_limit((const void*)rinv_kernel));
   {
     SNS_PROF(K_RINV, st);
-    rinv_kernel<<<grid, 256, smem, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
+    rinv_kernel<<<grid, kRinvThreads, smem, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;

@@ -46,10 +46,66 @@ SNS_D void qr_factor_cta(double* __restrict__ W, int64_t d, int64_t q, double* v
   }
 }
 
-// Rank check and back substitution x = R^{-1} z, column-oriented: after x_k is
-// known, z[0:k] -= R[0:k, k] x_k.  z lives in shared memory.
+// Copies 8 bytes global -> shared without staging through registers
+// (cp.async; completion per thread via commit/wait groups).
+SNS_D void cp_async8(double* dst_smem, const double* src) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(src) : "memory");
+}
+SNS_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+SNS_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Column-oriented back substitution on one CTA: solves R y = y0 in place for
+// rows 0..kend of y (shared memory), where R is upper triangular, column k at
+// W + k * ldw, and rd[k] = 1 / R[k, k].  Step k: y_k = y[k] * rd[k] (final,
+// since step k writes only rows i < k), then y[i] -= R[i, k] y_k for i < k.
+// Each thread owns the rows i = tid (mod blockDim.x), so one barrier per step
+// suffices (row k - 1 is read by all only after it).  With RING > 0 the thread
+// streams its rows of columns k-1, k-2, ... into a shared-memory ring of RING
+// columns (ldr doubles apart) with cp.async, RING - 1 columns ahead, so the
+// serial chain never waits on L2.  emit(k, y_k) is called by thread 0.
+template <int RING, typename Emit>
+SNS_D void tri_backsolve_cta(const double* __restrict__ W, int64_t ldw, int64_t kend, double* y, const double* rd,
+                             double* ring, int64_t ldr, Emit emit) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if constexpr (RING > 0) {
+    auto issue = [&](int64_t k) {
+      if (k >= 0) {
+        const double* rk = W + k * ldw;
+        double* slot = ring + (k % RING) * ldr;
+        for (int64_t i = tid; i < k; i += nt) cp_async8(slot + i, rk + i);
+      }
+      cp_async_commit();
+    };
+    for (int p = 0; p < RING - 1; ++p) issue(kend - p);
+    for (int64_t k = kend; k >= 0; --k) {
+      issue(k - (RING - 1));
+      cp_async_wait<RING - 1>();
+      const double yk = y[k] * rd[k];
+      if (tid == 0) emit(k, yk);
+      const double* slot = ring + (k % RING) * ldr;
+      for (int64_t i = tid; i < k; i += nt) y[i] = fma(-slot[i], yk, y[i]);
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+  } else {
+    for (int64_t k = kend; k >= 0; --k) {
+      const double yk = y[k] * rd[k];
+      if (tid == 0) emit(k, yk);
+      const double* rk = W + k * ldw;
+      for (int64_t i = tid; i < k; i += nt) y[i] = fma(-rk[i], yk, y[i]);
+      __syncthreads();
+    }
+  }
+}
+
+// Rank check and back substitution x = R^{-1} z.  Shared memory `sm` holds
+// 2 (q - 1) doubles (z, then the reciprocals of R's diagonal) plus, with
+// RING > 0, RING * (q - 1) doubles for the column ring.
+template <int RING = 0>
 SNS_D void qr_finish_cta(const double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ x,
-                         int32_t* status, double* sres, double* z, double* red) {
+                         int32_t* status, double* sres, double* sm, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t n = q - 1;
   double mx = 0.0;
@@ -70,19 +126,15 @@ SNS_D void qr_finish_cta(const double* __restrict__ W, int64_t d, int64_t q, dou
     if (sres) *sres = (n < d) ? fabs(W[n * d + n]) : 0.0;
   }
   if (!x) return;
-  for (int64_t i = tid; i < n; i += nt) z[i] = W[n * d + i];
-  __syncthreads();
-  for (int64_t k = n - 1; k >= 0; --k) {
-    const double xk = z[k] / W[k * d + k];
-    __syncthreads();
-    if (tid == 0) {
-      z[k] = xk;
-      x[k] = (bad || gmax == 0.0) ? 0.0 : xk;
-    }
-    for (int64_t i = tid; i < k; i += nt) z[i] = fma(-W[k * d + i], xk, z[i]);
-    __syncthreads();
+  const bool zero = bad || gmax == 0.0;
+  double* z = sm;
+  double* rd = sm + n;
+  for (int64_t i = tid; i < n; i += nt) {
+    z[i] = W[n * d + i];
+    rd[i] = 1.0 / W[i * d + i];
   }
+  __syncthreads();
+  tri_backsolve_cta<RING>(W, d, n - 1, z, rd, sm + 2 * n, n, [&](int64_t k, double xk) { x[k] = zero ? 0.0 : xk; });
 }
-
 
 }  // namespace sns
