@@ -111,7 +111,11 @@ typedef struct {
   sns_sketch_desc sk;
   double tol;
   int32_t max_iter;        /* cap on inner passes over A (0 = library default 400) */
-  int32_t inner;           /* inner CG steps per refinement step (0 = default) */
+  int32_t inner;           /* most inner CG steps per refinement step (0 = default 8); a step
+                              ends earlier, on the device, once the preconditioned CG residual
+                              has dropped by max(tol / (2 eta), 4e-3), eta the current backward
+                              error (Sec. 1.2 sketch-and-precondition; the per-step floor reflects
+                              the FP32 passes) */
   int32_t precondition;    /* 1 = R from QR(SA) (default when nonzero); 0 = R = I
                               (unpreconditioned reference iteration) */
   int32_t reserved;

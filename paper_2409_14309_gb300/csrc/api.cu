@@ -34,6 +34,9 @@ static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 // of the residual pass (FP32 products, compensated sums): its eta floor is at
 // most ~3e-8, so eta is still resolved to a few percent at 1e-6.
 constexpr double kCheapGradTol = 1e-6;
+// Upper bound on inner CG steps per refinement cycle when the caller sets none;
+// cycles normally end earlier, on the device.
+constexpr int kDefaultInnerMax = 8;
 
 cudaError_t raise_smem_limit(const void* func) {
   static std::mutex mu;
@@ -386,6 +389,8 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   SNS_CUDA_TRY(cudaStreamWaitEvent(side.st, side.ev_in, 0));
   s = rinv_build(W, d, n, I.Rinv, I.RinvT, !precond, side.st);
   if (s != SNS_OK) return s;
+  s = pgram_build(I.Rinv, n, I.P, side.st);
+  if (s != SNS_OK) return s;
   SNS_CUDA_TRY(cudaEventRecord(side.ev_out, side.st));
   bool rinv_joined = false;
   DenseArgs da{prob->A, prob->lda, prob->b, prob->m, n, f64};
@@ -393,9 +398,11 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   const DenseArgs* dap = prob->fmt == SNS_CSR_F32 ? nullptr : &da;
   const CsrArgs* cap = prob->fmt == SNS_CSR_F32 ? &ca : nullptr;
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 400;
-  const int inner = opts->inner > 0 ? opts->inner : 6;
+  const int inner = opts->inner > 0 ? opts->inner : kDefaultInnerMax;
   int passes = 0, outer = 0;
   double eta = 0.0, rn = 0.0;
+  s = iter_reset(I, st);
+  if (s != SNS_OK) return s;
   for (;;) {
     s = resid_pass(dap, cap, x, I, outer == 0, opts->tol < kCheapGradTol, st);
     if (s != SNS_OK) return s;
@@ -405,28 +412,27 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     ++outer;
     eta = hp[0];
     rn = hp[1];
+    passes = (int)hp[4];                 // normal passes the cycles actually ran
     if (!(eta > opts->tol)) break;       // converged (also stops on eta == 0)
     if (passes >= max_iter) {
       if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
       info_fill(info, SNS_ENOTCONV, passes, outer, eta, rn, sres);
       return SNS_ENOTCONV;
     }
-    // inner CG on the preconditioned normal equations
+    // inner solver: preconditioned CG on A^T A dx = g (M^-1 = R^-1 R^-T); the
+    // cycle stops itself on the device, later launches of the budget return at once
     if (!rinv_joined) {
       SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
       rinv_joined = true;
     }
-    s = small_matvec(I.RinvT, I.g, n, I.rhs, nullptr, 0.0, nullptr, st);
+    s = pcg_start(I, n, opts->tol, st);
     if (s != SNS_OK) return s;
-    s = cg_init(I, n, st);
-    if (s != SNS_OK) return s;
-    for (int k = 0; k < inner && passes < max_iter; ++k, ++passes) {
-      if ((s = small_matvec(I.Rinv, I.p, n, I.z, I.z32, 0.0, nullptr, st)) != SNS_OK) return s;
+    const int budget = std::min(inner, max_iter - passes);
+    for (int k = 0; k < budget; ++k) {
       if ((s = normal_pass(dap, cap, I, st)) != SNS_OK) return s;
-      if ((s = small_matvec(I.RinvT, I.w, n, I.qv, nullptr, 0.0, nullptr, st)) != SNS_OK) return s;
-      if ((s = cg_step(I, n, st)) != SNS_OK) return s;
+      if ((s = pcg_step(I, n, st)) != SNS_OK) return s;
     }
-    s = small_matvec(I.Rinv, I.y, n, nullptr, nullptr, 1.0, x, st);
+    s = pcg_apply(I, n, x, st);
     if (s != SNS_OK) return s;
   }
   if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));

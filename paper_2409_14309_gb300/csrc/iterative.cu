@@ -41,8 +41,8 @@ static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t iter_ws_bytes(int64_t n, int grid) {
   size_t s = 0;
-  s += 2 * al256((size_t)n * n * 8);          // Rinv, RinvT
-  s += 9 * al256((size_t)n * 8);              // g w rhs y res p qv z
+  s += 3 * al256((size_t)n * n * 8);          // Rinv, RinvT, P
+  s += 6 * al256((size_t)n * 8);              // g w z rx s dx
   s += al256(64 * 8);                         // scal
   s += 3 * al256((size_t)n * 4);              // xhi xlo z32
   s += al256((size_t)grid * n * 4);           // part
@@ -58,15 +58,13 @@ IterWs iter_ws_carve(void* base, int64_t n, int grid) {
   auto take = [&](size_t b) { uint8_t* r = p; p += al256(b); return r; };
   W.Rinv = (double*)take((size_t)n * n * 8);
   W.RinvT = (double*)take((size_t)n * n * 8);
+  W.P = (double*)take((size_t)n * n * 8);
   W.g = (double*)take(n * 8);
   W.w = (double*)take(n * 8);
-  W.rhs = (double*)take(n * 8);
-  W.y = (double*)take(n * 8);
-  W.res = (double*)take(n * 8);
-  W.p = (double*)take(n * 8);
-  W.qv = (double*)take(n * 8);
   W.z = (double*)take(n * 8);
-  (void)take(n * 8);
+  W.rx = (double*)take(n * 8);
+  W.s = (double*)take(n * 8);
+  W.dx = (double*)take(n * 8);
   W.scal = (double*)take(64 * 8);
   W.xhi = (float*)take(n * 4);
   W.xlo = (float*)take(n * 4);
@@ -81,15 +79,28 @@ IterWs iter_ws_carve(void* base, int64_t n, int grid) {
 
 // Scalar slots in W.scal.
 enum { kRR = 0, kRnorm2 = 1, kAnorm2 = 2, kEta = 3, kGnorm2 = 4, kRnorm = 5, kPQ = 6 };
+// Inner-loop control (device-side, so the host never waits inside a cycle):
+// kStop2 = the CG residual^2 at which the cycle ends, kDone = nonzero once it
+// has (later launches of the cycle return at once), kPasses = normal passes run.
+enum { kStop2 = 16, kDone = 17, kPasses = 18 };
+// Slots 8..12 are copied to the host after each residual pass:
+// eta, ||r||, ||g||, ||A||_F, passes run.
+constexpr int kHostSlots = 5;
+// Per-cycle floor of the CG residual reduction: the FP32 passes (z = R^-1 p
+// rounded to FP32 and A z in FP32) limit what one refinement cycle can gain,
+// and iterating past that only repeats work the next cycle redoes.
+constexpr double kInnerFloor = 4e-3;
 
 // Deterministic two-level reduction of per-CTA partial rows.  CTA b has
 // written its row part[b * stride + c], c < nc.  CTAs form groups of 32; the
 // last CTA of a group (ticket) adds the group's rows in CTA order (FP64) into
 // lvl2[group]; the last group to finish adds the group sums in group order and
 // calls emit(c, value).  Tickets are reset by the CTAs that consume them.
+// Returns true in the one CTA that emitted (after a barrier, so its emitted
+// values are visible to all its threads).
 constexpr int kRedGroup = 32;
 template <typename PT, typename F>
-SNS_D void tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, uint32_t* __restrict__ tickets,
+SNS_D bool tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, uint32_t* __restrict__ tickets,
                        double* __restrict__ lvl2, F&& emit) {
   __shared__ int s_last;
   const int64_t G = gridDim.x;
@@ -100,7 +111,7 @@ SNS_D void tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, 
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(tickets + grp, 1u) == (uint32_t)(gsize - 1));
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
     double acc = 0.0;
@@ -114,7 +125,7 @@ SNS_D void tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, 
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(tickets + ngroups, 1u) == (uint32_t)(ngroups - 1));
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
     double acc = 0.0;
@@ -123,7 +134,60 @@ SNS_D void tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, 
     emit(c, acc);
   }
   if (threadIdx.x == 0) tickets[ngroups] = 0;
+  __syncthreads();
+  return true;
 }
+
+// Vectors of the inner solver (see pcg_alpha), passed by value to the kernels.
+struct PcgVecs {
+  double *z, *rx, *s, *dx, *w, *scal;
+  float* z32;
+};
+static PcgVecs pcg_vecs(const IterWs& W) { return PcgVecs{W.z, W.rx, W.s, W.dx, W.w, W.scal, W.z32}; }
+constexpr int kPcgTicket = 63;           // ticket slot of pcg_matvec (tree_reduce uses 0..ngroups)
+
+// One-CTA reductions for the O(n) epilogues: warp sums, then thread 0 adds
+// the per-warp partials in order (the FP64 pipe is narrow, so no thread
+// repeats work another has done).  Result valid in thread 0 only.
+SNS_D double cta_sum0(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Inner solver: preconditioned CG on the normal equations A^T A dx = g with
+// M^-1 = P = R^-1 R^-T, R from the QR of SA (Sec. 1.2, sketch-and-precondition).
+// In exact arithmetic this is CG on R^-T A^T A R^-1 y = R^-T g with dx = R^-1 y,
+// written in x-space so one iteration needs one pass over A (w = A^T A z) and
+// one n x n matvec (s = P r); all O(n) work runs in the final CTA of those two
+// kernels:
+//   pass epilogue:   alpha = rr / (z.w);  dx += alpha z;  r -= alpha w
+//   matvec epilogue: rr' = r.s;  beta = rr'/rr;  z = s + beta z (and FP32 z)
+// P is formed once per solve; kappa(P) = kappa(R)^2 costs ~kappa(R)^2 eps64
+// relative accuracy in P r, irrelevant for a preconditioner.
+SNS_D void pcg_alpha(const PcgVecs& V, int64_t n) {
+  __shared__ double red[32];
+  __shared__ double s_alpha;
+  double zw = 0.0;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) zw = fma(V.z[c], V.w[c], zw);
+  zw = cta_sum0(zw, red);
+  if (threadIdx.x == 0) {
+    const double rr = V.scal[kRR];
+    s_alpha = (zw > 0.0 && rr > 0.0) ? rr / zw : 0.0;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    V.dx[c] = fma(alpha, V.z[c], V.dx[c]);
+    V.rx[c] = fma(-alpha, V.w[c], V.rx[c]);
+  }
+}
+
 
 // ------------------------------------------------------------------ dense FP32
 // Compensated accumulator: value = hi + lo, lo collecting rounding errors.
@@ -339,7 +403,8 @@ resid_pass_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
 template <int VEC, int NCH>
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ z32,
-                float* __restrict__ part, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
+                float* __restrict__ part, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  if (V.scal[kDone] != 0.0) return;                  // this refinement cycle has already converged
   extern __shared__ __align__(16) float fsm[];       // [kPassWarps][n]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float zr[NCH][VEC], acc[NCH][VEC];
@@ -399,7 +464,7 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
     for (int ww = 0; ww < kPassWarps; ++ww) s += fsm[(size_t)ww * n + c];
     out[c] = s;
   }
-  tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
+  if (tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { V.w[c] = s; })) pcg_alpha(V, n);
 }
 
 // ------------------------------------------------------------------ FP64 dense
@@ -447,7 +512,8 @@ resid_pass_f64(const double* __restrict__ A, int64_t lda, const double* __restri
 
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, const double* __restrict__ z,
-                double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
+                double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  if (V.scal[kDone] != 0.0) return;
   extern __shared__ __align__(16) double dsm[];      // z[n], wl[n]
   double* zs = dsm;
   double* wl = dsm + n;
@@ -466,7 +532,7 @@ normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
   __syncthreads();
   double* out = partd + (size_t)blockIdx.x * (n + 4);
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = wl[c];
-  tree_reduce(partd, n + 4, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
+  if (tree_reduce(partd, n + 4, n, ticket, lvl2, [&](int64_t c, double s) { V.w[c] = s; })) pcg_alpha(V, n);
 }
 
 // ------------------------------------------------------------------ CSR
@@ -521,7 +587,8 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                 int64_t m, int64_t n, const float* __restrict__ z32, float* __restrict__ part,
-                uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ wout) {
+                uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  if (V.scal[kDone] != 0.0) return;
   extern __shared__ __align__(16) float fsm[];       // z[n], wl[n]
   float* zs = fsm;
   float* wl = fsm + n;
@@ -542,7 +609,7 @@ normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ 
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * n;
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = wl[c];
-  tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { wout[c] = s; });
+  if (tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { V.w[c] = s; })) pcg_alpha(V, n);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -567,7 +634,7 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     {
       SNS_PROF(K_NORMAL, st);
-    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.lvl2, W.w);
+    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.lvl2, pcg_vecs(W));
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -625,7 +692,7 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_f64<<<W.grid, kPassThreads, smem, st>>>(static_cast<const double*>(da->A), da->lda, da->m, da->n,
-                                                        W.z, W.partd, W.ticket, W.lvl2, W.w);
+                                                        W.z, W.partd, W.ticket, W.lvl2, pcg_vecs(W));
     }
   } else {
     const size_t smem = (size_t)ca->n * 8;
@@ -633,130 +700,161 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
     {
       SNS_PROF(K_NORMAL, st);
     normal_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->m, ca->n, W.z32, W.part,
-                                                        W.ticket, W.lvl2, W.w);
+                                                        W.ticket, W.lvl2, pcg_vecs(W));
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
 
-// out_i = sum_k M[i, k] v[k] (row-major n x n); optional FP32 copy and
-// accum += alpha * out.  One warp per row.
-// Small dense FP64 matvec out = M v (n x n, row-major; R^-1 or R^-T): one warp
-// per row, 4 rows per 128-thread CTA, each lane's loads issued together.
 constexpr int kSmallThreads = 128;
+
+// s = P v, one warp per row (4 rows per CTA); the last CTA to finish runs the
+// epilogue.  START (v = g): r = g, dx = 0, z = s, rr = g.s and the cycle's stop
+// level (the residual must drop by max(tol / (2 eta), kInnerFloor)).  STEP
+// (v = r): beta step as above, one more pass counted, done once rr' <= stop.
+template <bool START>
 __global__ void __launch_bounds__(kSmallThreads)
-small_matvec_kernel(const double* __restrict__ M, const double* __restrict__ v, int64_t n,
-                    double* __restrict__ out, float* __restrict__ out32, double alpha, double* __restrict__ accum) {
+pcg_matvec(const double* __restrict__ P, int64_t n, const double* __restrict__ v, PcgVecs V,
+           uint32_t* __restrict__ ticket, double tol) {
+  __shared__ double red[kSmallThreads / 32];
+  __shared__ double s_beta;
+  __shared__ int s_last;
+  if (!START && V.scal[kDone] != 0.0) return;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n; i += nw) {
-    const double* mr = M + i * n;
-    double s = 0.0;
+    const double* pr = P + i * n;
+    double acc = 0.0;
     int64_t k = lane;
     for (; k + 224 < n; k += 256) {
-      double mv[8], vv[8];
+      double pv[8], vv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        mv[u] = __ldg(mr + k + 32 * u);
-        vv[u] = __ldg(v + k + 32 * u);
+        pv[u] = __ldg(pr + k + 32 * u);
+        vv[u] = __ldcg(v + k + 32 * u);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s = fma(mv[u], vv[u], s);
+      for (int u = 0; u < 8; ++u) acc = fma(pv[u], vv[u], acc);
     }
-    for (; k < n; k += 32) s = fma(__ldg(mr + k), __ldg(v + k), s);
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (out) out[i] = s;
-      if (out32) out32[i] = (float)s;
-      if (accum) accum[i] += alpha * s;
+    for (; k < n; k += 32) acc = fma(__ldg(pr + k), __ldcg(v + k), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) V.s[i] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *ticket = 0;
+  double rs = 0.0;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) rs = fma(__ldcg(v + c), __ldcg(V.s + c), rs);
+  rs = cta_sum0(rs, red);
+  if (threadIdx.x == 0) {
+    if (START) {
+      V.scal[kRR] = rs;
+      const double eta = V.scal[kEta];
+      const double want = (eta > 0.0) ? 0.5 * tol / eta : kInnerFloor;
+      const double ratio = want > kInnerFloor ? want : kInnerFloor;
+      V.scal[kStop2] = ratio * ratio * rs;
+      V.scal[kDone] = (rs > 0.0) ? 0.0 : 1.0;
+      s_beta = 0.0;
+    } else {
+      const double rr = V.scal[kRR];
+      s_beta = (rr > 0.0) ? rs / rr : 0.0;
+      V.scal[kRR] = rs;
+      V.scal[kPasses] += 1.0;
+      if (!(rs > V.scal[kStop2])) V.scal[kDone] = 1.0;
     }
+  }
+  __syncthreads();
+  const double beta = s_beta;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    const double sc = __ldcg(V.s + c);
+    double zc;
+    if (START) {
+      zc = sc;
+      V.rx[c] = __ldcg(v + c);
+      V.dx[c] = 0.0;
+    } else {
+      zc = fma(beta, V.z[c], sc);
+    }
+    V.z[c] = zc;
+    V.z32[c] = (float)zc;
   }
 }
 
-sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
-                        double* accum, cudaStream_t st) {
-  const int rows_per_cta = kSmallThreads / 32;
-  const int grid = (int)std::max<int64_t>(1, (n + rows_per_cta - 1) / rows_per_cta);
+__global__ void __launch_bounds__(kSmallThreads) pcg_apply_kernel(const double* __restrict__ dx, int64_t n,
+                                                                  double* __restrict__ x) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    x[c] += dx[c];
+}
+
+// P = R^-1 R^-T from the row-major upper-triangular R^-1: P[i][j] =
+// sum_{k >= max(i, j)} Rinv[i][k] Rinv[j][k].  16 x 16 output tiles of the
+// upper triangle (mirrored), k in tiles of 16 through shared memory.
+constexpr int kPT = 16;
+__global__ void __launch_bounds__(kPT * kPT) pgram_kernel(const double* __restrict__ Rinv, int64_t n,
+                                                          double* __restrict__ P) {
+  __shared__ double ta[kPT][kPT + 1], tb[kPT][kPT + 1];
+  const int64_t T = (n + kPT - 1) / kPT;
+  int64_t idx = blockIdx.x, ti = 0;
+  while (idx >= T - ti) { idx -= T - ti; ++ti; }     // upper-triangle tile (ti, tj), tj >= ti
+  const int64_t tj = ti + idx;
+  const int ty = threadIdx.x / kPT, tx = threadIdx.x % kPT;
+  const int64_t i0 = ti * kPT, j0 = tj * kPT;
+  double acc = 0.0;
+  for (int64_t k0 = j0; k0 < n; k0 += kPT) {         // Rinv[j][k] = 0 for k < j0 <= j
+    const int64_t ra = i0 + ty, rb = j0 + ty, kk = k0 + tx;
+    ta[ty][tx] = (ra < n && kk < n) ? Rinv[ra * n + kk] : 0.0;
+    tb[ty][tx] = (rb < n && kk < n) ? Rinv[rb * n + kk] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPT; ++u) acc = fma(ta[ty][u], tb[tx][u], acc);
+    __syncthreads();
+  }
+  const int64_t i = i0 + ty, j = j0 + tx;
+  if (i < n && j < n) {
+    P[i * n + j] = acc;
+    P[j * n + i] = acc;
+  }
+}
+
+sns_status pgram_build(const double* Rinv, int64_t n, double* P, cudaStream_t st) {
+  const int64_t T = (n + kPT - 1) / kPT;
+  {
+    SNS_PROF(K_RINV, st);
+    pgram_kernel<<<(unsigned)(T * (T + 1) / 2), kPT * kPT, 0, st>>>(Rinv, n, P);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+static int pcg_grid(int64_t n) { return (int)std::max<int64_t>(1, (n + kSmallThreads / 32 - 1) / (kSmallThreads / 32)); }
+
+sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st) {
   {
     SNS_PROF(K_MATVEC, st);
-  small_matvec_kernel<<<grid, kSmallThreads, 0, st>>>(M, v, n, out, out32, alpha, accum);
+    pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.g, pcg_vecs(W), W.ticket + kPcgTicket, tol);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
-
-// One-CTA reductions for the O(n) CG and eta kernels: warp sums, then thread 0
-// adds the kSmallThreads / 32 partials (the FP64 pipe is narrow, so no thread
-// repeats work another has done).  Result valid in thread 0 only.
-SNS_D double small_sum0(double v, double* red) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kSmallThreads / 32; ++w) t += red[w];
-  return t;
-}
-
-// CG on (R^-T A^T A R^-1) y = rhs.  init: y = 0, res = p = rhs, rr = |res|^2.
-__global__ void __launch_bounds__(kSmallThreads)
-cg_init_kernel(const double* __restrict__ rhs, int64_t n, double* y, double* res, double* p, double* scal) {
-  __shared__ double red[kSmallThreads / 32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double r = rhs[i];
-    y[i] = 0.0;
-    res[i] = r;
-    p[i] = r;
-    s = fma(r, r, s);
-  }
-  s = small_sum0(s, red);
-  if (threadIdx.x == 0) scal[kRR] = s;
-}
-// step: q = R^-T w (given in qv); alpha = rr / (p.q); y += alpha p;
-// res -= alpha q; rr' = |res|^2; p = res + (rr'/rr) p.
-__global__ void __launch_bounds__(kSmallThreads)
-cg_step_kernel(int64_t n, const double* __restrict__ qv, double* y, double* res, double* p, double* scal) {
-  __shared__ double red[2][kSmallThreads / 32];
-  __shared__ double bc[2];
-  double pq = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) pq = fma(p[i], qv[i], pq);
-  pq = small_sum0(pq, red[0]);
-  const double rr = scal[kRR];
-  if (threadIdx.x == 0) bc[0] = (pq > 0.0 && rr > 0.0) ? rr / pq : 0.0;
-  __syncthreads();
-  const double alpha = bc[0];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    y[i] = fma(alpha, p[i], y[i]);
-    const double r = fma(-alpha, qv[i], res[i]);
-    res[i] = r;
-    s = fma(r, r, s);
-  }
-  const double rr2 = small_sum0(s, red[1]);
-  if (threadIdx.x == 0) {
-    bc[1] = (rr > 0.0) ? rr2 / rr : 0.0;
-    scal[kRR] = rr2;      // every thread read the old value before the second barrier
-  }
-  __syncthreads();
-  const double beta = bc[1];
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = fma(beta, p[i], res[i]);
-}
-
-sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st) {
+sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st) {
   {
-    SNS_PROF(K_CG, st);
-  cg_init_kernel<<<1, kSmallThreads, 0, st>>>(W.rhs, n, W.y, W.res, W.p, W.scal);
+    SNS_PROF(K_MATVEC, st);
+    pcg_matvec<false><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.rx, pcg_vecs(W), W.ticket + kPcgTicket, 0.0);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
-sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st) {
+sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st) {
   {
     SNS_PROF(K_CG, st);
-  cg_step_kernel<<<1, kSmallThreads, 0, st>>>(n, W.qv, W.y, W.res, W.p, W.scal);
+    pcg_apply_kernel<<<(unsigned)std::max<int64_t>(1, (n + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0,
+                       st>>>(W.dx, n, x);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -768,7 +866,7 @@ __global__ void __launch_bounds__(kSmallThreads) eta_kernel(const double* __rest
   __shared__ double red[kSmallThreads / 32];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(g[i], g[i], s);
-  s = small_sum0(s, red);
+  s = cta_sum0(s, red);
   if (threadIdx.x == 0) {
     const double rn = sqrt(scal[kRnorm2]);
     const double an = sqrt(scal[kAnorm2]);
@@ -780,15 +878,21 @@ __global__ void __launch_bounds__(kSmallThreads) eta_kernel(const double* __rest
     scal[9] = rn;
     scal[10] = gn;
     scal[11] = an;
+    scal[12] = scal[kPasses];
   }
 }
+sns_status iter_reset(const IterWs& W, cudaStream_t st) {
+  SNS_CUDA_TRY(cudaMemsetAsync(W.scal + kStop2, 0, 3 * sizeof(double), st));
+  return SNS_OK;
+}
+
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st) {
   {
     SNS_PROF(K_ETA, st);
   eta_kernel<<<1, kSmallThreads, 0, st>>>(W.g, n, W.scal);
   }
   SNS_CUDA_TRY(cudaGetLastError());
-  SNS_CUDA_TRY(cudaMemcpyAsync(host_out, W.scal + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SNS_CUDA_TRY(cudaMemcpyAsync(host_out, W.scal + 8, kHostSlots * sizeof(double), cudaMemcpyDeviceToHost, st));
   return SNS_OK;
 }
 

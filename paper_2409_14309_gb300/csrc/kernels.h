@@ -85,7 +85,8 @@ sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, dou
 // Iterative refinement (SAP-SAS).
 struct IterWs {
   double *Rinv, *RinvT;       // n x n row-major
-  double *g, *w, *rhs, *y, *res, *p, *qv, *z, *scal;  // n-vectors and scalars
+  double* P;                  // n x n: R^-1 R^-T, the inner solver's preconditioner
+  double *g, *w, *z, *rx, *s, *dx, *scal;  // n-vectors and scalars
   float *xhi, *xlo, *z32;     // n
   float* part;                // partial n-vectors from passes [grid][n]
   double* partd;              // FP64 partials [grid][n + 4]
@@ -101,10 +102,19 @@ int iter_grid();
 sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, const IterWs& W, bool want_anorm,
                       bool exact_g, cudaStream_t st);
 sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, cudaStream_t st);
-sns_status small_matvec(const double* M, const double* v, int64_t n, double* out, float* out32, double alpha,
-                        double* accum, cudaStream_t st);
-sns_status cg_init(const IterWs& W, int64_t n, cudaStream_t st);
-sns_status cg_step(const IterWs& W, int64_t n, cudaStream_t st);
+// P = R^-1 R^-T (symmetric) from the row-major R^-1.
+sns_status pgram_build(const double* Rinv, int64_t n, double* P, cudaStream_t st);
+// Zeroes the inner-loop control words (stop level, done flag, pass count).
+sns_status iter_reset(const IterWs& W, cudaStream_t st);
+// Refinement cycle of the inner solver (preconditioned CG on A^T A dx = g with
+// M^-1 = P; g from the last residual pass): pcg_start sets dx = 0, r = g,
+// z = P g and the stop level, after which each normal_pass + pcg_step is one
+// iteration; the cycle ends on the device once the CG residual has dropped by
+// max(tol / (2 eta), 4e-3) (later launches return at once) or the host's
+// launch budget runs out.  pcg_apply adds dx to x.
+sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st);
+sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st);
+sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st);
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st);
 
 // Batched.
