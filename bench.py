@@ -60,14 +60,32 @@ class ClockSampler:
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
 
     def start(self):
+        """Starts sampling and returns once the first sample is written, so
+        nvidia-smi's start-up (driver queries) stays outside the timed region."""
+        self.base = 0
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self._lines() < 1:
+            time.sleep(0.02)
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
+
+    def mark(self):
+        """Marks the start of the timed region: later samples are the region's."""
+        self.base = self._lines()
 
     def stop(self):
         if self.proc is None:
@@ -86,12 +104,14 @@ class ClockSampler:
                     rows.append(parts)
         if not rows:
             return None
+        in_region = rows[self.base:]
+        rows = in_region if in_region else rows[-1:]
         sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
         mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "samples_in_region": len(in_region)}
 
 
 # ------------------------------------------------------------------ workload
@@ -255,6 +275,7 @@ def main():
     clk.start()
     barrier()
     torch.cuda.synchronize()
+    clk.mark()
     ev[0].record(stream)
     for k in range(args.steps):
         _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
@@ -376,7 +397,7 @@ def main():
             "config": {"workload": WORKLOAD, "m": M, "n": N, "d": D, "kappa": KAPPA, "tol_eta": TOL,
                        "sketch": "countsketch", "parallelism": f"replicas x{world}",
                        "l2": "A is 1.08 GB > 129 MB L2 and is streamed every pass; no flush needed"},
-            "p50_ms": p(0.50), "p99_ms": p(0.99),
+            "p50_ms": p(0.50), "p99_ms": p(0.99), "step_ms": [round(t, 4) for t in step_ms],
             "kernel_timing": "per-launch CUDA events on the launching stream, in a second pass of the same "
                              "K solves; value and latencies come from the uninstrumented pass",
             "roofline": roof(dom) if dom else None,

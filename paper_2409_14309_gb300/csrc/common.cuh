@@ -113,6 +113,17 @@ SNS_D bool spin_until_ge(const volatile int* flag, int target, long long limit) 
   return *flag >= target;
 }
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// launch_dependent() may become resident while the previous kernel of the
+// stream is still finishing; it must call grid_dep_wait() before it reads
+// anything that kernel wrote (work on read-only inputs may come first).
+// grid_dep_trigger() lets the next dependent kernel start launching; a CTA
+// that exits triggers implicitly.  Without the launch attribute both are no-ops.
+SNS_D void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+SNS_D void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+SNS_D void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 }  // namespace sns
 
 // Host-side launch error check used by the dispatch layer.
@@ -129,4 +140,22 @@ sns_status record_cuda_error(cudaError_t e);
 // several host threads; setting the limit per call would let one thread lower
 // it between another thread's set and launch.
 cudaError_t raise_smem_limit(const void* func);
+
+// Launches kernel<<<grid, block, smem, st>>>(args...) as a programmatic
+// dependent of the stream's previous kernel (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 }

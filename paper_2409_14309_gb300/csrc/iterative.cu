@@ -25,6 +25,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "prof.h"
@@ -36,6 +40,28 @@ constexpr int kPassWarps = kPassThreads / 32;
 constexpr int kNormU = 4;       // rows in flight per warp (normal pass)
 
 int iter_grid() { return num_sms() * 4; }
+
+// Grid of one full wave for a pass kernel: SMs x resident CTAs per SM (capped
+// by the workspace's partial rows).  A second, partial wave would stream the
+// end of A at a fraction of the occupancy.  Cached per (device, kernel, smem).
+static int pass_grid(const void* fn, size_t smem, int cap) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, fn, smem);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return std::min(it->second, cap);
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPassThreads, smem) != cudaSuccess || occ < 1) occ = 1;
+  const int g = num_sms() * occ;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = g;
+  return std::min(g, cap);
+}
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -99,6 +125,23 @@ constexpr double kInnerFloor = 4e-3;
 // Returns true in the one CTA that emitted (after a barrier, so its emitted
 // values are visible to all its threads).
 constexpr int kRedGroup = 32;
+// Sum of the cnt values p[k * stride] in the order k = 0, 1, ...; loads are
+// issued in batches (32 floats: a group of float partials in one L2 round
+// trip; 8 doubles, which keeps the FP64 passes' register budget).
+template <typename PT>
+SNS_D double sum_strided(const PT* __restrict__ p, int64_t stride, int64_t cnt) {
+  constexpr int K = sizeof(PT) == 4 ? 32 : 8;
+  double acc = 0.0;
+  for (int64_t k0 = 0; k0 < cnt; k0 += K) {
+    PT v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (k0 + k < cnt) ? __ldcg(p + (k0 + k) * stride) : PT(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (k0 + k < cnt) acc += (double)v[k];
+  }
+  return acc;
+}
 template <typename PT, typename F>
 SNS_D bool tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, uint32_t* __restrict__ tickets,
                        double* __restrict__ lvl2, F&& emit) {
@@ -113,13 +156,8 @@ SNS_D bool tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, 
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
-    double acc = 0.0;
-    const PT* pc = part + grp * kRedGroup * stride + c;
-#pragma unroll 8
-    for (int64_t k = 0; k < gsize; ++k) acc += (double)__ldcg(pc + k * stride);
-    lvl2[grp * stride + c] = acc;
-  }
+  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x)
+    lvl2[grp * stride + c] = sum_strided(part + grp * kRedGroup * stride + c, stride, gsize);
   if (threadIdx.x == 0) tickets[grp] = 0;
   __threadfence();
   __syncthreads();
@@ -127,12 +165,7 @@ SNS_D bool tree_reduce(const PT* __restrict__ part, int64_t stride, int64_t nc, 
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) {
-    double acc = 0.0;
-#pragma unroll 8
-    for (int64_t q = 0; q < ngroups; ++q) acc += __ldcg(lvl2 + q * stride + c);
-    emit(c, acc);
-  }
+  for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) emit(c, sum_strided(lvl2 + c, stride, ngroups));
   if (threadIdx.x == 0) tickets[ngroups] = 0;
   __syncthreads();
   return true;
@@ -404,9 +437,20 @@ template <int VEC, int NCH>
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ z32,
                 float* __restrict__ part, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
-  if (V.scal[kDone] != 0.0) return;                  // this refinement cycle has already converged
   extern __shared__ __align__(16) float fsm[];       // [kPassWarps][n]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // A is read-only: start this warp's first rows towards L2 before waiting
+  // for the kernel that produced z
+  {
+    const int64_t pc = min((int64_t)lane * ((n + 31) / 32), n - 1);   // lanes spread over the row
+#pragma unroll
+    for (int u = 0; u < kNormU; ++u)
+      if (gw * kNormU + u < m) prefetch_l2(A + (gw * kNormU + u) * lda + pc);
+  }
+  grid_dep_wait();
+  if (V.scal[kDone] != 0.0) return;                  // this refinement cycle has already converged
   float zr[NCH][VEC], acc[NCH][VEC];
   bool ok[NCH];
 #pragma unroll
@@ -419,8 +463,6 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
       acc[q][v] = 0.f;
     }
   }
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r0 = gw * kNormU; r0 < m; r0 += nw * kNormU) {
     float a[kNormU][NCH][VEC];
 #pragma unroll
@@ -449,6 +491,7 @@ normal_pass_f32(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, 
         for (int v = 0; v < VEC; ++v) acc[q][v] = fmaf(t, a[u][q][v], acc[q][v]);
     }
   }
+  grid_dep_trigger();                                // the next kernel may start launching
   float* myrow = fsm + (size_t)w * n;
 #pragma unroll
   for (int q = 0; q < NCH; ++q)
@@ -513,6 +556,7 @@ resid_pass_f64(const double* __restrict__ A, int64_t lda, const double* __restri
 __global__ void __launch_bounds__(kPassThreads)
 normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, const double* __restrict__ z,
                 double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  grid_dep_wait();
   if (V.scal[kDone] != 0.0) return;
   extern __shared__ __align__(16) double dsm[];      // z[n], wl[n]
   double* zs = dsm;
@@ -588,6 +632,7 @@ __global__ void __launch_bounds__(kPassThreads)
 normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                 int64_t m, int64_t n, const float* __restrict__ z32, float* __restrict__ part,
                 uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  grid_dep_wait();
   if (V.scal[kDone] != 0.0) return;
   extern __shared__ __align__(16) float fsm[];       // z[n], wl[n]
   float* zs = fsm;
@@ -623,18 +668,21 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
     auto k = want_anorm ? (exact_g ? resid_pass_f32<VEC, NCH, U, true, true> : resid_pass_f32<VEC, NCH, U, true, false>)
                         : (exact_g ? resid_pass_f32<VEC, NCH, U, false, true> : resid_pass_f32<VEC, NCH, U, false, false>);
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
+    const int grid = pass_grid((const void*)k, smem, W.grid);
     {
       SNS_PROF(K_RESID, st);
-    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket, W.lvl2,
-                                          W.g, W.scal);
+    k<<<grid, kPassThreads, smem, st>>>(A, a.lda, static_cast<const float*>(a.b), a.m, a.n, x, W.partd, W.ticket, W.lvl2,
+                                        W.g, W.scal);
     }
   } else {
     const size_t smem = (size_t)kPassWarps * a.n * 4;
     auto k = normal_pass_f32<VEC, NCH>;
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
+    const int grid = pass_grid((const void*)k, smem, W.grid);
     {
       SNS_PROF(K_NORMAL, st);
-    k<<<W.grid, kPassThreads, smem, st>>>(A, a.lda, a.m, a.n, W.z32, W.part, W.ticket, W.lvl2, pcg_vecs(W));
+    SNS_CUDA_TRY(launch_dependent(k, dim3(grid), dim3(kPassThreads), smem, st, A, a.lda, a.m, a.n, W.z32, W.part,
+                                  W.ticket, W.lvl2, pcg_vecs(W)));
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -720,19 +768,27 @@ pcg_matvec(const double* __restrict__ P, int64_t n, const double* __restrict__ v
   __shared__ double red[kSmallThreads / 32];
   __shared__ double s_beta;
   __shared__ int s_last;
-  if (!START && V.scal[kDone] != 0.0) return;
+  grid_dep_trigger();                                // few CTAs: let the next pass launch now
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // P is read-only here: load this warp's first chunk of its first row before
+  // waiting for the kernel that produced v
+  double p0[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) p0[u] = (gw < n && lane + 32 * u < n) ? __ldg(P + gw * n + lane + 32 * u) : 0.0;
+  grid_dep_wait();
+  if (!START && V.scal[kDone] != 0.0) return;
   for (int64_t i = gw; i < n; i += nw) {
     const double* pr = P + i * n;
     double acc = 0.0;
     int64_t k = lane;
     for (; k + 224 < n; k += 256) {
       double pv[8], vv[8];
+      const bool pre = (i == gw && k == lane);       // chunk already in p0
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        pv[u] = __ldg(pr + k + 32 * u);
+        pv[u] = pre ? p0[u] : __ldg(pr + k + 32 * u);
         vv[u] = __ldcg(v + k + 32 * u);
       }
 #pragma unroll
@@ -845,7 +901,8 @@ sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st) {
 sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st) {
   {
     SNS_PROF(K_MATVEC, st);
-    pcg_matvec<false><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.rx, pcg_vecs(W), W.ticket + kPcgTicket, 0.0);
+    SNS_CUDA_TRY(launch_dependent(pcg_matvec<false>, dim3(pcg_grid(n)), dim3(kSmallThreads), 0, st, W.P, n, W.rx,
+                                  pcg_vecs(W), W.ticket + kPcgTicket, 0.0));
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
