@@ -265,14 +265,27 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
 
   // Update column cc with reflector j (rows >= j; f = beta * u^T c), then
   // build reflector c1 = j + 1 from it and publish.  With j < 0 the column is
-  // only reflected (column 0).
-  auto critical = [&](double* cc, int64_t j, double beta) {
+  // only reflected (column 0).  The dot over rows > j and its CTA reduction
+  // need neither beta nor v_0 (row j's u entry), so they run before
+  // scalars() fetches them: the reflector's rows are published ahead of its
+  // scalars, and this overlaps the dot with the producer's norm and sqrt.
+  auto critical = [&](double* cc, int64_t j, auto&& scalars, double& beta, double& v0) {
     const int64_t c1 = j + 1;
     double f = 0.0;
-    if (j >= 0 && beta != 0.0) {
+    if (j >= 0) {
+      // early, non-blocking tries at beta_j and v_0: the poll below costs a
+      // full L2 round trip when it starts only after the reduction
+      const double* ps = pub + 2 * j;
+      const double e0b = ld_relaxed(ps), e0v = ld_relaxed(ps + 1);
       double part = 0.0;
-      for (int64_t i = coop_first_row(j); i < d; i += kCoopThreads) part = fma(vsm[i], cc[i], part);
-      f = beta * coop_sum_all(part, redc[0]);
+      for (int64_t i = coop_first_row(j + 1); i < d; i += kCoopThreads) part = fma(vsm[i], cc[i], part);
+      const double e1b = ld_relaxed(ps), e1v = ld_relaxed(ps + 1);
+      // row j of this column, read by every thread before the reduction's
+      // barrier: its owner overwrites it in the update loop below
+      const double cj = cc[j];
+      const double t = coop_sum_all(part, redc[0]);
+      scalars(e0b, e0v, e1b, e1v);
+      if (beta != 0.0) f = beta * fma(v0, cj, t);
     }
     const bool publish = c1 < steps;
     double* ucol = U + c1 * d;                         // published rows c1+1..
@@ -292,27 +305,30 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
     if (tid == 0) {
       const double x0 = cc[c1];
       const double normx = sqrt(nrm2);
-      double alpha = x0, v0 = 0.0, bt = 0.0;
+      double alpha = x0, vv0 = 0.0, bt = 0.0;
       if (normx > 0.0) {
         alpha = (x0 >= 0.0) ? -normx : normx;
-        v0 = x0 - alpha;
-        bt = -1.0 / (alpha * v0);
+        vv0 = x0 - alpha;
+        bt = -1.0 / (alpha * vv0);
       }
       cc[c1] = alpha;
       bcast[kCoopBatch + 1] = bt;
-      bcast[kCoopBatch + 2] = v0;
+      bcast[kCoopBatch + 2] = vv0;
       st_relaxed(pub + 2 * c1, bt);
-      st_relaxed(pub + 2 * c1 + 1, v0);
+      st_relaxed(pub + 2 * c1 + 1, vv0);
     }
   };
 
-  if (b == 0) critical(col(0), -1, 0.0);
+  {
+    double b0 = 0.0, v00 = 0.0;
+    if (b == 0) critical(col(0), -1, [](double, double, double, double) {}, b0, v00);
+  }
   const int64_t jend = clast < steps ? clast : steps;
   for (int64_t j = 0; j < jend; ++j) {
     const bool mine = (j % G) == b;
     __syncthreads();                                   // previous step done; owner's bcast visible
-    // reflector j into this thread's rows of vsm
-    double beta, v0 = 0.0;
+    // reflector j's rows > j into this thread's rows of vsm
+    double beta = 0.0, v0 = 0.0;
     const bool row_j = coop_first_row(j) == j;         // this thread holds row j (u_j[0] = v_0)
     if (mine) {
       beta = bcast[kCoopBatch + 1];
@@ -321,23 +337,7 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
       for (int64_t i = coop_first_row(j + 1); i < d; i += kCoopThreads) vsm[i] = cj[i];
     } else {
       const double* uj = U + j * d;
-      int64_t i = coop_first_row(j + 1);
-      {   // first 8 rows together with beta and v_0
-        const double* ad[10];
-        double vv[10];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) ad[u] = (i + u * kCoopThreads < d) ? uj + i + u * kCoopThreads : nullptr;
-        ad[8] = pub + 2 * j;
-        ad[9] = row_j ? pub + 2 * j + 1 : nullptr;
-        coop_poll<10>(ad, vv, err);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (ad[u]) vsm[i + u * kCoopThreads] = vv[u];
-        beta = vv[8];
-        if (row_j) v0 = vv[9];
-        i += 8 * kCoopThreads;
-      }
-      for (; i < d; i += 8 * kCoopThreads) {
+      for (int64_t i = coop_first_row(j + 1); i < d; i += 8 * kCoopThreads) {
         const double* ad[8];
         double vv[8];
 #pragma unroll
@@ -348,10 +348,33 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
           if (ad[u]) vsm[i + u * kCoopThreads] = vv[u];
       }
     }
-    if (row_j) vsm[j] = v0;
+    // beta_j and v_0 (published after the rows; the caller may pass two
+    // earlier loads of them, used if either already holds the values); row j
+    // of vsm
+    auto scalars = [&](double e0b, double e0v, double e1b, double e1v) {
+      if (!mine) {
+        auto ready = [](double x) { return __double_as_longlong(x) != kSentinel; };
+        if (ready(e0b) && ready(e0v)) {
+          beta = e0b;
+          v0 = e0v;
+        } else if (ready(e1b) && ready(e1v)) {
+          beta = e1b;
+          v0 = e1v;
+        } else {
+          const double* ad[2] = {pub + 2 * j, pub + 2 * j + 1};
+          double vv[2];
+          coop_poll<2>(ad, vv, err);
+          beta = vv[0];
+          v0 = vv[1];
+        }
+      }
+      if (row_j) vsm[j] = v0;
+    };
     // look-ahead column j + 1
     const int64_t c1 = j + 1;
-    if (c1 % G == b) critical(col((c1 - b) / G), j, beta);
+    const double none = __longlong_as_double(kSentinel);
+    if (c1 % G == b) critical(col((c1 - b) / G), j, scalars, beta, v0);
+    else scalars(none, none, none, none);
     if (beta == 0.0) continue;
     // other owned columns > j + 1, up to kCoopBatch per batched reduction
     int64_t k0 = (c1 + 1 - b + G - 1) / G;               // first owned index with column > j + 1
@@ -388,7 +411,11 @@ __global__ void __launch_bounds__(kFinishThreads) qr_finish_kernel(QrOut o) {
   qr_finish_cta<kTriRing>(o.W, o.d, o.q, o.x, o.status, o.sres, zsm, red);
 }
 
-static int qr_coop_grid(int64_t q) { return (int)std::max<int64_t>(1, std::min<int64_t>(q, num_sms())); }
+// Up to two CTAs per SM: with fewer columns per CTA, the CTA about to build the
+// next reflector has no other columns' updates queued in front of it (measured:
+// 4.33 -> 4.15 us per column at d = 1024, q = 257; 7.9 -> 6.9 at d = 2048,
+// q = 513).  The launcher checks co-residency.
+static int qr_coop_grid(int64_t q) { return (int)std::max<int64_t>(1, std::min<int64_t>(q, 2 * (int64_t)num_sms())); }
 
 // Workspace: U (q x d doubles) | pub (2 q doubles) | err (int).  U and pub are
 // set to the sentinel and err to 0 by one memset each per factorisation.
@@ -403,20 +430,31 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
   int* err = reinterpret_cast<int*>(w + qr_coop_err_offset(o.d, o.q));
   SNS_CUDA_TRY(cudaMemsetAsync(U, 0xFF, qr_coop_sent_bytes(o.d, o.q), st));
   SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
-  const int grid = qr_coop_grid(o.q);
-  const int64_t own = (o.q + grid - 1) / grid;
   int dev = 0, smem_max = 0;
   SNS_CUDA_TRY(cudaGetDevice(&dev));
   SNS_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t static_smem = 2048;                     // red, bcast, flag word (upper bound)
-  const size_t smem_cols = (size_t)(1 + own) * o.d * 8;
-  const bool in_smem = smem_cols + static_smem <= (size_t)smem_max;
-  const size_t smem = in_smem ? smem_cols : (size_t)o.d * 8;
-  const void* fn = in_smem ? (const void*)qr_coop_kernel<true> : (const void*)qr_coop_kernel<false>;
-  SNS_CUDA_TRY(raise_smem_limit(fn));
-  int occ = 0;
-  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kCoopThreads, smem));
-  if (occ < 1) return SNS_EINVAL;
+  const size_t static_smem = 2048;                     // red, bcast (upper bound)
+  // widest grid (up to two CTAs per SM) whose CTAs are all co-resident
+  int grid = 0;
+  size_t smem = 0;
+  const void* fn = nullptr;
+  for (int g = qr_coop_grid(o.q); g >= 1; g = (g > num_sms()) ? num_sms() : 0) {
+    const int64_t own = (o.q + g - 1) / g;
+    const size_t smem_cols = (size_t)(1 + own) * o.d * 8;
+    const bool in_smem = smem_cols + static_smem <= (size_t)smem_max;
+    const size_t sm = in_smem ? smem_cols : (size_t)o.d * 8;
+    const void* f = in_smem ? (const void*)qr_coop_kernel<true> : (const void*)qr_coop_kernel<false>;
+    SNS_CUDA_TRY(raise_smem_limit(f));
+    int occ = 0;
+    SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kCoopThreads, sm));
+    if ((int64_t)occ * num_sms() >= g) {
+      grid = g;
+      smem = sm;
+      fn = f;
+      break;
+    }
+  }
+  if (!fn) return SNS_EINVAL;
   double* W = o.W;
   int64_t d = o.d, q = o.q;
   void* args[] = {&W, &d, &q, &U, &pub, &err};
