@@ -48,6 +48,24 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
+def read_stream_gbs(dev):
+    """Read-only HBM stream on this GPU (torch sum over 4 GiB of FP32, best of 5),
+    reported beside the copy-bandwidth peak: the passes only read A."""
+    import torch
+    x = torch.ones(1 << 30, dtype=torch.float32, device=dev)
+    best = float("inf")
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x.sum()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del x
+    torch.cuda.empty_cache()
+    return (1 << 32) / (best / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -120,6 +138,22 @@ def make_inputs(rank, device):
     from synth import ill_conditioned_problem
     A, b, _ = ill_conditioned_problem(M, N, seed=DATA_SEED + 1000 * rank, kappa=KAPPA, noise=NOISE)
     return A, b
+
+
+def max_over_ranks(ms, device, world):
+    """The slowest rank's time (the step is done when every replica is done)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, max_ms):
+    """Solves per second of the whole job: every rank solved `steps` problems."""
+    return steps * world / (max_ms / 1e3)
 
 
 def kernel_profile(L):
@@ -219,7 +253,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cs-variant", default="auto", choices=["auto", "sorted", "stream"])
-    ap.add_argument("--workload", default="solve", choices=["solve", "batched", "served", "sketches"])
+    ap.add_argument("--workload", default="solve",
+                    choices=["solve", "batched", "served", "sketches", "latency", "csr"])
     ap.add_argument("--requests", type=int, default=400)
     args = ap.parse_args()
     warm = max(3, args.warmup)
@@ -236,6 +271,10 @@ def main():
         return run_served(args)
     if args.workload == "sketches":
         return run_sketches(args)
+    if args.workload == "latency":
+        return run_latency(args)
+    if args.workload == "csr":
+        return run_csr(args)
 
     import torch
     import torch.distributed as dist
@@ -286,12 +325,8 @@ def main():
     clocks = clk.stop()
     launches = L.snsolve_launch_count() - launches0
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev, world)
+    value = whole_job_rate(args.steps, world, total_ms)
 
     # the same K solves again with a CUDA event pair around every launch (on
     # the launching stream): per-kernel durations for the roofline.  Kept out
@@ -314,6 +349,7 @@ def main():
 
     # roofline of the dominant kernel and of the sketch apply
     hbm_peak, bf16_peak, peak_kind = peaks()
+    read_gbs = read_stream_gbs(dev) if rank == 0 else None
     traffic = traffic_table()
     src = source_hash()
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
@@ -330,6 +366,7 @@ def main():
             ach = amount / avg_s / 1e9
             return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": ach / hbm_peak, "traffic": tval, "peak_kind": f"{peak_kind} copy bandwidth",
+                    "read_stream_GBps": read_gbs, "frac_of_read_stream": ach / read_gbs if read_gbs else None,
                     "algorithmic_bytes_per_launch": amount, "avg_launch_ms": avg_s * 1e3,
                     "launches_per_step": cnt / args.steps}
         ach = amount / avg_s / 1e12
@@ -375,12 +412,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ke * world / (ems / 1e3), "unit": "solves/s",
+        ems = max_over_ranks(e0.elapsed_time(e1), dev, world)
+        e2e = {"value": whole_job_rate(ke, world, ems), "unit": "solves/s",
                "h2d_bytes_per_step": int(A.numel() * 4 + b.numel() * 4), "d2h_bytes_per_step": int(N * 8)}
 
     cpu = None
@@ -644,6 +677,120 @@ def run_sketches(args):
     print(json.dumps({"metric": METRIC, "workload": "sketches", "config": {"m": M, "n": N, "d": D},
                       "peaks": {"hbm_GBps": hbm_peak, "bf16_TFLOPs": bf16_peak, "kind": kind_peak},
                       "sketches": out}))
+
+
+# ------------------------------------------------------------------ small-problem latency
+def run_latency(args):
+    """4096 x 64 FP64 N(0,1), x_true N(0,1), noise 1e-3, CountSketch d = 256 with
+    sketch seed 0: per-call latency of sketch-and-solve and of a solve to
+    eta <= 1e-10 (microseconds, host wall clock around the synchronous call)."""
+    import torch
+    import paper_2409_14309_gb300 as sns
+    dev = torch.device("cuda", 0)
+    ctx = sns.Context(0)
+    rng = np.random.default_rng(1001)
+    m, n, d = 4096, 64, 256
+    A_h = rng.standard_normal((m, n))
+    b_h = A_h @ rng.standard_normal(n) + 1e-3 * rng.standard_normal(m)
+    A = torch.from_numpy(A_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    prob = sns.dense_problem(A, b)
+    out = {}
+    for name, tol in (("sketch_and_solve", 0.0), ("sap_eta_1e-10", 1e-10)):
+        op = sns.opts(d, "countsketch", 0, "auto", tol=tol)
+        ws = torch.empty(ctx.lstsq_workspace(prob, op), dtype=torch.uint8, device=dev)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            ctx.lstsq_problem(prob, op, x=x, ws=ws)
+        torch.cuda.synchronize()
+        ts = []
+        info = None
+        for _ in range(max(args.steps, 50)):
+            t0 = time.perf_counter()
+            _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e6)
+        ts.sort()
+        out[name] = {"p50_us": ts[len(ts) // 2], "p99_us": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
+                     "status": info.status, "iters": info.iters, "outer": info.outer, "eta": info.eta}
+    print(json.dumps({"metric": "small-problem solve latency (us)", "workload": "latency", "unit": "us",
+                      "higher_is_better": False, "dtype": "f64",
+                      "config": {"workload": "dense FP64 N(0,1) 4096 x 64, noise 1e-3, CountSketch d=256 seed 0",
+                                 "m": m, "n": n, "d": d}, "latency": out}))
+
+
+# ------------------------------------------------------------------ sparse workload
+def _csr_dense_rows(m, n, dens, n_dense, gen, dev):
+    """CSR m x n: rows 0..n_dense-1 dense and scaled x100, the others with
+    round(dens * n) uniformly random columns (duplicates add); N(0,1) values;
+    b = A x_true + 1e-3 noise.  Built on the device."""
+    import torch
+    k = max(1, int(round(dens * n)))
+    cnt = torch.full((m,), k, dtype=torch.int64, device=dev)
+    cnt[:n_dense] = n
+    rowptr = torch.zeros(m + 1, dtype=torch.int64, device=dev)
+    rowptr[1:] = torch.cumsum(cnt, 0)
+    nnz = int(rowptr[-1])
+    sparse_cols = torch.sort(torch.randint(0, n, (m - n_dense, k), generator=gen, device=dev, dtype=torch.int32),
+                             dim=1)[0].reshape(-1)
+    dense_cols = torch.arange(n, device=dev, dtype=torch.int32).repeat(n_dense)
+    col = torch.cat([dense_cols, sparse_cols]).contiguous()
+    val = torch.randn(nnz, generator=gen, device=dev)
+    val[: n_dense * n] *= 100.0
+    xt = torch.randn(n, generator=gen, device=dev, dtype=torch.float64)
+    rows = torch.repeat_interleave(torch.arange(m, device=dev), cnt)
+    b = torch.zeros(m, dtype=torch.float64, device=dev).index_add_(0, rows, val.double() * xt[col.long()])
+    b = (b + 1e-3 * torch.randn(m, generator=gen, device=dev, dtype=torch.float64)).float()
+    return rowptr, col, val, b.contiguous(), nnz
+
+
+def run_csr(args):
+    """CSR 2^21 x 512, density 1 % plus 64 dense rows x100, CountSketch d = 2048:
+    preconditioned against unpreconditioned iteration to eta <= 1e-8 (solves/s
+    and passes over A), and the CSR sketch's rate (8 B per nonzero + 8 B per row)."""
+    import torch
+    import paper_2409_14309_gb300 as sns
+    from paper_2409_14309_gb300 import abi
+    dev = torch.device("cuda", 0)
+    ctx = sns.Context(0)
+    L = abi.lib()
+    m, n, d, tol = 1 << 21, 512, 2048, 1e-8
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1003)
+    rowptr, col, val, b, nnz = _csr_dense_rows(m, n, 0.01, 64, gen, dev)
+    hbm_peak, _, peak_kind = peaks()
+    out = {}
+    for name, pre in (("preconditioned", True), ("unpreconditioned", False)):
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.warmup // 3)):
+            ctx.lstsq_csr(rowptr, col, val, b, n, d, seed=SKETCH_SEED, tol=tol, max_iter=4000, precondition=pre)
+        torch.cuda.synchronize()
+        L.snsolve_profile(1)
+        kernel_profile(L)
+        steps = max(2, args.steps // 4)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            _, info = ctx.lstsq_csr(rowptr, col, val, b, n, d, seed=SKETCH_SEED, tol=tol, max_iter=4000,
+                                    precondition=pre)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        prof = kernel_profile(L)
+        L.snsolve_profile(0)
+        out[name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": dt * 1e3, "status": info.status,
+                     "passes": info.iters, "outer": info.outer, "eta": info.eta,
+                     "kernels_ms": {k: v[0] / steps for k, v in prof.items()}}
+    byts = 8.0 * nnz + 8.0 * m
+    gms = out["preconditioned"]["kernels_ms"].get("cs_gather_csr")
+    sk = None
+    if gms:
+        sk = {"kernel": "cs_gather_csr", "ms": gms, "GBps": byts / (gms / 1e3) / 1e9,
+              "frac": byts / (gms / 1e3) / 1e9 / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth",
+              "algorithmic_bytes": byts}
+    print(json.dumps({"metric": "CSR LS solves/s, preconditioned vs not, to eta <= 1e-8", "workload": "csr",
+                      "unit": "solves/s", "higher_is_better": True, "dtype": "f32 passes + f64 QR/solves",
+                      "config": {"workload": "CSR 2097152 x 512, 1% + 64 dense rows x100, noise 1e-3, "
+                                             "CountSketch d=2048", "m": m, "n": n, "nnz": nnz, "d": d},
+                      "solve": out, "sketch_apply": sk}))
 
 
 def run_reference(args, rank, world):
