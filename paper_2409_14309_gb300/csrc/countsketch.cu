@@ -378,7 +378,7 @@ cs_gather_dense(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, i
 
 // Phase 2 (CSR): a lane takes a whole sparse row and adds it into the CTA's
 // shared row accumulator (n floats + 1 for b) with shared atomics.
-__global__ void __launch_bounds__(kGatherWarps * 32)
+__global__ void __launch_bounds__(kGatherWarps * 32, 4)
 cs_gather_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
               const float* __restrict__ b, int64_t n, uint32_t d, int64_t nblk, int64_t spi, int64_t parts,
               const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ seg,
@@ -403,8 +403,23 @@ cs_gather_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ co
           const int64_t row = rid & 0x7FFFFFFFu;
           const float sg = (rid >> 31) ? -1.f : 1.f;
           const int64_t e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
-          for (int64_t e = e0; e < e1; ++e) atomicAdd(acc + __ldg(col + e), sg * __ldg(val + e));
-          atomicAdd(acc + n, sg * __ldg(b + row));
+          const float bv = __ldg(b + row);
+          // the row's entries 8 at a time, all loads issued before the adds:
+          // rows are visited in bucket order, so every row is a random access
+          for (int64_t e = e0; e < e1; e += 8) {
+            int32_t cc[8];
+            float vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const bool ok = e + u < e1;
+              cc[u] = ok ? __ldg(col + e + u) : -1;
+              vv[u] = ok ? __ldg(val + e + u) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (cc[u] >= 0) atomicAdd(acc + cc[u], sg * vv[u]);
+          }
+          atomicAdd(acc + n, sg * bv);
         }
       }
     }

@@ -28,6 +28,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -580,81 +581,311 @@ normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
 }
 
 // ------------------------------------------------------------------ CSR
-__global__ void __launch_bounds__(kPassThreads)
-resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
-               const float* __restrict__ b, int64_t m, int64_t n, const double* __restrict__ x,
-               double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ g,
-               double* __restrict__ scal, int want_anorm) {
-  extern __shared__ __align__(16) double dsm[];      // x[n], gl[n]
-  double* xs = dsm;
-  double* gl = dsm + n;
-  __shared__ double sred[kPassWarps][2];
+// ------------------------------------------------------------------ CSR
+// Rows are walked in chunks of 32 per warp (chunks go round the CTAs first, so
+// neighbouring chunks land on different SMs).  A row with at most kLongRow
+// nonzeros belongs to one lane, which loads its entries kRowBatch at a time.
+// Longer rows (dense rows) go to a per-CTA queue in shared memory that all
+// warps of the CTA drain after the main loop, each long row by a whole warp
+// with coalesced loads (inline when the queue is full).  Products are
+// scattered with shared-memory atomics into a per-warp accumulator row
+// (PERWARP; else one per CTA when n is too large), so only lanes of one warp
+// meet on an address; accumulator rows are added in a fixed order and reduced
+// across CTAs with tree_reduce.  The sum is deterministic up to the order in
+// which one atomic instruction applies equal-address lanes, and the order in
+// which warps drain the long-row queue.
+constexpr int kLongRow = 32;
+constexpr int kRowBatch = 8;             // entries loaded at once per lane (short rows)
+constexpr int kLongBatch = 16;           // per lane for long rows: 512-entry rows in one round trip
+// Shared memory up to which the CSR passes keep one accumulator row per warp.
+constexpr size_t kCsrSmemPerWarpMax = 100 * 1024;
+
+constexpr int kLongQueue = 256;          // long rows queued per CTA (more are done in place)
+struct LongQueue {
+  int64_t row[kLongQueue];
+  int count, next;
+};
+
+// Walks this warp's chunks; short rows go to short_row(row, e0, e1) on their
+// lane; long rows are queued for the CTA (or passed to long_row(row, e0, e1)
+// by the whole warp when the queue is full), and all warps of the CTA drain
+// the queue after the main loop, one long row per warp at a time.
+template <typename Short, typename Long>
+SNS_D void csr_walk(const int64_t* __restrict__ rowptr, int64_t m, LongQueue& Q, Short&& short_row, Long&& long_row) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) { xs[c] = x[c]; gl[c] = 0.0; }
-  __syncthreads();
-  double rr = 0.0, an = 0.0;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e0 = rowptr[r], e1 = rowptr[r + 1];
-    double s = 0.0;
-    for (int64_t e = e0; e < e1; ++e) {
-      const uint32_t c = (uint32_t)col[e];
-      const double a = val[e];
-      if (c < (uint64_t)n) s = fma(a, xs[c], s);
-      an = fma(a, a, an);
-    }
-    const double rv = (double)b[r] - s;
-    rr = fma(rv, rv, rr);
-    for (int64_t e = e0; e < e1; ++e) {
-      const uint32_t c = (uint32_t)col[e];
-      if (c < (uint64_t)n) atomicAdd(gl + c, (double)val[e] * rv);
-    }
-  }
-  rr = warp_sum(rr);
-  an = warp_sum(an);
-  if (lane == 0) { sred[w][0] = rr; sred[w][1] = an; }
-  __syncthreads();
-  double* out = partd + (size_t)blockIdx.x * (n + 4);
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = gl[c];
+  const int64_t gw = (int64_t)w * gridDim.x + blockIdx.x;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (threadIdx.x == 0) {
-    double a0 = 0.0, a1 = 0.0;
-    for (int ww = 0; ww < kPassWarps; ++ww) { a0 += sred[ww][0]; a1 += sred[ww][1]; }
-    out[n] = a0;
-    out[n + 1] = a1;
+    Q.count = 0;
+    Q.next = 0;
   }
-  tree_reduce(partd, n + 4, n + 2, ticket, lvl2, [&](int64_t c, double s) {
-    if (c < n) g[c] = s;
-    else if (c == n) scal[kRnorm2] = s;
-    else if (want_anorm) scal[kAnorm2] = s;
-  });
+  __syncthreads();
+  for (int64_t r0 = gw * 32; r0 < m; r0 += nw * 32) {
+    const int64_t r = r0 + lane;
+    int64_t e0 = 0, e1 = 0;
+    if (r < m) {
+      e0 = __ldg(rowptr + r);
+      e1 = __ldg(rowptr + r + 1);
+    }
+    const bool lng = (e1 - e0) > kLongRow;
+    if (!lng && r < m) short_row(r, e0, e1);
+    bool inline_long = false;
+    if (lng) {
+      const int slot = atomicAdd(&Q.count, 1);
+      if (slot < kLongQueue) Q.row[slot] = r;
+      else inline_long = true;
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, inline_long);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      long_row(r0 + src, __shfl_sync(0xffffffffu, e0, src), __shfl_sync(0xffffffffu, e1, src));
+    }
+  }
+  __syncthreads();
+  const int nq = min(Q.count, kLongQueue);
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(&Q.next, 1);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= nq) break;
+    const int64_t row = Q.row[k];
+    long_row(row, __ldg(rowptr + row), __ldg(rowptr + row + 1));
+  }
 }
 
-__global__ void __launch_bounds__(kPassThreads)
+template <bool PERWARP>
+__global__ void __launch_bounds__(kPassThreads, 3)
 normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                 int64_t m, int64_t n, const float* __restrict__ z32, float* __restrict__ part,
                 uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
+  extern __shared__ __align__(16) float fsm[];       // z[n], accumulators [PERWARP ? warps : 1][n]
+  __shared__ LongQueue Q;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int nacc = PERWARP ? kPassWarps : 1;
   grid_dep_wait();
   if (V.scal[kDone] != 0.0) return;
-  extern __shared__ __align__(16) float fsm[];       // z[n], wl[n]
   float* zs = fsm;
-  float* wl = fsm + n;
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) { zs[c] = z32[c]; wl[c] = 0.f; }
+  float* acc = fsm + n;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) zs[c] = z32[c];
+  for (int64_t c = threadIdx.x; c < nacc * n; c += blockDim.x) acc[c] = 0.f;
   __syncthreads();
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e0 = rowptr[r], e1 = rowptr[r + 1];
-    float s = 0.f;
-    for (int64_t e = e0; e < e1; ++e) {
-      const uint32_t c = (uint32_t)col[e];
-      if (c < (uint64_t)n) s = fmaf(val[e], zs[c], s);
+  float* wl = acc + (PERWARP ? (size_t)w * n : 0);
+  auto short_row = [&](int64_t, int64_t e0, int64_t e1) {
+    for (int64_t eb = e0; eb < e1; eb += kRowBatch) {
+      int32_t cc[kRowBatch];
+      float vv[kRowBatch];
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        const bool ok = eb + u < e1;
+        cc[u] = ok ? __ldg(col + eb + u) : -1;
+        vv[u] = ok ? __ldg(val + eb + u) : 0.f;
+      }
+      float t = 0.f;
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u)
+        if ((uint32_t)cc[u] < (uint64_t)n) t = fmaf(vv[u], zs[cc[u]], t);
+      if (eb + kRowBatch >= e1 && eb == e0) {           // the usual case: one batch holds the row
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u)
+          if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(wl + cc[u], vv[u] * t);
+        return;
+      }
+      // rows of 9..32 entries: finish the dot, then scatter from the top
+      for (int64_t e = eb + kRowBatch; e < e1; ++e) {
+        const uint32_t c = (uint32_t)__ldg(col + e);
+        if (c < (uint64_t)n) t = fmaf(__ldg(val + e), zs[c], t);
+      }
+      for (int64_t e = e0; e < e1; ++e) {
+        const uint32_t c = (uint32_t)__ldg(col + e);
+        if (c < (uint64_t)n) atomicAdd(wl + c, __ldg(val + e) * t);
+      }
+      return;
     }
-    for (int64_t e = e0; e < e1; ++e) {
-      const uint32_t c = (uint32_t)col[e];
-      if (c < (uint64_t)n) atomicAdd(wl + c, val[e] * s);
+  };
+  auto long_row = [&](int64_t, int64_t a0, int64_t a1) {
+    float t = 0.f;
+    for (int64_t eb = a0; eb < a1; eb += 32 * kLongBatch) {
+      int32_t cc[kLongBatch];
+      float vv[kLongBatch];
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u) {
+        const int64_t e = eb + u * 32 + lane;
+        cc[u] = e < a1 ? __ldg(col + e) : -1;
+        vv[u] = e < a1 ? __ldg(val + e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u)
+        if ((uint32_t)cc[u] < (uint64_t)n) t = fmaf(vv[u], zs[cc[u]], t);
     }
-  }
+    t = warp_sum(t);
+    for (int64_t eb = a0; eb < a1; eb += 32 * kLongBatch) {
+      int32_t cc[kLongBatch];
+      float vv[kLongBatch];
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u) {
+        const int64_t e = eb + u * 32 + lane;
+        cc[u] = e < a1 ? __ldg(col + e) : -1;
+        vv[u] = e < a1 ? __ldg(val + e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u)
+        if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(wl + cc[u], vv[u] * t);
+    }
+  };
+  csr_walk(rowptr, m, Q, short_row, long_row);
+  grid_dep_trigger();
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * n;
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[c] = wl[c];
-  if (tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double s) { V.w[c] = s; })) pcg_alpha(V, n);
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < nacc; ++k) t += acc[(size_t)k * n + c];
+    out[c] = t;
+  }
+  if (tree_reduce(part, n, n, ticket, lvl2, [&](int64_t c, double v) { V.w[c] = v; })) pcg_alpha(V, n);
+}
+
+// Residual pass on CSR: r_i = b_i - a_i . x with exact products and
+// compensated sums (x = x_hi + x_lo in FP32), one FP64 value per row; g = A^T r
+// with FP64 shared atomics of a * r (EXACT) or FP32 atomics of a * r_hi.
+template <bool EXACT, bool ANORM, bool PERWARP>
+__global__ void __launch_bounds__(kPassThreads, 2)
+resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+               const float* __restrict__ b, int64_t m, int64_t n, const double* __restrict__ x,
+               double* __restrict__ partd, uint32_t* __restrict__ ticket, double* __restrict__ lvl2, double* __restrict__ g,
+               double* __restrict__ scal) {
+  using AccT = typename std::conditional<EXACT, double, float>::type;
+  extern __shared__ __align__(16) double dsm[];      // x_hi[n], x_lo[n] (FP32), accumulators
+  __shared__ double sred[kPassWarps][2];
+  __shared__ LongQueue Q;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int nacc = PERWARP ? kPassWarps : 1;
+  float* xh = reinterpret_cast<float*>(dsm);
+  float* xl = xh + n;
+  AccT* acc = reinterpret_cast<AccT*>(dsm + n);
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    const double xv = x[c];
+    xh[c] = (float)xv;
+    xl[c] = (float)(xv - (double)xh[c]);
+  }
+  for (int64_t c = threadIdx.x; c < nacc * n; c += blockDim.x) acc[c] = AccT(0);
+  __syncthreads();
+  AccT* gl = acc + (PERWARP ? (size_t)w * n : 0);
+  Comp rrc = {0.f, 0.f};
+  float an = 0.f;
+  auto add_entry = [&](Comp& sdot, int32_t c, float a) {
+    if ((uint32_t)c < (uint64_t)n) {
+      comp_fma(sdot, a, xh[c]);
+      sdot.lo = fmaf(a, xl[c], sdot.lo);
+    }
+    if (ANORM) an = fmaf(a, a, an);
+  };
+  auto resid_of = [&](float bv, Comp sdot, float& rh, float& rl) {
+    Comp rc = {bv, 0.f};
+    comp_add(rc, -sdot.hi);
+    rc.lo -= sdot.lo;
+    rh = rc.hi + rc.lo;
+    rl = rc.lo - (rh - rc.hi);
+  };
+  auto scatter = [&](int32_t c, float a, float rh, double rd) {
+    if ((uint32_t)c < (uint64_t)n) {
+      if constexpr (EXACT) atomicAdd(gl + c, (double)a * rd);
+      else atomicAdd(gl + c, a * rh);
+    }
+  };
+  auto short_row = [&](int64_t r, int64_t e0, int64_t e1) {
+    const float bv = __ldg(b + r);
+    int32_t cc[kRowBatch];
+    float vv[kRowBatch];
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u) {
+      const bool ok = e0 + u < e1;
+      cc[u] = ok ? __ldg(col + e0 + u) : -1;
+      vv[u] = ok ? __ldg(val + e0 + u) : 0.f;
+    }
+    Comp sdot = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u)
+      if (cc[u] >= 0) add_entry(sdot, cc[u], vv[u]);
+    for (int64_t e = e0 + kRowBatch; e < e1; ++e) add_entry(sdot, __ldg(col + e), __ldg(val + e));
+    float rh, rl;
+    resid_of(bv, sdot, rh, rl);
+    comp_fma(rrc, rh, rh);
+    rrc.lo = fmaf(2.f * rh, rl, rrc.lo);
+    const double rd = EXACT ? (double)rh + (double)rl : 0.0;
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u)
+      if (cc[u] >= 0) scatter(cc[u], vv[u], rh, rd);
+    for (int64_t e = e0 + kRowBatch; e < e1; ++e) scatter(__ldg(col + e), __ldg(val + e), rh, rd);
+  };
+  auto long_row = [&](int64_t r, int64_t a0, int64_t a1) {
+    Comp sdot = {0.f, 0.f};
+    for (int64_t eb = a0; eb < a1; eb += 32 * kLongBatch) {
+      int32_t cc[kLongBatch];
+      float vv[kLongBatch];
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u) {
+        const int64_t e = eb + u * 32 + lane;
+        cc[u] = e < a1 ? __ldg(col + e) : -1;
+        vv[u] = e < a1 ? __ldg(val + e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u)
+        if (cc[u] >= 0) add_entry(sdot, cc[u], vv[u]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sdot = comp_plus(sdot, comp_shfl_xor(sdot, o));
+    float rh, rl;
+    resid_of(__ldg(b + r), sdot, rh, rl);
+    if (lane == 0) {
+      comp_fma(rrc, rh, rh);
+      rrc.lo = fmaf(2.f * rh, rl, rrc.lo);
+    }
+    const double rd = EXACT ? (double)rh + (double)rl : 0.0;
+    for (int64_t eb = a0; eb < a1; eb += 32 * kLongBatch) {
+      int32_t cc[kLongBatch];
+      float vv[kLongBatch];
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u) {
+        const int64_t e = eb + u * 32 + lane;
+        cc[u] = e < a1 ? __ldg(col + e) : -1;
+        vv[u] = e < a1 ? __ldg(val + e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLongBatch; ++u)
+        if (cc[u] >= 0) scatter(cc[u], vv[u], rh, rd);
+    }
+  };
+  csr_walk(rowptr, m, Q, short_row, long_row);
+  const double rrw = warp_sum((double)rrc.hi + (double)rrc.lo);
+  const double anw = ANORM ? warp_sum((double)an) : 0.0;
+  if (lane == 0) {
+    sred[w][0] = rrw;
+    sred[w][1] = anw;
+  }
+  __syncthreads();
+  double* out = partd + (size_t)blockIdx.x * (n + 4);
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < nacc; ++k) t += (double)acc[(size_t)k * n + c];
+    out[c] = t;
+  }
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int ww = 0; ww < kPassWarps; ++ww) {
+      a0 += sred[ww][0];
+      a1 += sred[ww][1];
+    }
+    out[n] = a0;
+    out[n + 1] = a1;
+  }
+  tree_reduce(partd, n + 4, n + 2, ticket, lvl2, [&](int64_t c, double v) {
+    if (c < n) g[c] = v;
+    else if (c == n) scal[kRnorm2] = v;
+    else if (ANORM) scal[kAnorm2] = v;
+  });
 }
 
 // ------------------------------------------------------------------ launchers
@@ -720,12 +951,24 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
                                                        W.ticket, W.lvl2, W.g, W.scal, want_anorm ? 1 : 0);
     }
   } else {
-    const size_t smem = (size_t)ca->n * 16;
-    SNS_CUDA_TRY(raise_smem_limit((const void*)resid_pass_csr));
+    const int64_t n = ca->n;
+    const size_t esz = exact_g ? 8 : 4;
+    const bool perwarp = (size_t)n * 8 + (size_t)kPassWarps * n * esz <= kCsrSmemPerWarpMax;
+    const size_t smem = (size_t)n * 8 + (perwarp ? (size_t)kPassWarps : 1) * n * esz;
+    const void* fns[2][2][2] = {{{(const void*)resid_pass_csr<false, false, false>, (const void*)resid_pass_csr<false, false, true>},
+                                 {(const void*)resid_pass_csr<false, true, false>, (const void*)resid_pass_csr<false, true, true>}},
+                                {{(const void*)resid_pass_csr<true, false, false>, (const void*)resid_pass_csr<true, false, true>},
+                                 {(const void*)resid_pass_csr<true, true, false>, (const void*)resid_pass_csr<true, true, true>}}};
+    const void* fn = fns[exact_g][want_anorm][perwarp];
+    SNS_CUDA_TRY(raise_smem_limit(fn));
+    const int grid = pass_grid(fn, smem, W.grid);
+    const float* bb = ca->b;
+    const double* xx = x;
+    void* args[] = {(void*)&ca->rowptr, (void*)&ca->col, (void*)&ca->val, (void*)&bb, (void*)&ca->m, (void*)&ca->n,
+                    (void*)&xx, (void*)&W.partd, (void*)&W.ticket, (void*)&W.lvl2, (void*)&W.g, (void*)&W.scal};
     {
       SNS_PROF(K_RESID, st);
-    resid_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->b, ca->m, ca->n, x, W.partd,
-                                                       W.ticket, W.lvl2, W.g, W.scal, want_anorm ? 1 : 0);
+      SNS_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kPassThreads), args, smem, st));
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
@@ -743,12 +986,16 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
                                                         W.z, W.partd, W.ticket, W.lvl2, pcg_vecs(W));
     }
   } else {
-    const size_t smem = (size_t)ca->n * 8;
-    SNS_CUDA_TRY(raise_smem_limit((const void*)normal_pass_csr));
+    const int64_t n = ca->n;
+    const bool perwarp = (size_t)(1 + kPassWarps) * n * 4 <= kCsrSmemPerWarpMax;
+    const size_t smem = (size_t)(1 + (perwarp ? kPassWarps : 1)) * n * 4;
+    auto k = perwarp ? normal_pass_csr<true> : normal_pass_csr<false>;
+    SNS_CUDA_TRY(raise_smem_limit((const void*)k));
+    const int grid = pass_grid((const void*)k, smem, W.grid);
     {
       SNS_PROF(K_NORMAL, st);
-    normal_pass_csr<<<W.grid, kPassThreads, smem, st>>>(ca->rowptr, ca->col, ca->val, ca->m, ca->n, W.z32, W.part,
-                                                        W.ticket, W.lvl2, pcg_vecs(W));
+      SNS_CUDA_TRY(launch_dependent(k, dim3(grid), dim3(kPassThreads), smem, st, ca->rowptr, ca->col, ca->val, ca->m,
+                                    ca->n, W.z32, W.part, W.ticket, W.lvl2, pcg_vecs(W)));
     }
   }
   SNS_CUDA_TRY(cudaGetLastError());
