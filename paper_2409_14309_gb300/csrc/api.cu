@@ -476,7 +476,8 @@ sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64
 }
 sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes) {
   if (!bytes || mp < 1 || d < 1) return SNS_EINVAL;
-  *bytes = ((size_t)d * 4 + 255) / 256 * 256 + (size_t)(mp < 1024 ? mp : 1024) + 256;
+  const size_t m2 = (size_t)(mp < 1024 ? mp : 1024);
+  *bytes = ((size_t)d * 4 + 255) / 256 * 256 + (m2 + 255) / 256 * 256 + (m2 + 1) * 4;
   return SNS_OK;
 }
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host) {

@@ -34,8 +34,8 @@ static int64_t np2(int64_t m) {
 }
 
 struct SrhtLayout {
-  int64_t mp, m1, m2, q;
-  size_t off_sample, off_need, off_y, bytes;
+  int64_t mp, m1, m2, q, ldy;
+  size_t off_sample, off_need, off_nlist, off_y, bytes;
 };
 static SrhtLayout srht_layout(int64_t m, int64_t n, int64_t d, bool f64) {
   SrhtLayout L{};
@@ -43,11 +43,13 @@ static SrhtLayout srht_layout(int64_t m, int64_t n, int64_t d, bool f64) {
   L.m2 = std::min<int64_t>(L.mp, kM2);
   L.m1 = L.mp / L.m2;
   L.q = n + 1;
+  L.ldy = (L.q + 3) & ~(int64_t)3;                 // 16-byte rows for vector stores
   size_t off = 0;
   auto take = [&](size_t b) { size_t o = off; off += (b + 255) & ~(size_t)255; return o; };
   L.off_sample = take((size_t)d * 4);
   L.off_need = take((size_t)L.m2);
-  L.off_y = take((size_t)L.mp * L.q * (f64 ? 8 : 4));
+  L.off_nlist = take((size_t)(L.m2 + 1) * 4);
+  L.off_y = take((size_t)L.mp * L.ldy * (f64 ? 8 : 4));
   L.bytes = off;
   return L;
 }
@@ -58,7 +60,7 @@ size_t srht_ws_bytes(int64_t m, int64_t n, int64_t d, bool f64) { return srht_la
 // memory; the chosen values are then bitonic-sorted.  Also marks needed p2.
 __global__ void __launch_bounds__(1024)
 srht_sample_kernel(int64_t mp, int64_t d, uint64_t s0, int32_t* __restrict__ sample, uint8_t* __restrict__ need,
-                   int64_t m2) {
+                   int32_t* __restrict__ nlist, int64_t m2) {
   extern __shared__ __align__(16) int32_t ssm[];
   int cap = 1;
   while (cap < 2 * d) cap <<= 1;
@@ -121,10 +123,24 @@ srht_sample_kernel(int64_t mp, int64_t d, uint64_t s0, int32_t* __restrict__ sam
     sample[i] = sel[i];
     need[sel[i] % m2] = 1;
   }
+  __syncthreads();
+  // ascending list of the needed p2 (one thread per p2; m2 <= blockDim), count at nlist[m2]
+  {
+    __shared__ int wcnt[32];
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    const bool f = i < m2 && need[i];
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int k = 0; k < w; ++k) base += wcnt[k];
+    if (f) nlist[base + __popc(bal & ((1u << lane) - 1u))] = i;
+    if (i == (int)blockDim.x - 1) nlist[m2] = base + __popc(bal);
+  }
 }
 
-static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sample, uint8_t* need, int64_t m2,
-                              cudaStream_t st) {
+static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sample, uint8_t* need,
+                              int32_t* nlist, int64_t m2, cudaStream_t st) {
   int cap = 1;
   while (cap < 2 * d) cap <<= 1;
   int dp = 1;
@@ -133,7 +149,7 @@ static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sam
   SNS_CUDA_TRY(raise_smem_limit((const void*)srht_sample_kernel));
   {
     SNS_PROF(K_SRHT_SAMPLE, st);
-  srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, m2);
+  srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, nlist, m2);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -237,38 +253,169 @@ srht_pass1(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, int64_
   }
 }
 
-// Pass 2: CTA per sampled row.
+// Pass 1 for FP32 with 1024-row blocks: 16 columns per tile; each thread loads
+// 16 float4 (4 columns of 16 rows 64 apart, row pointers stepped, no per-element
+// index arithmetic); tile stride 1026 so the four column groups of a warp's
+// stores fall on distinct banks; only the needed rows (compact list from the
+// sampler) are written back, as float4 when the tile lies inside A.
+constexpr int kT1 = 16;
+constexpr int kLdt1 = 1026;
+__global__ void __launch_bounds__(256, 3)
+srht_pass1_f32(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
+               int64_t ntile, uint64_t s_sign, const int32_t* __restrict__ nlist, float* __restrict__ Y, int64_t ldy) {
+  extern __shared__ __align__(16) float tile[];   // [kT1][kLdt1]
+  __shared__ float sgn[kM2];
+  const int tid = threadIdx.x;
+  const int64_t i1 = blockIdx.x / ntile;
+  const int64_t c0 = (blockIdx.x % ntile) * kT1;
+  const int64_t q = n + 1;
+  const int ncol = (int)std::min<int64_t>(kT1, q - c0);
+  const int64_t r0 = i1 * kM2;
+  for (int rl = tid; rl < kM2; rl += blockDim.x) {
+    const int64_t row = r0 + rl;
+    sgn[rl] = (row < m) ? ((splitmix_at(s_sign, (uint64_t)row) >> 63) ? -1.f : 1.f) : 0.f;
+  }
+  __syncthreads();
+  const bool vec = c0 + kT1 <= n;                 // the whole tile lies inside A (aligned rows)
+  const int rsub = tid >> 2, c4 = tid & 3;
+  if (vec) {
+    const float* p = A + (r0 + rsub) * lda + c0 + 4 * c4;
+    const int64_t step = 64 * lda;
+    float4 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      v[u] = (r0 + rsub + 64 * u < m) ? __ldg(reinterpret_cast<const float4*>(p + u * step))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int rl = rsub + 64 * u;
+      const float sg = sgn[rl];
+      float* t = tile + (4 * c4) * kLdt1 + rl;
+      t[0] = sg * v[u].x;
+      t[kLdt1] = sg * v[u].y;
+      t[2 * kLdt1] = sg * v[u].z;
+      t[3 * kLdt1] = sg * v[u].w;
+    }
+  } else {
+    for (int e = tid; e < kM2 * kT1; e += blockDim.x) {
+      const int rl = e / kT1, c = e % kT1;
+      const int64_t row = r0 + rl, colj = c0 + c;
+      float v = 0.f;
+      if (c < ncol && row < m) v = (colj < n) ? __ldg(A + row * lda + colj) : __ldg(b + row);
+      tile[c * kLdt1 + rl] = sgn[rl] * v;
+    }
+  }
+  __syncthreads();
+  const int lane = tid & 31, w = tid >> 5;
+  for (int c = w; c < ncol; c += blockDim.x / 32) {
+    float* col = tile + c * kLdt1;
+    float x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = col[32 * k + lane];
+#pragma unroll
+    for (int sft = 1; sft < 32; sft <<= 1)
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if ((k & sft) == 0) {
+          const float a = x[k], bb = x[k + sft];
+          x[k] = a + bb;
+          x[k + sft] = a - bb;
+        }
+#pragma unroll
+    for (int sft = 1; sft < 32; sft <<= 1)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float o = __shfl_xor_sync(0xffffffffu, x[k], sft);
+        x[k] = (lane & sft) ? (o - x[k]) : (x[k] + o);
+      }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) col[32 * k + lane] = x[k];
+  }
+  __syncthreads();
+  const int nneed = nlist[kM2];
+  if (vec) {
+    for (int k = rsub; k < nneed; k += 64) {
+      const int p2 = nlist[k];
+      const float* t = tile + (4 * c4) * kLdt1 + p2;
+      *reinterpret_cast<float4*>(Y + (r0 + p2) * ldy + c0 + 4 * c4) = make_float4(t[0], t[kLdt1], t[2 * kLdt1], t[3 * kLdt1]);
+    }
+  } else {
+    for (int e = tid; e < nneed * kT1; e += blockDim.x) {
+      const int k = e / kT1, c = e % kT1;
+      if (c < ncol) {
+        const int p2 = nlist[k];
+        Y[(r0 + p2) * ldy + c0 + c] = tile[c * kLdt1 + p2];
+      }
+    }
+  }
+}
+
+// Pass 2: CTA per sampled row p = p1 * m2 + p2.  Warp w adds the terms
+// i1 = w, w + 8, ... of sum_{i1} (-1)^popcount(p1 & i1) Y[i1, p2, :] for 32 * kCPL
+// columns at a time (kCPL per lane, kB terms' loads in flight), each as a
+// compensated (TwoSum) pair; the 8 warps' pairs are then added in warp order.
+constexpr int kCPL = 9;
+constexpr int kP2B = 4;
 template <typename T>
 __global__ void __launch_bounds__(256)
-srht_pass2(const T* __restrict__ Y, int64_t ldy, int64_t q, int64_t m1, int64_t m2, const int32_t* __restrict__ sample,
-           T scale, T* __restrict__ SA, int64_t ldsa, T* __restrict__ Sb, int64_t sbs) {
+srht_pass2_split(const T* __restrict__ Y, int64_t ldy, int64_t q, int64_t m1, int64_t m2,
+                 const int32_t* __restrict__ sample, T scale, T* __restrict__ SA, int64_t ldsa, T* __restrict__ Sb,
+                 int64_t sbs) {
+  constexpr int kW = 8;
+  __shared__ T shi[kW][32 * kCPL], slo[kW][32 * kCPL];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t k = blockIdx.x;
   const int64_t p = sample[k];
   const int64_t p1 = p / m2, p2 = p % m2;
-  for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
-    // compensated (Kahan-Babuska) summation of the m1 signed terms; 16 rows of
-    // Y are loaded before they are added, so 16 loads are in flight
-    constexpr int kL = 16;
-    T acc = T(0), err = T(0);
-    for (int64_t i0 = 0; i0 < m1; i0 += kL) {
-      T v[kL];
+  for (int64_t cb = 0; cb < q; cb += 32 * kCPL) {
+    T hi[kCPL], lo[kCPL];
 #pragma unroll
-      for (int u = 0; u < kL; ++u) {
-        const int64_t i1 = i0 + u;
-        v[u] = (i1 < m1) ? __ldg(Y + (i1 * m2 + p2) * ldy + c) : T(0);
+    for (int s = 0; s < kCPL; ++s) hi[s] = lo[s] = T(0);
+    for (int64_t i0 = w; i0 < m1; i0 += (int64_t)kW * kP2B) {
+      T v[kP2B][kCPL];
+      bool neg[kP2B];
+#pragma unroll
+      for (int bb = 0; bb < kP2B; ++bb) {
+        const int64_t i = i0 + (int64_t)bb * kW;
+        const bool ok = i < m1;
+        neg[bb] = ok && (__popcll((unsigned long long)(p1 & i)) & 1);
+        const T* row = Y + ((ok ? i : 0) * m2 + p2) * ldy + cb + lane;
+#pragma unroll
+        for (int s = 0; s < kCPL; ++s)
+          v[bb][s] = (ok && cb + lane + 32 * s < q) ? __ldg(row + 32 * s) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < kL; ++u) {
-        const int64_t i1 = i0 + u;
-        const T w = (__popcll((unsigned long long)(p1 & i1)) & 1) ? -v[u] : v[u];
-        const T s = acc + w;
-        err += (fabs(acc) >= fabs(w)) ? ((acc - s) + w) : ((w - s) + acc);
-        acc = s;
-      }
+      for (int bb = 0; bb < kP2B; ++bb)
+#pragma unroll
+        for (int s = 0; s < kCPL; ++s) {
+          const T x = neg[bb] ? -v[bb][s] : v[bb][s];
+          const T t = hi[s] + x;
+          const T bv = t - hi[s];
+          lo[s] += (hi[s] - (t - bv)) + (x - bv);
+          hi[s] = t;
+        }
     }
-    acc = (acc + err) * scale;
-    if (c < q - 1) SA[k * ldsa + c] = acc;
-    else Sb[k * sbs] = acc;
+#pragma unroll
+    for (int s = 0; s < kCPL; ++s) {
+      shi[w][lane + 32 * s] = hi[s];
+      slo[w][lane + 32 * s] = lo[s];
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < 32 * kCPL && cb + cc < q; cc += blockDim.x) {
+      T h = shi[0][cc], l = slo[0][cc];
+      for (int ww = 1; ww < kW; ++ww) {
+        const T x = shi[ww][cc];
+        const T t = h + x;
+        const T bv = t - h;
+        l += ((h - (t - bv)) + (x - bv)) + slo[ww][cc];
+        h = t;
+      }
+      const T r = (h + l) * scale;
+      const int64_t c = cb + cc;
+      if (c < q - 1) SA[k * ldsa + c] = r;
+      else Sb[k * sbs] = r;
+    }
+    __syncthreads();
   }
 }
 
@@ -277,24 +424,39 @@ static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, 
                            uint8_t* ws, const SrhtLayout& L, cudaStream_t st) {
   int32_t* sample = reinterpret_cast<int32_t*>(ws + L.off_sample);
   uint8_t* need = ws + L.off_need;
+  int32_t* nlist = reinterpret_cast<int32_t*>(ws + L.off_nlist);
   T* Y = reinterpret_cast<T*>(ws + L.off_y);
-  sns_status s = srht_sample(L.mp, d, seed, sample, need, L.m2, st);
+  sns_status s = srht_sample(L.mp, d, seed, sample, need, nlist, L.m2, st);
   if (s != SNS_OK) return s;
-  constexpr int kSrhtCT = srht_ct<T>();
-  const int64_t ntile = (L.q + kSrhtCT - 1) / kSrhtCT;
-  const size_t smem = ((size_t)kSrhtCT * (L.m2 + 1) + L.m2) * sizeof(T);
-  SNS_CUDA_TRY(raise_smem_limit((const void*)srht_pass1<T>));
-  {
-    SNS_PROF(K_SRHT_PASS1, st);
-  srht_pass1<T><<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(static_cast<const T*>(a.A), a.lda,
-                                                              static_cast<const T*>(a.b), a.m, a.n, L.m2, ntile,
-                                                              stream_state(seed, kStreamSrhtSign), need, Y, L.q);
+  const uint64_t s_sign = stream_state(seed, kStreamSrhtSign);
+  const bool fast = sizeof(T) == 4 && L.m2 == kM2 && a.lda % 4 == 0 && (uintptr_t)a.A % 16 == 0;
+  if (fast) {
+    const int64_t ntile = (L.q + kT1 - 1) / kT1;
+    const size_t smem = (size_t)kT1 * kLdt1 * 4;
+    SNS_CUDA_TRY(raise_smem_limit((const void*)srht_pass1_f32));
+    {
+      SNS_PROF(K_SRHT_PASS1, st);
+      srht_pass1_f32<<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(
+          static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, ntile, s_sign, nlist,
+          reinterpret_cast<float*>(Y), L.ldy);
+    }
+  } else {
+    constexpr int kSrhtCT = srht_ct<T>();
+    const int64_t ntile = (L.q + kSrhtCT - 1) / kSrhtCT;
+    const size_t smem = ((size_t)kSrhtCT * (L.m2 + 1) + L.m2) * sizeof(T);
+    SNS_CUDA_TRY(raise_smem_limit((const void*)srht_pass1<T>));
+    {
+      SNS_PROF(K_SRHT_PASS1, st);
+      srht_pass1<T><<<(unsigned)(L.m1 * ntile), 256, smem, st>>>(static_cast<const T*>(a.A), a.lda,
+                                                                static_cast<const T*>(a.b), a.m, a.n, L.m2, ntile,
+                                                                s_sign, need, Y, L.ldy);
+    }
   }
   SNS_CUDA_TRY(cudaGetLastError());
   {
     SNS_PROF(K_SRHT_PASS2, st);
-  srht_pass2<T><<<(unsigned)d, 256, 0, st>>>(Y, L.q, L.q, L.m1, L.m2, sample, (T)(1.0 / std::sqrt((double)d)), SA,
-                                             ldsa, Sb, sbs);
+    srht_pass2_split<T><<<(unsigned)d, 256, 0, st>>>(Y, L.ldy, L.q, L.m1, L.m2, sample,
+                                                    (T)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -320,11 +482,14 @@ __global__ void widen_i32(const int32_t* in, int64_t n, int64_t* out) {
 sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out, void* ws, size_t ws_bytes,
                              cudaStream_t st) {
   const int64_t m2 = std::min<int64_t>(mp, kM2);
-  const size_t need = ((size_t)d * 4 + 255) / 256 * 256 + (size_t)m2;
+  const size_t o_need = ((size_t)d * 4 + 255) / 256 * 256;
+  const size_t o_list = o_need + ((size_t)m2 + 255) / 256 * 256;
+  const size_t need = o_list + (size_t)(m2 + 1) * 4;
   if (!ws || ws_bytes < need || d > kSrhtMaxD) return SNS_ENOMEM;
   int32_t* sample = static_cast<int32_t*>(ws);
-  uint8_t* nd = static_cast<uint8_t*>(ws) + ((size_t)d * 4 + 255) / 256 * 256;
-  sns_status s = srht_sample(mp, d, seed, sample, nd, m2, st);
+  uint8_t* nd = static_cast<uint8_t*>(ws) + o_need;
+  int32_t* nl = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(ws) + o_list);
+  sns_status s = srht_sample(mp, d, seed, sample, nd, nl, m2, st);
   if (s != SNS_OK) return s;
   {
     SNS_PROF(K_MISC, st);
