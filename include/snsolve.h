@@ -68,10 +68,13 @@ typedef enum {
 
 /* CountSketch variants. */
 typedef enum {
-  SNS_CS_AUTO = 0,          /* library picks (deterministic unless d is too large) */
-  SNS_CS_SORTED = 1,        /* bucket-sorted segmented sum: bitwise reproducible */
-  SNS_CS_STREAM = 2         /* one streaming pass with vector reductions into SA (order of
-                               additions varies run to run) */
+  SNS_CS_AUTO = 0,          /* library picks: FP32 dense -> SORTED while d <= 8192, else STREAM;
+                               FP64 dense -> SORTED; CSR -> STREAM */
+  SNS_CS_SORTED = 1,        /* bucket-sorted segmented sum: bitwise reproducible on dense input;
+                               on CSR (d <= 8192) each bucket's rows are added with shared-memory
+                               atomics, so the order varies there too */
+  SNS_CS_STREAM = 2         /* one streaming pass with float reductions into SA (FP32 dense, CSR;
+                               order of additions varies run to run) */
 } sns_cs_variant;
 
 /* Implicit sketch descriptor.  S is never stored: its entries are functions of

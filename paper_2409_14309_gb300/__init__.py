@@ -116,8 +116,8 @@ class Context:
         """SA = S A and Sb = S b for a dense CUDA matrix."""
         return self.sketch_problem(dense_problem(A, b), sketch_desc(d, kind, seed, variant), A.dtype, ws, stream)
 
-    def sketch_csr(self, rowptr, col, val, b, n, d, seed=0, ws=None, stream=None):
-        return self.sketch_problem(csr_problem(rowptr, col, val, b, n), sketch_desc(d, "countsketch", seed),
+    def sketch_csr(self, rowptr, col, val, b, n, d, seed=0, variant="auto", ws=None, stream=None):
+        return self.sketch_problem(csr_problem(rowptr, col, val, b, n), sketch_desc(d, "countsketch", seed, variant),
                                    torch.float32, ws, stream)
 
     # -------------------------------------------------------------- solve

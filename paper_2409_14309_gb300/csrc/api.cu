@@ -127,8 +127,8 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
     case SNS_COUNTSKETCH:
       if (sk->variant < SNS_CS_AUTO || sk->variant > SNS_CS_STREAM) return SNS_EINVAL;
       if (sk->variant == SNS_CS_SORTED && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
-      if (sk->variant == SNS_CS_STREAM && p->fmt != SNS_DENSE_F32) return SNS_EINVAL;
-      if (p->fmt == SNS_CSR_F32 && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
+      if (sk->variant == SNS_CS_STREAM && p->fmt == SNS_DENSE_F64) return SNS_EINVAL;
+      if (p->fmt == SNS_CSR_F32 && sk->variant == SNS_CS_SORTED && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
       if (p->fmt == SNS_CSR_F32 && p->n > 50000) return SNS_EINVAL;
       return SNS_OK;
     case SNS_GAUSSIAN:
@@ -143,10 +143,15 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
   }
 }
 
+// CountSketch variant: FP64 dense is always sorted; CSR is sorted only when
+// asked for (the CSR iterative passes add in a varying order anyway, and the
+// streaming pass reads the CSR arrays once, in order); FP32 dense is sorted
+// unless asked otherwise or d is above the sorted variant's limit.
 static bool cs_use_sorted(const sns_problem* p, const sns_sketch_desc* sk) {
-  if (p->fmt != SNS_DENSE_F32) return true;
+  if (p->fmt == SNS_DENSE_F64) return true;
   if (sk->variant == SNS_CS_STREAM) return false;
   if (sk->variant == SNS_CS_SORTED) return true;
+  if (p->fmt == SNS_CSR_F32) return false;
   return sk->d <= cs_sorted_max_d();
 }
 
@@ -170,6 +175,9 @@ static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, vo
     case SNS_COUNTSKETCH:
       if (p->fmt == SNS_CSR_F32) {
         CsrArgs ca{p->rowptr, p->col, p->val, static_cast<const float*>(p->b), p->m, p->n, p->nnz};
+        if (!cs_use_sorted(p, sk))
+          return cs_apply_csr_stream(ca, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb),
+                                     sbs, st);
         return cs_apply_csr(ca, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, ws,
                             ws_bytes, st);
       }

@@ -641,6 +641,100 @@ sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, i
   return SNS_OK;
 }
 
+// Streaming CountSketch on CSR: rows in order, chunks of 32 rows per warp
+// (chunks go round the CTAs first), a lane per row with 8 entries loaded at
+// once, rows with more than 32 nonzeros taken by the whole warp (16 entries per
+// lane at once); every nonzero a_ij is added as s(i) a_ij into SA[h(i), j] by a
+// float reduction in L2, b_i into Sb[h(i)].  One pass over the CSR arrays; the
+// order of the additions into a given SA entry varies run to run.  SA and Sb
+// must be zero.
+constexpr int kCsrBatch = 8, kCsrLongBatch = 16, kCsrLongRow = 32;
+__global__ void __launch_bounds__(256)
+cs_stream_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+              const float* __restrict__ b, int64_t m, int64_t n, uint32_t d, uint64_t s0, float* __restrict__ SA,
+              int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)w * gridDim.x + blockIdx.x;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = gw * 32; r0 < m; r0 += nw * 32) {
+    const int64_t r = r0 + lane;
+    int64_t e0 = 0, e1 = 0;
+    uint32_t h = 0;
+    float sg = 0.f;
+    if (r < m) {
+      e0 = __ldg(rowptr + r);
+      e1 = __ldg(rowptr + r + 1);
+      const uint64_t key = splitmix_at(s0, (uint64_t)r);
+      h = bucket_of(key, d);
+      sg = (key >> 63) ? -1.f : 1.f;
+      atomicAdd(Sb + (int64_t)h * sbs, sg * __ldg(b + r));
+    }
+    const bool lng = (e1 - e0) > kCsrLongRow;
+    if (!lng && r < m) {
+      float* dst = SA + (int64_t)h * ldsa;
+      for (int64_t eb = e0; eb < e1; eb += kCsrBatch) {
+        int32_t cc[kCsrBatch];
+        float vv[kCsrBatch];
+#pragma unroll
+        for (int u = 0; u < kCsrBatch; ++u) {
+          const bool ok = eb + u < e1;
+          cc[u] = ok ? __ldg(col + eb + u) : -1;
+          vv[u] = ok ? __ldg(val + eb + u) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kCsrBatch; ++u)
+          if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(dst + cc[u], sg * vv[u]);
+      }
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, lng);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t a0 = __shfl_sync(0xffffffffu, e0, src), a1 = __shfl_sync(0xffffffffu, e1, src);
+      const uint32_t hs = __shfl_sync(0xffffffffu, h, src);
+      const float ss = __shfl_sync(0xffffffffu, sg, src);
+      float* dst = SA + (int64_t)hs * ldsa;
+      for (int64_t eb = a0; eb < a1; eb += 32 * kCsrLongBatch) {
+        int32_t cc[kCsrLongBatch];
+        float vv[kCsrLongBatch];
+#pragma unroll
+        for (int u = 0; u < kCsrLongBatch; ++u) {
+          const int64_t e = eb + u * 32 + lane;
+          cc[u] = e < a1 ? __ldg(col + e) : -1;
+          vv[u] = e < a1 ? __ldg(val + e) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kCsrLongBatch; ++u)
+          if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(dst + cc[u], ss * vv[u]);
+      }
+    }
+  }
+}
+
+sns_status cs_apply_csr_stream(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
+                               int64_t sbs, cudaStream_t st) {
+  if (ldsa == a.n) {
+    SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
+  }
+  if (sbs == 1) {
+    SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
+  }
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_stream_csr, 256, 0));
+  const int grid = num_sms() * std::max(occ, 1);
+  {
+    SNS_PROF(K_CS_CSR, st);
+    cs_stream_csr<<<grid, 256, 0, st>>>(a.rowptr, a.col, a.val, a.b, a.m, a.n, (uint32_t)d,
+                                       stream_state(seed, kStreamCountSketch), SA, ldsa, Sb, sbs);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
 int64_t cs_sorted_max_d() { return 8192; }
 
 // Debug: buckets and signs of rows [0, m) exactly as the kernels compute them.

@@ -44,6 +44,10 @@ sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, v
                                  int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
 sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
                                  int64_t sbs, cudaStream_t st);
+// Streaming CountSketch on CSR (one pass, float reductions into SA; SA and Sb
+// are zeroed here).  The order of additions varies run to run.
+sns_status cs_apply_csr_stream(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
+                               int64_t sbs, cudaStream_t st);
 sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb, int64_t sbs,
                         void* ws, size_t ws_bytes, cudaStream_t st);
 sns_status debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t* h, int8_t* s, cudaStream_t st);

@@ -75,11 +75,12 @@ def test_sorted_variant_bitwise_reproducible():
     assert torch.equal(r1[0], r2[0]) and torch.equal(r1[1], r2[1])
 
 
+@pytest.mark.parametrize("variant", ["auto", "sorted", "stream"])
 @pytest.mark.parametrize("m,n,d,dens", [(1, 1, 1, 1.0), (5000, 40, 160, 0.05), (70001, 512, 2048, 0.01)])
-def test_countsketch_csr(m, n, d, dens):
+def test_countsketch_csr(m, n, d, dens, variant):
     c = ctx()
     A, b, _ = csr_problem(m, n, seed=m, density=dens, n_dense=min(8, m))
-    SA, Sb = c.sketch_csr(dev(A.rowptr), dev(A.col), dev(A.val), dev(b), n, d, seed=4)
+    SA, Sb = c.sketch_csr(dev(A.rowptr), dev(A.col), dev(A.val), dev(b), n, d, seed=4, variant=variant)
     ref = OS.countsketch_apply_csr(A.rowptr, A.col, A.val, n, d, 4)
     scale = np.sqrt(np.sum(A.val.astype(np.float64) ** 2) + np.sum(b.astype(np.float64) ** 2))
     assert rel_fro(SA.cpu().numpy(), ref, scale) <= TOL32
