@@ -385,36 +385,57 @@ def main():
                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "avg_apply_ms": sk_ms / sk_n,
                   "algorithmic_bytes": M * (N + 1) * 4.0}
 
-    # end to end: host-resident inputs, copied in every step through the public API
+    # end to end: host-resident inputs (pinned), copied in every step and solved
+    # through the public API, the solution read back every step.  Two device
+    # buffers and a copy stream: step k+1's inputs are copied while step k is
+    # solved, as a serving loop would do (the host-to-device link, ~210 GB/s
+    # here, otherwise serialises with the solve).
     e2e = None
     if not args.no_e2e:
         Ah = torch.from_numpy(A_h).pin_memory()
         bh = torch.from_numpy(b_h).pin_memory()
         xh = torch.empty(N, dtype=torch.float64).pin_memory()
-        Ad = torch.empty_like(A)
-        bd = torch.empty_like(b)
-        for _ in range(2):
-            Ad.copy_(Ah, non_blocking=True)
-            bd.copy_(bh, non_blocking=True)
+        bufs = [(torch.empty_like(A), torch.empty_like(b)) for _ in range(2)]
+        copy_st = torch.cuda.Stream(device=dev)
+        done_copy = [torch.cuda.Event() for _ in range(2)]
+        free_buf = [torch.cuda.Event() for _ in range(2)]
+
+        def issue_copy(k):
+            Ad, bd = bufs[k % 2]
+            with torch.cuda.stream(copy_st):
+                copy_st.wait_event(free_buf[k % 2])
+                Ad.copy_(Ah, non_blocking=True)
+                bd.copy_(bh, non_blocking=True)
+                done_copy[k % 2].record(copy_st)
+
+        def solve(k):
+            Ad, bd = bufs[k % 2]
+            stream.wait_event(done_copy[k % 2])
             xx, _ = ctx.lstsq(Ad, bd, D, seed=SKETCH_SEED, tol=TOL, ws=ws)
+            free_buf[k % 2].record(stream)
             xh.copy_(xx, non_blocking=True)
+
+        for k in range(2):                       # warm-up of the whole loop
+            issue_copy(k)
+            solve(k)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         ke = max(3, args.steps // 2)
         barrier()
-        e0.record(stream)
-        for _ in range(ke):
-            Ad.copy_(Ah, non_blocking=True)
-            bd.copy_(bh, non_blocking=True)
-            xx, _ = ctx.lstsq(Ad, bd, D, seed=SKETCH_SEED, tol=TOL, ws=ws)
-            xh.copy_(xx, non_blocking=True)
-        e1.record(stream)
+        t0 = time.perf_counter()
+        issue_copy(0)
+        for k in range(ke):
+            if k + 1 < ke:
+                issue_copy(k + 1)
+            solve(k)
         torch.cuda.synchronize()
+        ems = (time.perf_counter() - t0) * 1e3
         barrier()
-        ems = max_over_ranks(e0.elapsed_time(e1), dev, world)
+        ems = max_over_ranks(ems, dev, world)
         e2e = {"value": whole_job_rate(ke, world, ems), "unit": "solves/s",
-               "h2d_bytes_per_step": int(A.numel() * 4 + b.numel() * 4), "d2h_bytes_per_step": int(N * 8)}
+               "h2d_bytes_per_step": int(A.numel() * 4 + b.numel() * 4), "d2h_bytes_per_step": int(N * 8),
+               "pipelined": "step k+1's host-to-device copy overlaps step k's solve (two device buffers, a copy "
+                            "stream); every step copies its inputs and reads back its solution",
+               "timer": "host wall clock around the loop, after a device synchronize on both sides"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
