@@ -211,8 +211,9 @@ SNS_D void stage_rows(float* staging, const float* A, int64_t lda, int64_t col0,
 
 // BULK: rows of A arrive by cp.async.bulk one chunk ahead (needs 16-byte
 // aligned rows and ncols % 4 == 0); otherwise each thread loads its elements.
+constexpr int kUThreads = 512;    // 16 warps: G generation is the instruction-heavy part
 template <bool BULK>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kUThreads, 1)
 gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
            uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
            int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int* __restrict__ err) {
@@ -278,18 +279,25 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     // A chunk -> BF16, K-major: task (column nn, 8 consecutive k): one 16-byte
     // store per task; consecutive threads take consecutive columns (distinct
     // 16-byte bank groups)
+    const bool full = BULK && rows == kUKT && ncols == npad;     // no padding in this chunk
     for (int t = tid; t < kUKC * npad; t += blockDim.x) {
       const int nn = t % npad, k8 = t / npad;
       float f[8];
+      if (full) {
+        const float* src = staging + (size_t)(8 * k8) * ncols + nn;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int k = 8 * k8 + j;
-        float v = 0.f;
-        if (nn < ncols && k < rows) {
-          if (BULK) v = staging[(size_t)k * ncols + nn];
-          else v = __ldg(A + (i0 + k) * lda + col0 + nn);
+        for (int j = 0; j < 8; ++j) f[j] = src[(size_t)j * ncols];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * k8 + j;
+          float v = 0.f;
+          if (nn < ncols && k < rows) {
+            if (BULK) v = staging[(size_t)k * ncols + nn];
+            else v = __ldg(A + (i0 + k) * lda + col0 + nn);
+          }
+          f[j] = v;
         }
-        f[j] = v;
       }
       uint4 w;
       w.x = pack_bf16(f[0], f[1]);
@@ -312,14 +320,18 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     for (int t = tid; t < (kUG / 4) * kUKC; t += blockDim.x) {
       const int gl = t % (kUG / 4), k8 = t / (kUG / 4);
       const int64_t g = (r_base / 32) * 8 + gl;
-      const int rows_here = min(kUKT - 8 * k8, rows);
-      uint64_t ctr = (uint64_t)(i0 + 8 * k8) * (uint64_t)groups + (uint64_t)g;
+      // outputs ctr0, ctr0 + groups, ... of the stream: the generator state
+      // advances by groups * gamma between them (no multiply per output)
+      const uint64_t ctr0 = (uint64_t)(i0 + 8 * k8) * (uint64_t)groups + (uint64_t)g;
+      uint64_t stt = s0 + (ctr0 + 1) * kGamma;
+      const uint64_t step = (uint64_t)groups * kGamma;
       uint64_t key[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        key[j] = (j < rows_here - 0 && 8 * k8 + j < rows) ? splitmix_at(s0, ctr) : 0ull;
-        ctr += (uint64_t)groups;
+        key[j] = mix64(stt);
+        stt += step;
       }
+      const int kvalid = rows - 8 * k8;                      // entries j < kvalid are rows of A
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = 32 * (gl >> 3) + (gl & 7) + 8 * q;
@@ -329,7 +341,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
         for (int j = 0; j < 8; ++j) {
           const uint32_t word = (q < 2) ? (uint32_t)key[j] : (uint32_t)(key[j] >> 32);
           const uint32_t idx = (word >> ((q & 1) * 16 + 4)) & 0xFFFu;
-          h[j] = (rowok && 8 * k8 + j < rows) ? (uint32_t)T[idx] : 0u;
+          h[j] = (rowok && j < kvalid) ? (uint32_t)T[idx] : 0u;
         }
         uint4 w;
         w.x = h[0] | (h[1] << 16);
@@ -362,17 +374,22 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
                    : "memory");
     }
     issued = c + 1;
-    // b column on the CUDA cores: row tid of the G tile times the BF16 b chunk
+    // b column on the CUDA cores: row tid mod 256 of the G tile times half of
+    // the BF16 b chunk (threads 256.. take the second half of K)
     if (with_b) {
       const float* bc = bst + s * kUKT;
+      const int grow = tid & (kUG - 1), kh = tid / kUG;
 #pragma unroll
-      for (int k8 = 0; k8 < kUKT / 8; ++k8) {
-        const uint4 w = *reinterpret_cast<const uint4*>(sA + kmaj_off(tid, 8 * k8));
+      for (int k8 = kh * (kUKC / 2); k8 < (kh + 1) * (kUKC / 2); ++k8) {
+        const uint4 w = *reinterpret_cast<const uint4*>(sA + kmaj_off(grow, 8 * k8));
+        const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * k8);
+        const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * k8 + 4);
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          sb_acc = fmaf(__uint_as_float(ws[h] << 16), bc[8 * k8 + 2 * h], sb_acc);
-          sb_acc = fmaf(__uint_as_float(ws[h] & 0xFFFF0000u), bc[8 * k8 + 2 * h + 1], sb_acc);
+          sb_acc = fmaf(__uint_as_float(ws[h] << 16), bv[2 * h], sb_acc);
+          sb_acc = fmaf(__uint_as_float(ws[h] & 0xFFFF0000u), bv[2 * h + 1], sb_acc);
         }
       }
     }
@@ -390,9 +407,13 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     if (tid == 0) atomicExch(err, 1);
   } else if (issued > 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int mt = warp >> 2, quarter = warp & 3;
+    // 16 warps: warp w reads TMEM lanes of quadrant w mod 4 (the hardware
+    // rule), tile (w / 4) mod 2, and one half of the columns (w / 8)
+    const int quarter = warp & 3, mt = (warp >> 2) & 1, chalf = warp >> 3;
+    const int halfc = ((npad / 16 + 1) / 2) * 16;
+    const int cbeg = chalf ? halfc : 0, cend = chalf ? npad : halfc;
     const int64_t row = r_base + (int64_t)mt * 128 + quarter * 32 + lane;
-    for (int c0 = 0; c0 < npad; c0 += 16) {
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
       uint32_t v[16];
       const uint32_t a = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 256 + c0);
       asm volatile(
@@ -417,7 +438,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
         }
       }
     }
-    if (with_b && r_base + tid < d) atomicAdd(Sb + (r_base + tid) * sbs, sb_acc * scale);
+    if (with_b && r_base + (tid & (kUG - 1)) < d) atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, sb_acc * scale);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -463,7 +484,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
     dim3 grid((unsigned)mtiles, (unsigned)ksplit, (unsigned)ntiles);
     {
       SNS_PROF(K_GAUSS, st);
-      kern<<<grid, 256, gauss_umma_smem(bulk), st>>>(
+      kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
           stream_state(seed, kStreamGaussian), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
           err);
