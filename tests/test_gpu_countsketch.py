@@ -36,7 +36,8 @@ def test_stream_keys_bit_exact():
 
 CASES = [  # m, n, d, lda_pad
     (1, 1, 1, 0), (31, 7, 7, 0), (33, 7, 28, 3), (4097, 64, 256, 0), (12305, 257, 1028, 0),
-    (9000, 128, 512, 4), (20000, 300, 1200, 0), (4096, 3, 5, 1), (50000, 16, 64, 0),
+    (9000, 128, 512, 4), (20000, 300, 1200, 0), (4096, 3, 5, 1), (50000, 16, 64, 0), (6000, 64, 1500, 0),
+    (300001, 36, 144, 0),
 ]
 
 
