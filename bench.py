@@ -68,31 +68,40 @@ def read_stream_gbs(dev):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """SM clock, its maximum, power and the clock event reasons of one GPU, from
+    an nvidia-smi subprocess polling every 20 ms (a separate process, so the
+    benchmark's own host thread is not slowed).  Each sample carries
+    nvidia-smi's timestamp; the timed region's samples are those between mark()
+    and stop().  Output is line-buffered (stdbuf) and nvidia-smi is stopped with
+    SIGINT so that no sample is lost."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.t_mark = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
 
     def start(self):
         """Starts sampling and returns once the first sample is written, so
         nvidia-smi's start-up (driver queries) stays outside the timed region."""
-        self.base = 0
+        import shutil
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            cmd = ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                   "-lms", "20"]
+            if shutil.which("stdbuf"):
+                cmd = ["stdbuf", "-oL"] + cmd
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
             return
         t0 = time.time()
         while time.time() - t0 < 3.0 and self._lines() < 1:
-            time.sleep(0.02)
+            time.sleep(0.01)
 
     def _lines(self):
         try:
@@ -102,34 +111,46 @@ class ClockSampler:
             return 0
 
     def mark(self):
-        """Marks the start of the timed region: later samples are the region's."""
-        self.base = self._lines()
+        """Marks the start of the timed region."""
+        self.t_mark = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
-        self.proc.terminate()
+        t_end = time.time()
+        time.sleep(0.03)                       # the sample that covers the region's end
+        import signal
         try:
+            self.proc.send_signal(signal.SIGINT)
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
+        import datetime
         rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append((ts, parts))
         if not rows:
             return None
-        in_region = rows[self.base:]
-        rows = in_region if in_region else rows[-1:]
-        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
-        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        t0 = self.t_mark if self.t_mark is not None else t_end
+        region = [p for ts, p in rows if t0 <= ts <= t_end]
+        use = region if region else [rows[-1][1]]
+        sm = [float(r[2]) for r in use if re.match(r"^[0-9.]+$", r[2])]
+        mx = [float(r[3]) for r in use if re.match(r"^[0-9.]+$", r[3])]
+        pw = [float(r[4]) for r in use if re.match(r"^[0-9.]+$", r[4])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in use for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "samples_in_region": len(in_region)}
+                "reasons": reasons, "samples": len(use), "samples_in_region": len(region),
+                "power_w_median": float(np.median(pw)) if pw else None, "source": "nvidia-smi, 20 ms period"}
 
 
 # ------------------------------------------------------------------ workload
@@ -254,8 +275,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cs-variant", default="auto", choices=["auto", "sorted", "stream"])
     ap.add_argument("--workload", default="solve",
-                    choices=["solve", "batched", "served", "sketches", "latency", "csr"])
+                    choices=["solve", "batched", "served", "sketches", "latency", "csr", "profile-case"])
     ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr"],
+                    help="profile-case: which small case to run")
     args = ap.parse_args()
     warm = max(3, args.warmup)
 
@@ -275,6 +298,8 @@ def main():
         return run_latency(args)
     if args.workload == "csr":
         return run_csr(args)
+    if args.workload == "profile-case":
+        return run_profile_case(args)
 
     import torch
     import torch.distributed as dist
@@ -595,25 +620,12 @@ def run_served(args):
         srv = sns.Server(ctx, hbm_budget_bytes=150 << 30, max_slots=slots)
         gaps = rng.exponential(1.0 / rate, size=R) if rate else np.zeros(R)
         t_sub, ids = [], []
-        t0 = time.perf_counter()
-        due = t0
-        for i in range(R):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            kind, data, n = pool[picks[i]]
-            d = 4 * n
-            if kind == "dense":
-                rid, _ = srv.submit(data[0], data[1], d, seed=i, tol=float(tols[i]), max_iter=1000)
-            else:
-                rid, _ = srv.submit_csr(*data, n, d, seed=i, tol=float(tols[i]), max_iter=2000)
-            ids.append(rid)
-            t_sub.append(time.perf_counter())
-        lat, bad, fails = [], 0, []
-        # completion times: poll in submission order with long waits; record when each returns done
-        done_t = {}
-        pending = list(range(R))
-        while pending:
+        done_t, pending = {}, []
+        bad, fails = 0, []
+
+        def reap():
+            # completion times are taken while requests are still arriving
+            nonlocal bad
             still = []
             for j in pending:
                 code, info = srv.poll(ids[j], timeout_us=0)
@@ -627,9 +639,27 @@ def run_served(args):
                                       "status": int(info.status), "iters": int(info.iters), "eta": float(info.eta)})
                 else:
                     still.append(j)
-            pending = still
+            pending[:] = still
+
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(R):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                reap()
+            kind, data, n = pool[picks[i]]
+            d = 4 * n
+            if kind == "dense":
+                rid, _ = srv.submit(data[0], data[1], d, seed=i, tol=float(tols[i]), max_iter=1000)
+            else:
+                rid, _ = srv.submit_csr(*data, n, d, seed=i, tol=float(tols[i]), max_iter=2000)
+            ids.append(rid)
+            t_sub.append(time.perf_counter())
+            pending.append(i)
+        while pending:
+            reap()
             if pending:
-                time.sleep(0.0002)
+                time.sleep(0.0001)
         t_end = max(done_t.values())
         srv.close()
         lat = [(done_t[j] - t_sub[j]) * 1e3 for j in range(R)]
@@ -741,6 +771,50 @@ def run_latency(args):
 
 
 # ------------------------------------------------------------------ sparse workload
+def run_profile_case(args):
+    """Small cases for profiler captures: inputs above the L2 size, a few hundred MB
+    on the device.  solve: 2^18 x 256 FP32 (kappa 1e6, noise 1e-4), CountSketch
+    d = 1024, two solves to eta <= 1e-6.  countsketch / srht / gaussian: three
+    sketches of a 2^18 x 256 N(0,1) matrix (2^19 rows for countsketch), d = 1024.
+    csr: 2^19 x 512 at 1 % plus 64 dense rows x100, d = 2048, two solves to 1e-8."""
+    import torch
+    import paper_2409_14309_gb300 as sns
+    dev = torch.device("cuda", 0)
+    ctx = sns.Context(0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    if args.case == "solve":
+        # the 256 x 256 orthogonal factor on the host (the profiler's environment
+        # does not load torch's GPU linear-algebra library)
+        n = 256
+        Z = torch.randn(n, n, generator=torch.Generator().manual_seed(7), dtype=torch.float64)
+        Q, R = torch.linalg.qr(Z)
+        Q = Q * torch.sign(torch.diagonal(R))[None, :]
+        sig = 1e6 ** (-torch.arange(n, dtype=torch.float64) / (n - 1))
+        Mx = (sig[:, None] * Q).float().to(dev)
+        A = (torch.randn(1 << 18, n, generator=gen, device=dev) @ Mx).contiguous()
+        xt = torch.randn(n, generator=gen, device=dev, dtype=torch.float64)
+        b = (A.double() @ xt + 1e-4 * torch.randn(1 << 18, generator=gen, device=dev, dtype=torch.float64)).float()
+        for _ in range(2):
+            x, info = ctx.lstsq(A, b, 1024, seed=1, tol=1e-6)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "solve", "status": info.status, "passes": info.iters, "eta": info.eta}))
+    elif args.case == "csr":
+        rowptr, col, val, b, nnz = _csr_dense_rows(1 << 19, 512, 0.01, 64, gen, dev)
+        for _ in range(2):
+            x, info = ctx.lstsq_csr(rowptr, col, val, b, 512, 2048, seed=1, tol=1e-8, max_iter=4000)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "csr", "status": info.status, "passes": info.iters, "nnz": nnz}))
+    else:
+        m = (1 << 19) if args.case == "countsketch" else (1 << 18)
+        A = torch.randn(m, 256, generator=gen, device=dev)
+        b = torch.randn(m, generator=gen, device=dev)
+        for _ in range(3):
+            SA, Sb = ctx.sketch(A, b, 1024, kind=args.case, seed=1)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "m": m, "norm_SA": float(SA.norm())}))
+
+
 def _csr_dense_rows(m, n, dens, n_dense, gen, dev):
     """CSR m x n: rows 0..n_dense-1 dense and scaled x100, the others with
     round(dens * n) uniformly random columns (duplicates add); N(0,1) values;

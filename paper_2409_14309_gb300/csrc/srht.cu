@@ -139,8 +139,111 @@ srht_sample_kernel(int64_t mp, int64_t d, uint64_t s0, int32_t* __restrict__ sam
   }
 }
 
+// The same sample for m' <= 2^20 with a bitmap of [0, m') in shared memory
+// (128 KB at most).  Warp 0 draws 32 keys at a time; a batch is decided in
+// parallel against the bitmap unless one of its draws could have been inserted
+// by an earlier draw of the same batch (equal draws, or a draw equal to an
+// earlier J), in which case lane 0 walks the batch in order.  The sorted sample
+// is then read off the bitmap in ascending order (block scan of popcounts).
+constexpr int64_t kSampleBitmapMax = (int64_t)1 << 20;
+__global__ void __launch_bounds__(1024)
+srht_sample_bitmap(int64_t mp, int64_t d, uint64_t s0, int32_t* __restrict__ sample, uint8_t* __restrict__ need,
+                   int32_t* __restrict__ nlist, int64_t m2) {
+  extern __shared__ __align__(16) uint32_t bits[];            // mp bits
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nwords = (int)((mp + 31) / 32);
+  for (int i = tid; i < nwords; i += blockDim.x) bits[i] = 0u;
+  for (int64_t i = tid; i < m2; i += blockDim.x) need[i] = 0;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t t0 = 0; t0 < d; t0 += 32) {
+      const int64_t t = t0 + lane;
+      const bool valid = t < d;
+      const uint32_t jbase = (uint32_t)(mp - d + t0);           // J of the batch's first draw
+      uint32_t u = 0xFFFFFFFFu;
+      if (valid) {
+        const uint64_t key = splitmix_at(s0, (uint64_t)t);
+        u = (uint32_t)(((key & 0xFFFFFFFFull) * ((uint64_t)jbase + lane + 1)) >> 32);
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, u);
+      const bool clash = valid && ((peers & lt) != 0u || (u >= jbase && u - jbase < (uint32_t)lane));
+      if (__any_sync(0xffffffffu, clash)) {
+        const int cnt = (int)min((int64_t)32, d - t0);
+        for (int l = 0; l < cnt; ++l) {
+          const uint32_t ul = __shfl_sync(0xffffffffu, u, l);
+          if (lane == 0) {
+            const bool found = (bits[ul >> 5] >> (ul & 31)) & 1u;
+            const uint32_t v = found ? jbase + (uint32_t)l : ul;
+            bits[v >> 5] |= 1u << (v & 31);
+          }
+          __syncwarp();
+        }
+      } else if (valid) {
+        const bool found = (bits[u >> 5] >> (u & 31)) & 1u;
+        const uint32_t v = found ? jbase + (uint32_t)lane : u;
+        atomicOr(&bits[v >> 5], 1u << (v & 31));
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ascending read-out: thread i scans words [i * per, (i + 1) * per)
+  const int per = (nwords + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int wb = tid * per, we = min(nwords, wb + per);
+  int cnt = 0;
+  for (int i = wb; i < we; ++i) cnt += __popc(bits[i]);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int pos = incl - cnt;
+  for (int k = 0; k < w; ++k) pos += wsum[k];
+  for (int i = wb; i < we; ++i) {
+    uint32_t x = bits[i];
+    while (x) {
+      const int bpos = __ffs(x) - 1;
+      x &= x - 1;
+      const int32_t v = i * 32 + bpos;
+      if (pos < d) {
+        sample[pos] = v;
+        need[v % m2] = 1;
+      }
+      ++pos;
+    }
+  }
+  __syncthreads();
+  {
+    __shared__ int wcnt[32];
+    const bool f = tid < m2 && need[tid];
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int k = 0; k < w; ++k) base += wcnt[k];
+    if (f) nlist[base + __popc(bal & ((1u << lane) - 1u))] = tid;
+    if (tid == (int)blockDim.x - 1) nlist[m2] = base + __popc(bal);
+  }
+}
+
 static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sample, uint8_t* need,
                               int32_t* nlist, int64_t m2, cudaStream_t st) {
+  if (mp <= kSampleBitmapMax) {
+    const size_t smem = (size_t)((mp + 31) / 32) * 4;
+    SNS_CUDA_TRY(raise_smem_limit((const void*)srht_sample_bitmap));
+    {
+      SNS_PROF(K_SRHT_SAMPLE, st);
+      srht_sample_bitmap<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, nlist,
+                                                m2);
+    }
+    SNS_CUDA_TRY(cudaGetLastError());
+    return SNS_OK;
+  }
   int cap = 1;
   while (cap < 2 * d) cap <<= 1;
   int dp = 1;

@@ -1,0 +1,58 @@
+"""SRHT apply on the GPU vs the FP64 oracle (Sec. 1.2.1: normalized Hadamard
+sketch applied by the fast transform, S = (1/sqrt(d)) P H D on [A | b] padded
+to m' = 2^ceil(log2 m) rows).  SA and Sb within ||SA_gpu - SA_ref||_F /
+||[A | b]||_F <= 1e-6 for FP32 data (1e-13 for FP64 data).  Each output row is
+a signed sum over all m' rows, so a wrong sampled row or sign shows up as an
+O(1) relative error, not a rounding one.  The cases cover both samplers
+(shared-memory bitmap for m' <= 2^20, hash set above), the 1024-row-block fast
+path and the generic path (m' < 1024, lda not a multiple of 4, FP64), ragged
+m and d = m'."""
+import numpy as np
+import pytest
+
+from gpu_util import ctx, dev, rel_fro
+from oracle import sketch as OS
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+
+
+@pytest.mark.parametrize("m,n,d", [
+    (5, 2, 3), (1000, 7, 64), (1024, 8, 1024), (3000, 16, 128), (70000, 33, 500), (131072, 64, 2048),
+    ((1 << 20) + 3, 4, 256),
+])
+def test_srht_dense_f32(m, n, d):
+    c = ctx()
+    rng = np.random.default_rng(m + 31 * n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    SA, Sb = c.sketch(dev(A), dev(b), d, kind="srht", seed=m % 97)
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
+    assert rel_fro(SA.cpu().numpy(), OS.srht_apply(A, d, m % 97), scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.srht_apply(b, d, m % 97), scale) <= TOL32
+
+
+@pytest.mark.parametrize("m,n,d", [(9, 3, 4), (4097, 10, 100)])
+def test_srht_dense_f64(m, n, d):
+    c = ctx()
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    SA, Sb = c.sketch(dev(A), dev(b), d, kind="srht", seed=5)
+    scale = np.linalg.norm(np.column_stack([A, b]))
+    assert rel_fro(SA.cpu().numpy(), OS.srht_apply(A, d, 5), scale) <= 1e-13
+    assert rel_fro(Sb.cpu().numpy(), OS.srht_apply(b, d, 5), scale) <= 1e-13
+
+
+def test_srht_seeds_differ_and_repeat():
+    """Same seed: the same sketch; another seed: another sample and signs."""
+    c = ctx()
+    rng = np.random.default_rng(2)
+    A = dev(rng.standard_normal((5000, 12)).astype(np.float32))
+    b = dev(rng.standard_normal(5000).astype(np.float32))
+    s1 = c.sketch(A, b, 256, kind="srht", seed=1)[0].cpu().numpy()
+    s1b = c.sketch(A, b, 256, kind="srht", seed=1)[0].cpu().numpy()
+    s2 = c.sketch(A, b, 256, kind="srht", seed=2)[0].cpu().numpy()
+    assert np.array_equal(s1, s1b)
+    assert np.linalg.norm(s1 - s2) > 0.5 * np.linalg.norm(s1)
