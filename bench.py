@@ -69,7 +69,7 @@ def read_stream_gbs(dev):
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """SM clock, its maximum, power and the clock event reasons of one GPU, from
-    an nvidia-smi subprocess polling every 20 ms (a separate process, so the
+    an nvidia-smi subprocess polling every 40 ms (a separate process, so the
     benchmark's own host thread is not slowed).  Each sample carries
     nvidia-smi's timestamp; the timed region's samples are those between mark()
     and stop().  Output is line-buffered (stdbuf) and nvidia-smi is stopped with
@@ -92,7 +92,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             cmd = ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                   "-lms", "20"]
+                   "-lms", "40"]
             if shutil.which("stdbuf"):
                 cmd = ["stdbuf", "-oL"] + cmd
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
@@ -118,7 +118,7 @@ class ClockSampler:
         if self.proc is None:
             return None
         t_end = time.time()
-        time.sleep(0.03)                       # the sample that covers the region's end
+        time.sleep(0.05)                       # the sample that covers the region's end
         import signal
         try:
             self.proc.send_signal(signal.SIGINT)
@@ -150,7 +150,7 @@ class ClockSampler:
         reasons = sorted({names[i] for r in use for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(use), "samples_in_region": len(region),
-                "power_w_median": float(np.median(pw)) if pw else None, "source": "nvidia-smi, 20 ms period"}
+                "power_w_median": float(np.median(pw)) if pw else None, "source": "nvidia-smi, 40 ms period"}
 
 
 # ------------------------------------------------------------------ workload
