@@ -368,9 +368,11 @@ cs_gather_tma(const float* __restrict__ A, int64_t lda, const float* __restrict_
 // ---------------------------------------------------------------------------
 // Phase 2, warp variant: a warp item is (chunk of kChunkRows consecutive
 // entries of one bucket's list, column tile of kWarpCT = 128 columns, i.e.
-// 512 B of each row).  Warps fetch items from a global counter.  The warp
-// loads the chunk's row ids 32 at a time (one coalesced load), keeps 8 row
-// tiles in flight (one float4 per lane each), and adds them into two register
+// 512 B of each row).  Warps fetch items from a global counter, one item
+// ahead: the next item's index and metadata load while the current item
+// streams.  The warp loads the chunk's row ids 32 at a time (one coalesced
+// load; the next 32 load while the current rows stream), keeps 8 row tiles in
+// flight (one float4 per lane each), and adds them into two register
 // accumulators (even / odd rows).  b entries are added per lane and summed by a
 // fixed shuffle tree.  The chunk's row goes to the partial buffer; the last
 // warp to finish a (bucket, tile) (ticket) adds the bucket's chunk rows in
@@ -388,24 +390,46 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = cbase[d];
   const int64_t nitems = nchunks * ntile;
-  for (;;) {
+  // item metadata: (bucket, first and end list entry); the next item's index
+  // and metadata are fetched while the current item streams its rows
+  struct Item {
+    int64_t g, lo, hi, len;
+    uint32_t k;
+  };
+  auto fetch = [&]() {
     uint32_t gi = 0;
     if (lane == 0) gi = atomicAdd(next_item, 1u);
-    const int64_t g = __shfl_sync(0xffffffffu, gi, 0);
-    if (g >= nitems) break;
-    const int64_t chunk = g / ntile, t = g % ntile;
-    const uint32_t k = __ldg(ctab + chunk);
-    const int64_t c = chunk - __ldg(cbase + k);
-    const int64_t len = __ldg(btot + k), base = __ldg(bbase + k);
-    const int64_t lo = base + c * kChunkRows;
-    const int64_t hi = min(base + len, lo + kChunkRows);
+    Item it;
+    it.g = __shfl_sync(0xffffffffu, gi, 0);
+    it.k = 0;
+    it.lo = it.hi = it.len = 0;
+    if (it.g < nitems) {
+      const int64_t chunk = it.g / ntile;
+      it.k = __ldg(ctab + chunk);
+      const int64_t c = chunk - __ldg(cbase + it.k);
+      it.len = __ldg(btot + it.k);
+      const int64_t base = __ldg(bbase + it.k);
+      it.lo = base + c * kChunkRows;
+      it.hi = min(base + it.len, it.lo + kChunkRows);
+    }
+    return it;
+  };
+  Item cur = fetch();
+  while (cur.g < nitems) {
+    const Item nxt = fetch();
+    const int64_t g = cur.g, t = g % ntile;
+    const uint32_t k = cur.k;
+    const int64_t len = cur.len, lo = cur.lo, hi = cur.hi;
     const int64_t col0 = t * kWarpCT;
     const bool okc = col0 + lane * 4 < n;
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), e0 = a0;   // even / odd rows
     float accb = 0.f;
+    uint32_t rid_next = (lo + lane < hi) ? __ldg(list + lo + lane) : 0u;
     for (int64_t j0 = lo; j0 < hi; j0 += 32) {
       const int nr = (int)min((int64_t)32, hi - j0);
-      const uint32_t rid_l = (lane < nr) ? __ldg(list + j0 + lane) : 0u;
+      const uint32_t rid_l = rid_next;
+      // the next 32 row ids load while these rows stream
+      rid_next = (j0 + 32 + lane < hi) ? __ldg(list + j0 + 32 + lane) : 0u;
       if (t == 0 && lane < nr) {
         const float bv = __ldg(b + (rid_l & 0x7FFFFFFFu));
         accb += (rid_l >> 31) ? -bv : bv;
@@ -438,6 +462,7 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
       float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
       if (okc) { out[0] = a0.x; out[1] = a0.y; out[2] = a0.z; out[3] = a0.w; }
       if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = accb;
+      cur = nxt;
       continue;
     }
     float* pr = part + (size_t)g * (kWarpCT + 4);
@@ -448,7 +473,10 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
     uint32_t old = 0;
     if (lane == 0) old = atomicAdd(ticket + (int64_t)k * ntile + t, 1u);
     old = __shfl_sync(0xffffffffu, old, 0);
-    if (old != (uint32_t)(nch_k - 1)) continue;
+    if (old != (uint32_t)(nch_k - 1)) {
+      cur = nxt;
+      continue;
+    }
     __threadfence();
     // last warp of bucket k, tile t: add the chunk rows in chunk order
     const int64_t g0 = (int64_t)__ldg(cbase + k) * ntile + t;
@@ -463,6 +491,7 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
     float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
     if (okc) { out[0] = s0.x; out[1] = s0.y; out[2] = s0.z; out[3] = s0.w; }
     if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = sb;
+    cur = nxt;
   }
 }
 
