@@ -98,12 +98,19 @@ cs_sort_blocks(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __res
   for (int i = tid; i < kSortWarps * (int)d; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
 
+  // hb keeps the bucket (bits 0..14; d <= 8192) and the sign (bit 15), so the
+  // scatter below does not hash again
   for (int j = 0; j < kRowsPerWarp; j += 32) {
     const int loc = w * kRowsPerWarp + j + lane;
     const int64_t row = r0 + loc;
     uint32_t h = kNoBucket;
-    if (row < m) h = bucket_of(splitmix_at(s0, (uint64_t)row), d);
-    hb[loc] = (uint16_t)h;
+    uint32_t sgn = 0;
+    if (row < m) {
+      const uint64_t key = splitmix_at(s0, (uint64_t)row);
+      h = bucket_of(key, d);
+      sgn = (uint32_t)(key >> 63);
+    }
+    hb[loc] = (uint16_t)(h == kNoBucket ? kNoBucket : (h | (sgn << 15)));
     const unsigned peers = __match_any_sync(0xffffffffu, h);
     if (h != kNoBucket && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
     __syncwarp();
@@ -150,13 +157,13 @@ cs_sort_blocks(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __res
   for (int j = 0; j < kRowsPerWarp; j += 32) {
     const int loc = w * kRowsPerWarp + j + lane;
     const int64_t row = r0 + loc;
-    const uint32_t h = hb[loc];
+    const uint32_t hw = hb[loc];
+    const uint32_t h = hw == kNoBucket ? kNoBucket : (hw & 0x7FFFu);
     const unsigned peers = __match_any_sync(0xffffffffu, h);
     uint32_t pos = 0;
     if (h != kNoBucket) {
       pos = cnt[w * d + h] + __popc(peers & lt);
-      const uint64_t key = splitmix_at(s0, (uint64_t)row);
-      sorted[r0 + pos] = (uint32_t)row | ((uint32_t)(key >> 63) << 31);
+      sorted[r0 + pos] = (uint32_t)row | ((hw >> 15) << 31);
     }
     __syncwarp();
     if (h != kNoBucket && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);

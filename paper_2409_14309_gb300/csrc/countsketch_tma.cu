@@ -134,19 +134,40 @@ cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, con
       if (lane == 0) Sb[k * sbs] = 0.f;
     }
     uint32_t pos = sbase[k];
-    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
-      const int64_t blk = b0 + lane;
-      const uint32_t sv = blk < nblk ? __ldg(seg + (size_t)k * nblk + blk) : 0u;
-      const uint32_t c = sv & 0xFFFFu, st = sv >> 16;
-      uint32_t inc = c;
+    // segment words of up to kSegAhead rounds of 32 blocks load together, and
+    // each segment's rows are copied 8 at a time, so a bucket costs a few
+    // dependent memory round trips instead of two per round
+    constexpr int kSegAhead = 8;
+    for (int64_t bb = 0; bb < nblk; bb += 32 * kSegAhead) {
+      uint32_t sv[kSegAhead];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
+      for (int r = 0; r < kSegAhead; ++r) {
+        const int64_t blk = bb + r * 32 + lane;
+        sv[r] = blk < nblk ? __ldg(seg + (size_t)k * nblk + blk) : 0u;
       }
-      const uint32_t ex = inc - c;
-      for (uint32_t i = 0; i < c; ++i) list[pos + ex + i] = __ldg(sorted + blk * kListRowsPerBlock + st + i);
-      pos += __shfl_sync(0xffffffffu, inc, 31);
+#pragma unroll
+      for (int r = 0; r < kSegAhead; ++r) {
+        const int64_t blk = bb + r * 32 + lane;
+        const uint32_t c = sv[r] & 0xFFFFu, st = sv[r] >> 16;
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += t;
+        }
+        const uint32_t ex = inc - c;
+        const uint32_t* src = sorted + blk * kListRowsPerBlock + st;
+        uint32_t* dst = list + pos + ex;
+        for (uint32_t i0 = 0; i0 < c; i0 += 8) {
+          uint32_t v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (i0 + u < c) ? __ldg(src + i0 + u) : 0u;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (i0 + u < c) dst[i0 + u] = v[u];
+        }
+        pos += __shfl_sync(0xffffffffu, inc, 31);
+      }
     }
   }
 }
