@@ -171,7 +171,11 @@ sns_status snsolve_lstsq_workspace_size(const sns_problem* prob, const sns_opts*
  * before return.  With tol <= 0 the call is asynchronous except that it waits
  * for the QR's rank check; with tol > 0 it synchronizes `stream` between
  * refinement steps (convergence scalars are computed on the device and read
- * from pinned memory).  Returns the same status as info->status. */
+ * from pinned memory).  Returns the same status as info->status: SNS_ERANK
+ * from the QR's rank check, SNS_ETIMEOUT when a bounded device-side wait of
+ * the sketch (tcgen05 Gaussian, bulk-copy CountSketch) or of the cooperative
+ * QR expired (nothing of the solve is then valid), SNS_ENOTCONV at the
+ * iteration cap. */
 sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* opts,
                          double* x, sns_info* info, void* ws, size_t ws_bytes, void* stream);
 

@@ -168,6 +168,15 @@ static size_t sketch_ws(const sns_problem* p, const sns_sketch_desc* sk) {
   return 0;
 }
 
+// Error word of the sketch kernels that wait on the device with bounded waits
+// (the tcgen05 Gaussian kernel, the bulk-copy CountSketch gather), or null.
+static const void* sketch_err_word(const sns_problem* p, const sns_sketch_desc* sk, const uint8_t* skws) {
+  if (sk->kind == SNS_GAUSSIAN) return skws + gauss_err_offset();
+  if (sk->kind == SNS_COUNTSKETCH && p->fmt == SNS_DENSE_F32 && cs_use_sorted(p, sk))
+    return skws + cs_layout(p->m, p->n, sk->d, false, false).off_err;
+  return nullptr;
+}
+
 static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, void* SA, int64_t ldsa, void* Sb,
                              int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
   DenseArgs da{p->A, p->lda, p->b, p->m, p->n, is_f64(p)};
@@ -366,12 +375,15 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
       const size_t eoff = L.off_qr + qr_coop_err_offset(d, q);
       SNS_CUDA_TRY(cudaMemcpyAsync(hp + 18, w + eoff, 4, cudaMemcpyDeviceToHost, st));
     }
+    const void* skerr = sketch_err_word(prob, &opts->sk, w + L.off_sk);
+    if (skerr) SNS_CUDA_TRY(cudaMemcpyAsync(hp + 19, skerr, 4, cudaMemcpyDeviceToHost, st));
     SNS_CUDA_TRY(cudaStreamSynchronize(st));
-    int32_t qs, qerr = 0;
+    int32_t qs, qerr = 0, serr = 0;
     memcpy(&qs, hp + 16, 4);
     if (coop) memcpy(&qerr, hp + 18, 4);
+    if (skerr) memcpy(&serr, hp + 19, 4);
     sres = hp[17];
-    if (qerr) {
+    if (qerr || serr) {
       info_fill(info, SNS_ETIMEOUT, 0, 0, 0.0, 0.0, 0.0);
       return SNS_ETIMEOUT;
     }

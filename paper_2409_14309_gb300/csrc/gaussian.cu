@@ -60,6 +60,7 @@ static const uint16_t* table_host() {
   return g_table;
 }
 
+size_t gauss_err_offset() { return 8192; }
 size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
   (void)m; (void)n; (void)d;
   return 8192 + 256;   // the BF16 table (uploaded per call) and an error word
@@ -469,9 +470,9 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
     const char* e = getenv("SNSOLVE_GAUSS");
     use_simt = (e && e[0] == 's') ? 1 : 0;
   }
+  int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + gauss_err_offset());
+  SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
   if (!use_simt) {
-    int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + 8192);
-    SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
     const int64_t mtiles = (d + kUG - 1) / kUG;
     const int64_t ntiles = (a.n + kUN - 1) / kUN;
     int64_t ksplit = std::max<int64_t>(1, (int64_t)num_sms() / std::max<int64_t>(1, mtiles * ntiles));

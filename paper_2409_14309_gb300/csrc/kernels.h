@@ -62,6 +62,9 @@ sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out,
 
 // Gaussian.
 size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d);
+// Byte offset in the Gaussian workspace of the error word its bounded waits
+// set (0 after a sketch that completed).
+size_t gauss_err_offset();
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
                              int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
 void gauss_table_host(uint16_t* out4096);
