@@ -56,3 +56,26 @@ def test_srht_seeds_differ_and_repeat():
     s2 = c.sketch(A, b, 256, kind="srht", seed=2)[0].cpu().numpy()
     assert np.array_equal(s1, s1b)
     assert np.linalg.norm(s1 - s2) > 0.5 * np.linalg.norm(s1)
+
+
+@pytest.mark.parametrize("mp,d", [
+    (1, 1), (2, 2), (8, 8), (64, 60), (1024, 1000), (4096, 3000), (1 << 20, 1024), (1 << 20, 16384),
+    (1 << 21, 1024), (1 << 30, 777),
+])
+def test_srht_row_sample_bit_exact(mp, d):
+    """The sampled rows equal the oracle's Floyd sample exactly: dense cases
+    (d close to m') make most draws collide and take the in-order path of the
+    bitmap sampler; m' > 2^20 takes the hash-set sampler."""
+    c = ctx()
+    for seed in (0, 12345):
+        got = c.srht_sample(mp, d, seed).cpu().numpy()
+        assert np.array_equal(got, OS.srht_sample(mp, d, seed))
+
+
+def test_srht_row_sample_rejects_out_of_range():
+    """m' must be a power of two below 2^31 and 1 <= d <= m'."""
+    import paper_2409_14309_gb300 as sns
+    c = ctx()
+    for mp, d in [(1 << 31, 8), (6, 2), (8, 9)]:
+        with pytest.raises(sns.SnsError):
+            c.srht_sample(mp, d, 0)
