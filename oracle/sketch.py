@@ -241,3 +241,52 @@ def countsketch_rows(A, d, seed, rows):
         idx = np.nonzero(h == k)[0]
         out.append((s[idx].reshape((-1,) + (1,) * (A.ndim - 1)) * A[idx].astype(np.float64)).sum(axis=0))
     return np.array(out)
+
+
+def gaussian_rows(A, d, seed, rows, bf16_operand=True):
+    """Selected output rows k of (G / sqrt(d)) A (Sec. 1.2.1), each from its own
+    row of G: G[k, i] = T[index(k, i)] for all i, then one dot product per
+    column; FP64.  Same layout as gaussian_indices, one row at a time, for
+    checking full-size results."""
+    A = np.asarray(A)
+    m = A.shape[0]
+    Ause = round_to_bf16_via_f32(A) if bf16_operand else A.astype(np.float64)
+    T = gaussian_table()
+    groups = gaussian_groups(d)
+    i = np.arange(m, dtype=np.uint64)
+    state = H.stream_state(seed, H.STREAM_GAUSSIAN)
+    out = []
+    for k in rows:
+        k = np.uint64(k)
+        g = (k // np.uint64(32)) * np.uint64(8) + (k % np.uint64(8))
+        q = (k // np.uint64(8)) % np.uint64(4)
+        key = H.splitmix64_at(state, i * np.uint64(groups) + g)
+        idx = ((key >> (np.uint64(16) * q)) & np.uint64(0xFFFF)) >> np.uint64(4)
+        out.append(T[idx.astype(np.int64)] @ Ause / math.sqrt(d))
+    return np.array(out)
+
+
+def _parity(x):
+    """Parity of the set bits of each uint64 (XOR folding)."""
+    x = x.copy()
+    for s in (32, 16, 8, 4, 2, 1):
+        x ^= x >> np.uint64(s)
+    return x & np.uint64(1)
+
+
+def srht_rows(A, d, seed, rows):
+    """Selected output rows r of the SRHT sketch (Sec. 1.2.1) straight from the
+    definition: with p = P[r], row r = (1/sqrt(d)) sum_i (-1)^popcount(p & i)
+    D_i A_i over the m real rows (the padding rows are zero); FP64.  For checking
+    full-size results one output row at a time."""
+    A = np.asarray(A)
+    m = A.shape[0]
+    P = srht_sample(next_pow2(m), d, seed)
+    Ds = srht_signs(m, seed)
+    Af = A.astype(np.float64)
+    i = np.arange(m, dtype=np.uint64)
+    out = []
+    for r in rows:
+        h = 1.0 - 2.0 * _parity(i & np.uint64(P[r])).astype(np.float64)
+        out.append((h * Ds) @ Af / math.sqrt(d))
+    return np.array(out)

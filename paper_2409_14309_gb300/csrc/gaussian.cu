@@ -61,10 +61,6 @@ static const uint16_t* table_host() {
 }
 
 size_t gauss_err_offset() { return 8192; }
-size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
-  (void)m; (void)n; (void)d;
-  return 8192 + 256;   // the BF16 table (uploaded per call) and an error word
-}
 
 constexpr int kGMt = 64, kGNt = 64, kGKc = 32;
 
@@ -152,7 +148,9 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // stage's mbarrier.  Two stages alternate, so writing chunk c+1 overlaps the
 // MMAs of chunk c.  The b column is accumulated on the CUDA cores from the same
 // BF16 G tile.  The epilogue reads TMEM (tcgen05.ld), scales by 1/sqrt(d) and
-// adds into SA / Sb with FP32 reductions (the K range is split over CTAs).
+// adds into SA / Sb with FP32 reductions (the K range is split over CTAs); it
+// also runs every kUFlush chunks into a per-CTA scratch tile, so no TMEM
+// accumulator sums more than 256 MMA steps.
 // Waits are bounded; on expiry the CTA records an error, lets its issued MMAs
 // drain (bounded), frees its TMEM and returns.
 constexpr int kUG = 256;          // G rows per CTA
@@ -163,6 +161,12 @@ constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 32 KB
 constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB
 constexpr uint32_t kUStaging = kUKT * kUN * 4;  // 64 KB of FP32 rows of A
 constexpr long long kUWait = 1LL << 24;
+// The tensor cores accumulate into TMEM in FP32 without round-to-nearest
+// (measured: relative error ~2^-24 per accumulated K = 16 step at m = 2^20);
+// every kUFlush chunks (256 steps) the accumulators are added, with
+// round-to-nearest, into the CTA's own FP32 tile in the workspace (L2-resident)
+// and restarted; the final epilogue adds that tile.
+constexpr int64_t kUFlush = 64;
 
 SNS_D uint32_t u_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 SNS_D uint32_t kmaj_off(int r, int k) { return (uint32_t)(((r >> 3) * kUKC + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2); }
@@ -217,7 +221,7 @@ template <bool BULK>
 __global__ void __launch_bounds__(kUThreads, 1)
 gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
            uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
-           int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int* __restrict__ err) {
+           int64_t ldsa, float* __restrict__ Sb, int64_t sbs, float* __restrict__ scratch, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t usm[];
   uint8_t* stA[2] = {usm, usm + kUStageA + kUStageB};
   uint8_t* stB[2] = {usm + kUStageA, usm + 2 * kUStageA + kUStageB};
@@ -262,6 +266,72 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   int64_t issued = 0;                                            // chunks whose MMAs were issued
   if (BULK && nchunks > 0 && warp == 0)
     stage_rows(staging, A, lda, col0, ncols, i_begin, (int)min((int64_t)kUKT, i_end - i_begin), &rows_ready);
+  // TMEM accumulators: periodic flushes add them into the CTA's scratch tile
+  // (layout [column block of 16][256 rows][16], so a warp's accesses are
+  // contiguous); the final flush adds the scratch tile, scales and reduces
+  // into SA (and the b column's register sums into Sb)
+  float* cta_scratch =
+      scratch ? scratch + (((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (kUG * kUN)
+              : nullptr;
+  int nflush = 0;
+  auto tmem_flush = [&](bool final_pass) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // 16 warps: warp w reads TMEM lanes of quadrant w mod 4 (the hardware
+    // rule), tile (w / 4) mod 2, and one half of the columns (w / 8)
+    const int quarter = warp & 3, mt = (warp >> 2) & 1, chalf = warp >> 3;
+    const int halfc = ((npad / 16 + 1) / 2) * 16;
+    const int cbeg = chalf ? halfc : 0, cend = chalf ? npad : halfc;
+    const int rloc = mt * 128 + quarter * 32 + lane;
+    const int64_t row = r_base + rloc;
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+      uint32_t vi[16];
+      const uint32_t a = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 256 + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
+            "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]),
+            "=r"(vi[15])
+          : "r"(a));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(vi[j]);
+      float4* sp = cta_scratch ? reinterpret_cast<float4*>(cta_scratch + ((c0 / 16) * kUG + rloc) * 16) : nullptr;
+      if (sp && nflush > 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 t = sp[j];
+          v[4 * j] += t.x; v[4 * j + 1] += t.y; v[4 * j + 2] += t.z; v[4 * j + 3] += t.w;
+        }
+      }
+      if (!final_pass) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        continue;
+      }
+      if (row < d) {
+        float* dst = SA + row * ldsa + col0 + c0;
+        if (c0 + 16 <= ncols && ((uintptr_t)dst & 15) == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j), "f"(v[j] * scale),
+                         "f"(v[j + 1] * scale), "f"(v[j + 2] * scale), "f"(v[j + 3] * scale)
+                         : "memory");
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < ncols) atomicAdd(dst + j, v[j] * scale);
+        }
+      }
+    }
+    if (final_pass) {
+      if (with_b && r_base + (tid & (kUG - 1)) < d)
+        atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, sb_acc * scale);
+    } else {
+      ++nflush;
+    }
+  };
+  int64_t c_acc0 = 0;                                            // first chunk since the last flush
   for (int64_t c = 0; c < nchunks; ++c) {
     const int s = (int)(c & 1);
     const int64_t u = c >> 1;                                    // use index of stage s
@@ -354,6 +424,17 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (cta_scratch && c > c_acc0 && (c - c_acc0) % kUFlush == 0) {
+      // chunks c_acc0 .. c - 1 are in TMEM: wait for their MMAs, add, restart
+      const int64_t cl = c - 1;
+      if (!u_wait(&mma_done[cl & 1], (uint32_t)((cl >> 1) & 1)) && lane == 0) atomicExch(&s_fail, 1);
+      __syncthreads();
+      if (s_fail) break;
+      tmem_flush(false);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      c_acc0 = c;
+    }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -362,7 +443,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
         for (int ks = 0; ks < kUKT / 16; ++ks) {
           const uint64_t ad = u_desc(u_smem(sA) + (uint32_t)mt * (kUStageA / 2) + (uint32_t)ks * 256u);
           const uint64_t bd = u_desc(u_smem(sB) + (uint32_t)ks * 256u);
-          const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+          const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr + (uint32_t)mt * 256u),
@@ -407,39 +488,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   if (!ok || s_fail) {
     if (tid == 0) atomicExch(err, 1);
   } else if (issued > 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // 16 warps: warp w reads TMEM lanes of quadrant w mod 4 (the hardware
-    // rule), tile (w / 4) mod 2, and one half of the columns (w / 8)
-    const int quarter = warp & 3, mt = (warp >> 2) & 1, chalf = warp >> 3;
-    const int halfc = ((npad / 16 + 1) / 2) * 16;
-    const int cbeg = chalf ? halfc : 0, cend = chalf ? npad : halfc;
-    const int64_t row = r_base + (int64_t)mt * 128 + quarter * 32 + lane;
-    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t a = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 256 + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(a));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < d) {
-        float* dst = SA + row * ldsa + col0 + c0;
-        if (c0 + 16 <= ncols && ((uintptr_t)dst & 15) == 0) {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j),
-                         "f"(__uint_as_float(v[j]) * scale), "f"(__uint_as_float(v[j + 1]) * scale),
-                         "f"(__uint_as_float(v[j + 2]) * scale), "f"(__uint_as_float(v[j + 3]) * scale)
-                         : "memory");
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < ncols) atomicAdd(dst + j, __uint_as_float(v[j]) * scale);
-        }
-      }
-    }
-    if (with_b && r_base + (tid & (kUG - 1)) < d) atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, sb_acc * scale);
+    tmem_flush(true);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -448,6 +497,34 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 
 size_t gauss_umma_smem(bool bulk) {
   return 2 * (size_t)(kUStageA + kUStageB) + (bulk ? kUStaging : 0) + 4096 * 2 + 2 * kUKT * 4;
+}
+
+// Launch shape of gauss_umma: row tiles of G x K splits x column tiles, one
+// CTA per SM; K ranges in whole chunks.
+struct GaussGrid {
+  int64_t mtiles, ntiles, ksplit, kchunk;
+};
+static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
+  GaussGrid g;
+  g.mtiles = (d + kUG - 1) / kUG;
+  g.ntiles = (n + kUN - 1) / kUN;
+  g.ksplit = std::max<int64_t>(1, (int64_t)num_sms() / std::max<int64_t>(1, g.mtiles * g.ntiles));
+  g.kchunk = (m + g.ksplit - 1) / g.ksplit;
+  g.kchunk = ((g.kchunk + kUKT - 1) / kUKT) * kUKT;
+  g.ksplit = (m + g.kchunk - 1) / g.kchunk;
+  return g;
+}
+// Scratch tiles (one 256 x 256 FP32 tile per CTA) when a CTA's K range is
+// longer than one flush period.
+static size_t gauss_scratch_bytes(int64_t m, int64_t n, int64_t d) {
+  const GaussGrid g = gauss_grid(m, n, d);
+  if (g.kchunk <= kUFlush * kUKT) return 0;
+  return (size_t)(g.mtiles * g.ksplit * g.ntiles) * kUG * kUN * 4;
+}
+constexpr size_t kGaussScratchOffset = 8192 + 256;
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
+  // the BF16 table (uploaded per call), an error word, the flush tiles
+  return kGaussScratchOffset + gauss_scratch_bytes(m, n, d);
 }
 
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
@@ -473,12 +550,11 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + gauss_err_offset());
   SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
   if (!use_simt) {
-    const int64_t mtiles = (d + kUG - 1) / kUG;
-    const int64_t ntiles = (a.n + kUN - 1) / kUN;
-    int64_t ksplit = std::max<int64_t>(1, (int64_t)num_sms() / std::max<int64_t>(1, mtiles * ntiles));
-    int64_t kchunk = (a.m + ksplit - 1) / ksplit;
-    kchunk = ((kchunk + kUKT - 1) / kUKT) * kUKT;
-    ksplit = (a.m + kchunk - 1) / kchunk;
+    const GaussGrid gg = gauss_grid(a.m, a.n, d);
+    const int64_t mtiles = gg.mtiles, ntiles = gg.ntiles, ksplit = gg.ksplit, kchunk = gg.kchunk;
+    float* scratch = gauss_scratch_bytes(a.m, a.n, d)
+                         ? reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + kGaussScratchOffset)
+                         : nullptr;
     const bool bulk = (a.n % 4 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.A % 16 == 0);
     auto kern = bulk ? gauss_umma<true> : gauss_umma<false>;
     SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
@@ -488,7 +564,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
       kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
           stream_state(seed, kStreamGaussian), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
-          err);
+          scratch, err);
     }
     SNS_CUDA_TRY(cudaGetLastError());
     return SNS_OK;
