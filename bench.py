@@ -126,31 +126,38 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        import datetime
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 10:
-                    continue
-                try:
-                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                except ValueError:
-                    continue
-                rows.append((ts, parts))
-        if not rows:
-            return None
-        t0 = self.t_mark if self.t_mark is not None else t_end
-        region = [p for ts, p in rows if t0 <= ts <= t_end]
-        use = region if region else [rows[-1][1]]
-        sm = [float(r[2]) for r in use if re.match(r"^[0-9.]+$", r[2])]
-        mx = [float(r[3]) for r in use if re.match(r"^[0-9.]+$", r[3])]
-        pw = [float(r[4]) for r in use if re.match(r"^[0-9.]+$", r[4])]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in use for i in range(4) if r[6 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(use), "samples_in_region": len(region),
-                "power_w_median": float(np.median(pw)) if pw else None, "source": "nvidia-smi, 40 ms period"}
+            return clock_summary(f.read().splitlines(), self.t_mark if self.t_mark is not None else t_end, t_end)
+
+
+def clock_summary(lines, t0, t1):
+    """Summary of nvidia-smi sample lines (ClockSampler.Q order, csv, no units)
+    taken in the wall-clock interval [t0, t1]: median SM clock, maximum clock,
+    the slowdown reasons seen, sample counts.  Falls back to the last sample
+    when none lies in the interval."""
+    import datetime
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            continue
+        rows.append((ts, parts))
+    if not rows:
+        return None
+    region = [p for ts, p in rows if t0 <= ts <= t1]
+    use = region if region else [rows[-1][1]]
+    sm = [float(r[2]) for r in use if re.match(r"^[0-9.]+$", r[2])]
+    mx = [float(r[3]) for r in use if re.match(r"^[0-9.]+$", r[3])]
+    pw = [float(r[4]) for r in use if re.match(r"^[0-9.]+$", r[4])]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in use for i in range(4) if r[6 + i].lower().startswith("active")})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(use), "samples_in_region": len(region),
+            "power_w_median": float(np.median(pw)) if pw else None, "source": "nvidia-smi, 40 ms period"}
 
 
 # ------------------------------------------------------------------ workload
