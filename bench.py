@@ -73,7 +73,8 @@ class ClockSampler:
     benchmark's own host thread is not slowed).  Each sample carries
     nvidia-smi's timestamp; the timed region's samples are those between mark()
     and stop().  Output is line-buffered (stdbuf) and nvidia-smi is stopped with
-    SIGINT so that no sample is lost."""
+    SIGINT so that no sample is lost.  The samples are kept in
+    $SNSOLVE_BENCH_OUT/clocks_rankN.csv (default: bench_out/ beside bench.py)."""
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -82,7 +83,8 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.t_mark = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        out = os.environ.get("SNSOLVE_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out, f"clocks_rank{device_index}.csv")
 
     def start(self):
         """Starts sampling and returns once the first sample is written, so
