@@ -14,7 +14,8 @@ it separately):
   seeded with state s0 is mix64(s0 + (i + 1) * gamma), so any output can be
   computed directly from its index (counter-based).
 * Stream separation: s0 = seed XOR (stream << 56), with stream 0 = CountSketch,
-  1 = SRHT signs, 2 = SRHT row sampling, 3 = Gaussian entries.
+  1 = SRHT signs, 2 = SRHT row sampling, 3 = Gaussian entries, 4 = the extra
+  draws of the sparse sign embedding.
 * Bucket of row i:  h(i) = ((k mod 2^32) * d) >> 32  (multiply-shift range
   reduction, Lemire 2019), k = output i of stream 0.
 * Sign of row i:  s(i) = -1 if bit 63 of k is set, else +1.
@@ -29,6 +30,7 @@ STREAM_COUNTSKETCH = 0
 STREAM_SRHT_SIGN = 1
 STREAM_SRHT_SAMPLE = 2
 STREAM_GAUSSIAN = 3
+STREAM_SPARSE_SIGN = 4
 
 
 def mix64(z):

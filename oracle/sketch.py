@@ -290,3 +290,55 @@ def srht_rows(A, d, seed, rows):
         h = 1.0 - 2.0 * _parity(i & np.uint64(P[r])).astype(np.float64)
         out.append((h * Ds) @ Af / math.sqrt(d))
     return np.array(out)
+
+# ---------------------------------------------------------------- sparse sign
+
+def sparse_sign_hash(m, d, zeta, seed):
+    """Rows (m x zeta, int64) and signs (m x zeta, +-1) of the sparse sign
+    embedding (Sec. 1.2.2, after Martinsson & Tropp 2020): column i of S holds
+    zeta nonzeros +-1/sqrt(zeta) at distinct rows.
+
+    Draw z = 0..zeta-1 of column i uses key k_z: output i of stream 0 for z = 0
+    (so zeta = 1 is the CountSketch), output i*(zeta-1) + z-1 of stream 4 for
+    z >= 1.  The rows follow Floyd's algorithm on [0, d): draw z considers
+    [0, J], J = d - zeta + z, takes u = ((k_z mod 2^32) * (J + 1)) >> 32, and
+    keeps u unless an earlier draw of the column took it, in which case it keeps
+    J.  The sign of draw z is -1 iff bit 63 of k_z is set."""
+    assert 1 <= zeta <= d
+    i = np.arange(m, dtype=np.uint64)
+    rows = np.zeros((m, zeta), dtype=np.int64)
+    signs = np.zeros((m, zeta))
+    for z in range(zeta):
+        if z == 0:
+            k = H.splitmix64_at(H.stream_state(seed, H.STREAM_COUNTSKETCH), i)
+        else:
+            k = H.splitmix64_at(H.stream_state(seed, H.STREAM_SPARSE_SIGN),
+                                i * np.uint64(zeta - 1) + np.uint64(z - 1))
+        J = d - zeta + z
+        with np.errstate(over="ignore"):
+            u = (((k & np.uint64(0xFFFFFFFF)) * np.uint64(J + 1)) >> np.uint64(32)).astype(np.int64)
+        taken = np.zeros(m, dtype=bool)
+        for zz in range(z):
+            taken |= rows[:, zz] == u
+        rows[:, z] = np.where(taken, J, u)
+        signs[:, z] = H.sign_of(k)
+    return rows, signs
+
+
+def sparse_sign_matrix(m, d, zeta, seed):
+    """Dense sparse sign embedding S (d x m, FP64)."""
+    rows, signs = sparse_sign_hash(m, d, zeta, seed)
+    S = np.zeros((d, m))
+    for z in range(zeta):
+        S[rows[:, z], np.arange(m)] = signs[:, z] / math.sqrt(zeta)
+    return S
+
+
+def sparse_sign_apply(A, d, zeta, seed):
+    """SA by scattering every row into its zeta rows of S (FP64)."""
+    A = np.asarray(A, dtype=np.float64)
+    rows, signs = sparse_sign_hash(A.shape[0], d, zeta, seed)
+    out = np.zeros((d,) + A.shape[1:])
+    for z in range(zeta):
+        np.add.at(out, rows[:, z], (signs[:, z] / math.sqrt(zeta)).reshape((-1,) + (1,) * (A.ndim - 1)) * A)
+    return out

@@ -171,3 +171,46 @@ def test_single_row_forms_equal_the_full_sketches(m, n, d):
     assert np.allclose(S.srht_rows(A, d, 6, rows), S.srht_apply(A, d, 6)[rows], rtol=0, atol=1e-12)
     b = rng.standard_normal(m)
     assert np.allclose(S.srht_rows(b, d, 6, rows), S.srht_apply(b, d, 6)[rows], rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- sparse sign embedding
+
+def test_sparse_sign_zeta1_is_the_countsketch():
+    """With one nonzero per column the embedding is the CountSketch itself."""
+    A = np.random.default_rng(1).standard_normal((3000, 4))
+    assert np.array_equal(S.sparse_sign_apply(A, 77, 1, 9), S.countsketch_apply(A, 77, 9))
+
+
+@pytest.mark.parametrize("zeta,d", [(2, 16), (4, 64), (8, 8), (3, 1000)])
+def test_sparse_sign_structure(zeta, d):
+    """Each column: exactly zeta nonzeros +-1/sqrt(zeta), at distinct rows; the
+    scatter form equals the dense product."""
+    m = 700
+    Sm = S.sparse_sign_matrix(m, d, zeta, 4)
+    nz = Sm != 0
+    assert np.all(nz.sum(axis=0) == zeta)
+    assert np.allclose(np.abs(Sm[nz]), 1 / math.sqrt(zeta))
+    A = np.random.default_rng(zeta).standard_normal((m, 3))
+    assert np.allclose(S.sparse_sign_apply(A, d, zeta, 4), Sm @ A, rtol=0, atol=1e-13)
+
+
+def test_sparse_sign_rows_uniform_over_subsets():
+    """Floyd's algorithm picks every zeta-subset of [0, d) with equal
+    probability: d = 5, zeta = 2 gives 10 subsets, chi-square over 50000
+    columns; the signs are balanced and independent of the rows."""
+    from itertools import combinations
+    rows, signs = S.sparse_sign_hash(50000, 5, 2, 11)
+    keys = [tuple(sorted(r)) for r in rows]
+    subsets = list(combinations(range(5), 2))
+    counts = np.array([keys.count(c) for c in subsets], dtype=float)
+    exp = 50000 / len(subsets)
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 27.9          # 9 degrees of freedom, p = 0.001
+    assert abs(signs.mean()) < 0.02
+
+
+def test_sparse_sign_isometry_in_expectation():
+    """E ||S x||^2 = ||x||^2 (each column has zeta entries of square 1/zeta)."""
+    x = np.random.default_rng(3).standard_normal(400)
+    vals = [np.linalg.norm(S.sparse_sign_apply(x, 32, 4, seed)) ** 2 for seed in range(300)]
+    assert abs(np.mean(vals) / np.linalg.norm(x) ** 2 - 1) < 0.05
