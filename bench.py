@@ -708,6 +708,7 @@ def run_sketches(args):
     out = {}
     for name, kind, variant in [("countsketch_sorted", "countsketch", "sorted"),
                                 ("countsketch_stream", "countsketch", "stream"),
+                                ("sparse_sign_zeta4", "sparse_sign", 4),
                                 ("gaussian_tcgen05", "gaussian", "auto"), ("srht", "srht", "auto")]:
         prob = sns.dense_problem(A, b)
         sk = sns.sketch_desc(D, kind, SKETCH_SEED, variant)

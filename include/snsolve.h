@@ -55,11 +55,13 @@ typedef enum {
 typedef enum {
   SNS_COUNTSKETCH = 0,  /* S[h(i), i] = s(i): one signed nonzero per column */
   SNS_GAUSSIAN = 1,     /* S = G / sqrt(d), G from a BF16 normal-quantile table */
-  SNS_SRHT = 2          /* S = P H D / sqrt(d) on m' = 2^ceil(log2 m) rows */
+  SNS_SRHT = 2,         /* S = P H D / sqrt(d) on m' = 2^ceil(log2 m) rows */
+  SNS_SPARSE_SIGN = 3   /* zeta nonzeros +-1/sqrt(zeta) per column at distinct rows (Sec. 1.2.2,
+                           after Martinsson & Tropp 2020); zeta = variant, 1..min(8, d); dense FP32
+                           only; one streaming pass with float reductions (order varies) */
 } sns_sketch_kind;
 
-/* Storage of A (the paper handles dense and sparse A through one interface,
- * Sec. 2.1). */
+/* Storage of A (one entry point serves dense and sparse A, Sec. 2.1). */
 typedef enum {
   SNS_DENSE_F32 = 0,    /* A float, row-major, lda >= n; b float */
   SNS_DENSE_F64 = 1,    /* A double, row-major, lda >= n; b double */
@@ -84,10 +86,14 @@ typedef enum {
  * SRHT: signs from t = 1, d distinct rows of [0, m') by Floyd's algorithm on t = 2.
  * Gaussian: G[k, i] = T[top 12 bits of 16-bit field (k div 8) mod 4 of output
  * i*G + 8*(k div 32) + (k mod 8) of t = 3], G = 8*ceil(d/32),
- * T[j] = BF16(Phi^-1((j + 1/2)/4096)). */
+ * T[j] = BF16(Phi^-1((j + 1/2)/4096)).
+ * Sparse sign: draw z of column i uses output i of t = 0 (z = 0; zeta = 1 is the
+ * CountSketch) or output i*(zeta-1) + z-1 of t = 4; rows by Floyd's algorithm on
+ * [0, d): u = ((k mod 2^32)*(J+1)) >> 32 with J = d - zeta + z, or J if an earlier
+ * draw of the column took u; the sign of draw z is bit 63 of its key. */
 typedef struct {
   int32_t kind;        /* sns_sketch_kind */
-  int32_t variant;     /* sns_cs_variant (CountSketch only; ignored otherwise) */
+  int32_t variant;     /* sns_cs_variant for CountSketch; zeta for SNS_SPARSE_SIGN; ignored otherwise */
   int64_t d;           /* sketch rows, n <= d; SRHT also d <= m' */
   uint64_t seed;
 } sns_sketch_desc;

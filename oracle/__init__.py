@@ -9,7 +9,7 @@ What it computes follows "Sketch 'n Solve" (arXiv 2409.14309):
 
 * the least-squares problem  min_x ||A x - b||^2  (Eq. 1, Sec. 1.3);
 * the reduced problem  min ||S A x^ - S b||^2  with S in R^{d x m} (Sec. 1.3);
-* the three-step paradigm: generate S, form SA and Sb, solve on SA (Sec. 1.2);
+* the method's steps: generate S, form SA and Sb, solve on SA (Sec. 1.2);
 * the sketch families the paper names: Clarkson-Woodruff / CountSketch (the
   default, Sec. 1.2.2), Gaussian and subsampled randomized Hadamard (Sec. 1.2.1);
 * sketch-and-precondition (SAP-SAS, Sec. 2.1), whose fixed point is the exact

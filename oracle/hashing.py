@@ -1,8 +1,8 @@
 """Counter-based random streams that define the implicit sketch S (step "generate S",
 Sec. 1.2 of the paper).  TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The paper says only that the Clarkson-Woodruff sketch combines a sparse matrix
-with a random sign matrix (Sec. 1.2.2); it fixes no generator.  Reading used
+The paper describes the Clarkson-Woodruff sketch only as sparse with random
+signs (Sec. 1.2.2); it fixes no generator.  Reading used
 here (shared, as a specification only, with the CUDA library, which implements
 it separately):
 

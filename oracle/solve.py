@@ -1,7 +1,7 @@
 """Solvers of the oracle, FP64.  TEST INFRASTRUCTURE ONLY.
 
-* Householder QR and back substitution: the "existing algorithms" that solve the
-  reduced problem min ||SA x^ - Sb||^2 (Sec. 1.2 step 3, Sec. 1.3).  Written out
+* Householder QR and back substitution: standard solvers for the reduced
+  problem min ||SA x^ - Sb||^2 (Sec. 1.2 step 3, Sec. 1.3).  Written out
   column by column: no blocking, no pivoting.
 * Sketch-and-solve: QR of the augmented matrix [SA | Sb] (d x (n+1)).  Its R has
   R[:n, :n] = R, R[:n, n] = z = (Q^T Sb)[:n] and |R[n, n]| = ||SA x^ - Sb||.

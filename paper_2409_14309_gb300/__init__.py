@@ -10,10 +10,10 @@ import ctypes as C
 import torch
 
 from . import abi
-from .abi import (SNS_COUNTSKETCH, SNS_GAUSSIAN, SNS_SRHT, SNS_CS_AUTO, SNS_CS_SORTED, SNS_CS_STREAM,
+from .abi import (SNS_COUNTSKETCH, SNS_GAUSSIAN, SNS_SRHT, SNS_SPARSE_SIGN, SNS_CS_AUTO, SNS_CS_SORTED, SNS_CS_STREAM,
                   SNS_DENSE_F32, SNS_DENSE_F64, SNS_CSR_F32, status_name)
 
-KIND = {"countsketch": SNS_COUNTSKETCH, "gaussian": SNS_GAUSSIAN, "srht": SNS_SRHT}
+KIND = {"countsketch": SNS_COUNTSKETCH, "gaussian": SNS_GAUSSIAN, "srht": SNS_SRHT, "sparse_sign": SNS_SPARSE_SIGN}
 VARIANT = {"auto": SNS_CS_AUTO, "sorted": SNS_CS_SORTED, "stream": SNS_CS_STREAM}
 
 
@@ -61,7 +61,14 @@ def csr_problem(rowptr, col, val, b, n):
 
 
 def sketch_desc(d, kind="countsketch", seed=0, variant="auto"):
-    return abi.sns_sketch_desc(kind=KIND[kind], variant=VARIANT[variant], d=int(d), seed=int(seed) & (2**64 - 1))
+    """Sketch descriptor.  For CountSketch `variant` is "auto", "sorted" or
+    "stream"; for the sparse sign embedding it is zeta, the nonzeros per column
+    (an int 1..8; "auto" means 4)."""
+    if kind == "sparse_sign":
+        v = 4 if variant == "auto" else int(variant)
+    else:
+        v = VARIANT[variant]
+    return abi.sns_sketch_desc(kind=KIND[kind], variant=v, d=int(d), seed=int(seed) & (2**64 - 1))
 
 
 def opts(d, kind="countsketch", seed=0, variant="auto", tol=0.0, max_iter=0, inner=0, precondition=True):

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libsnsolve.so")
 
 # enums
 SNS_OK, SNS_EINVAL, SNS_ENOMEM, SNS_ERANK, SNS_ENOTCONV, SNS_EAGAIN, SNS_ETIMEOUT, SNS_ECUDA, SNS_EBUDGET = range(9)
-SNS_COUNTSKETCH, SNS_GAUSSIAN, SNS_SRHT = range(3)
+SNS_COUNTSKETCH, SNS_GAUSSIAN, SNS_SRHT, SNS_SPARSE_SIGN = range(4)
 SNS_DENSE_F32, SNS_DENSE_F64, SNS_CSR_F32 = range(3)
 SNS_CS_AUTO, SNS_CS_SORTED, SNS_CS_STREAM = range(3)
 

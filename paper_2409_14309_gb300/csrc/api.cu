@@ -138,6 +138,10 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
       if (p->fmt == SNS_CSR_F32) return SNS_EINVAL;
       if (sk->d > next_pow2(p->m) || next_pow2(p->m) >= ((int64_t)1 << 31)) return SNS_EINVAL;
       return SNS_OK;
+    case SNS_SPARSE_SIGN:
+      if (p->fmt != SNS_DENSE_F32) return SNS_EINVAL;
+      if (sk->variant < 1 || sk->variant > 8 || sk->variant > sk->d) return SNS_EINVAL;
+      return SNS_OK;
     default:
       return SNS_EINVAL;
   }
@@ -164,6 +168,8 @@ static size_t sketch_ws(const sns_problem* p, const sns_sketch_desc* sk) {
       return gauss_ws_bytes(p->m, p->n, sk->d);
     case SNS_SRHT:
       return srht_ws_bytes(p->m, p->n, sk->d, is_f64(p));
+    case SNS_SPARSE_SIGN:
+      return 0;
   }
   return 0;
 }
@@ -197,6 +203,9 @@ static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, vo
                                ws_bytes, st);
     case SNS_SRHT:
       return srht_apply_dense(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, ws, ws_bytes, st);
+    case SNS_SPARSE_SIGN:
+      return cs_apply_sparse_sign(da, sk->d, sk->variant, sk->seed, static_cast<float*>(SA), ldsa,
+                                  static_cast<float*>(Sb), sbs, st);
   }
   return SNS_EINVAL;
 }

@@ -18,7 +18,13 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kMul1 = 0xBF58476D1CE4E5B9ull;
 constexpr uint64_t kMul2 = 0x94D049BB133111EBull;
 
-enum Stream : uint64_t { kStreamCountSketch = 0, kStreamSrhtSign = 1, kStreamSrhtSample = 2, kStreamGaussian = 3 };
+enum Stream : uint64_t {
+  kStreamCountSketch = 0,
+  kStreamSrhtSign = 1,
+  kStreamSrhtSample = 2,
+  kStreamGaussian = 3,
+  kStreamSparseSign = 4      // draws 1.. of the sparse sign embedding
+};
 
 SNS_HD uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * kMul1;

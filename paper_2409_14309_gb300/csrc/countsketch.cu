@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "prof.h"
@@ -511,6 +513,84 @@ cs_stream_dense(const float* __restrict__ A, int64_t lda, const float* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Sparse sign embedding (Sec. 1.2.2, after Martinsson & Tropp 2020), dense
+// FP32: column i of S holds zeta nonzeros +-1/sqrt(zeta) at distinct rows.
+// Draw z of row i uses output i of stream 0 (z = 0, so zeta = 1 is the
+// CountSketch) or output i*(zeta-1) + z-1 of stream 4; the rows follow Floyd's
+// algorithm on [0, d) (draw z takes u = ((k mod 2^32) * (J + 1)) >> 32,
+// J = d - zeta + z, or J if an earlier draw of the row took u) and the sign of
+// draw z is bit 63 of its key.  One streaming pass: each warp takes kSseRows
+// rows at a time and adds every row into its zeta rows of SA with vector
+// reductions.  SA and Sb must be zeroed.
+constexpr int kSseMaxZeta = 8;
+constexpr int kSseRows = 2;
+template <int VEC>
+__global__ void __launch_bounds__(256)
+cs_sparse_sign_dense(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
+                     uint32_t d, int zeta, uint64_t s0, uint64_t s4, float scale, float* __restrict__ SA,
+                     int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = gw * kSseRows; r0 < m; r0 += nw * kSseRows) {
+    uint32_t h[kSseRows][kSseMaxZeta];
+    float sg[kSseRows][kSseMaxZeta];
+#pragma unroll
+    for (int u = 0; u < kSseRows; ++u) {
+      const uint64_t row = (uint64_t)(r0 + u < m ? r0 + u : 0);
+#pragma unroll
+      for (int z = 0; z < kSseMaxZeta; ++z) {
+        h[u][z] = 0u;
+        sg[u][z] = 0.f;
+        if (z < zeta) {
+          const uint64_t key = z == 0 ? splitmix_at(s0, row) : splitmix_at(s4, row * (uint64_t)(zeta - 1) + (z - 1));
+          const uint32_t J = d - (uint32_t)zeta + (uint32_t)z;
+          const uint32_t cand = (uint32_t)(((key & 0xFFFFFFFFull) * ((uint64_t)J + 1)) >> 32);
+          bool taken = false;
+#pragma unroll
+          for (int zz = 0; zz < z; ++zz) taken = taken || (h[u][zz] == cand);
+          h[u][z] = taken ? J : cand;
+          sg[u][z] = (key >> 63) ? -scale : scale;
+        }
+      }
+    }
+    for (int64_t c0 = (int64_t)lane * VEC; c0 < n; c0 += 32 * VEC) {
+      float x[kSseRows][VEC];
+#pragma unroll
+      for (int u = 0; u < kSseRows; ++u)
+        if (r0 + u < m) load_vec<float, VEC>(A + (r0 + u) * lda + c0, x[u]);
+#pragma unroll
+      for (int u = 0; u < kSseRows; ++u) {
+        if (r0 + u >= m) continue;
+#pragma unroll
+        for (int z = 0; z < kSseMaxZeta; ++z) {
+          if (z >= zeta) break;
+          float* dst = SA + (int64_t)h[u][z] * ldsa + c0;
+          const float f = sg[u][z];
+          if constexpr (VEC == 4) {
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(f * x[u][0]),
+                         "f"(f * x[u][1]), "f"(f * x[u][2]), "f"(f * x[u][3])
+                         : "memory");
+          } else {
+            atomicAdd(dst, f * x[u][0]);
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kSseRows; ++u) {
+        if (r0 + u >= m) continue;
+        const float bv = __ldg(b + r0 + u);
+#pragma unroll
+        for (int z = 0; z < kSseMaxZeta; ++z)
+          if (z < zeta) atomicAdd(Sb + (int64_t)h[u][z] * sbs, sg[u][z] * bv);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 static int g_num_sms = 0;
 int num_sms() {
@@ -737,6 +817,38 @@ sns_status cs_apply_csr_stream(const CsrArgs& a, int64_t d, uint64_t seed, float
     SNS_PROF(K_CS_CSR, st);
     cs_stream_csr<<<grid, 256, 0, st>>>(a.rowptr, a.col, a.val, a.b, a.m, a.n, (uint32_t)d,
                                        stream_state(seed, kStreamCountSketch), SA, ldsa, Sb, sbs);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+sns_status cs_apply_sparse_sign(const DenseArgs& a, int64_t d, int zeta, uint64_t seed, float* SA, int64_t ldsa,
+                                float* Sb, int64_t sbs, cudaStream_t st) {
+  if (a.f64 || zeta < 1 || zeta > kSseMaxZeta || zeta > d) return SNS_EINVAL;
+  if (ldsa == a.n) {
+    SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
+  }
+  if (sbs == 1) {
+    SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
+  }
+  const bool v4 = (a.lda % 4 == 0) && (ldsa % 4 == 0) && (a.n % 4 == 0) && aligned(a.A, 16) && aligned(SA, 16);
+  const uint64_t s0 = stream_state(seed, kStreamCountSketch), s4 = stream_state(seed, kStreamSparseSign);
+  const float scale = (float)(1.0 / std::sqrt((double)zeta));
+  const int grid = num_sms() * 8;
+  {
+    SNS_PROF(K_CS_STREAM, st);
+    if (v4)
+      cs_sparse_sign_dense<4><<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda,
+                                                    static_cast<const float*>(a.b), a.m, a.n, (uint32_t)d, zeta, s0,
+                                                    s4, scale, SA, ldsa, Sb, sbs);
+    else
+      cs_sparse_sign_dense<1><<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda,
+                                                    static_cast<const float*>(a.b), a.m, a.n, (uint32_t)d, zeta, s0,
+                                                    s4, scale, SA, ldsa, Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;

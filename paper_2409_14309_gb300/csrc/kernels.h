@@ -42,6 +42,9 @@ int num_sms();
 
 sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
                                  int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+// Sparse sign embedding, dense FP32 (1 <= zeta <= min(8, d)); zeroes SA and Sb.
+sns_status cs_apply_sparse_sign(const DenseArgs& a, int64_t d, int zeta, uint64_t seed, float* SA, int64_t ldsa,
+                                float* Sb, int64_t sbs, cudaStream_t st);
 sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
                                  int64_t sbs, cudaStream_t st);
 // Streaming CountSketch on CSR (one pass, float reductions into SA; SA and Sb

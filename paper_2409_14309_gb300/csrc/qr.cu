@@ -1,6 +1,6 @@
 // FP64 Householder QR of the sketched augmented matrix [SA | Sb] (d x (n+1)) and
-// the triangular solves of sketch-and-solve (Sec. 1.2 step 3: "solve on SA
-// using existing algorithms"; the reduced problem of Sec. 1.3).
+// the triangular solves of sketch-and-solve (Sec. 1.2 step 3, which leaves the
+// small problem to standard solvers; the reduced problem of Sec. 1.3).
 //
 // R_aug = the (n+1) x (n+1) triangular factor of [SA | Sb]: its leading n x n
 // block is R, its last column holds z = (Q^T Sb)[0:n], and |R_aug[n, n]| is the

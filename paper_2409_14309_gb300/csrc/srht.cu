@@ -1,5 +1,5 @@
-// Subsampled randomized Hadamard sketch (Sec. 1.2.1: Hadamard sketches built
-// from normalized Hadamard matrices and applied by the fast Hadamard transform):
+// Subsampled randomized Hadamard sketch (Sec. 1.2.1; a Hadamard-based sketch
+// applied with a fast transform):
 //   S [A | b] = (1/sqrt(d)) P H_{m'} D [A | b],   m' = 2^ceil(log2 m),
 // H unnormalised Sylvester-Hadamard (H[p, i] = (-1)^popcount(p & i)), D the
 // signs of stream 1, P the d rows of [0, m') chosen by Floyd's algorithm on

@@ -1,5 +1,5 @@
-"""SRHT apply on the GPU vs the FP64 oracle (Sec. 1.2.1: normalized Hadamard
-sketch applied by the fast transform, S = (1/sqrt(d)) P H D on [A | b] padded
+"""SRHT apply on the GPU vs the FP64 oracle (Sec. 1.2.1: Hadamard-based sketch
+with a fast transform, S = (1/sqrt(d)) P H D on [A | b] padded
 to m' = 2^ceil(log2 m) rows).  SA and Sb within ||SA_gpu - SA_ref||_F /
 ||[A | b]||_F <= 1e-6 for FP32 data (1e-13 for FP64 data).  Each output row is
 a signed sum over all m' rows, so a wrong sampled row or sign shows up as an
