@@ -79,9 +79,17 @@ def test_workspace_queries_and_validation(lib):
         (_prob(), abi.sns_sketch_desc(kind=9, d=40)),          # bad kind
         (_prob(fmt=1), abi.sns_sketch_desc(kind=1, d=40)),     # Gaussian needs FP32
         (_prob(m=100), abi.sns_sketch_desc(kind=2, d=200)),    # SRHT d > m'
+        (_prob(), abi.sns_sketch_desc(kind=3, variant=9, d=40)),   # sparse sign: zeta > 8
+        (_prob(), abi.sns_sketch_desc(kind=3, variant=0, d=40)),   # sparse sign: zeta < 1
+        (_prob(n=4), abi.sns_sketch_desc(kind=3, variant=6, d=5)),  # sparse sign: zeta > d
+        (_prob(fmt=1), abi.sns_sketch_desc(kind=3, variant=2, d=40)),  # sparse sign needs FP32 dense
     ]
     for p, s in bad:
         assert lib.snsolve_sketch_workspace_size(C.byref(p), C.byref(s), C.byref(sz)) == 1
+    # the sparse sign embedding streams: no workspace
+    sse = abi.sns_sketch_desc(kind=3, variant=8, d=40, seed=1)
+    assert lib.snsolve_sketch_workspace_size(C.byref(_prob()), C.byref(sse), C.byref(sz)) == 0
+    assert sz.value == 0
     op = abi.sns_opts(sk=sk, tol=1e-8)
     assert lib.snsolve_lstsq_workspace_size(C.byref(_prob()), C.byref(op), C.byref(sz)) == 0
     with_iter = sz.value
