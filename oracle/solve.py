@@ -192,3 +192,27 @@ def sketch_and_precondition(A, b, SA, Sb, tol=1e-14, max_iter=1000):
     xhat, R, _ = sketch_and_solve(SA, Sb)
     x, it, est = lsqr_preconditioned(A, b, R, xhat, tol=tol, max_iter=max_iter)
     return x, it, est, xhat
+
+
+def apply_inverse_r(A, R):
+    """Y = A R^{-1} formed explicitly (the "apply" of sketch-and-apply), column
+    by column from Y R = A: Y[:, j] = (A[:, j] - Y[:, :j] R[:j, j]) / R[j, j]."""
+    A = np.asarray(A, dtype=np.float64)
+    n = R.shape[0]
+    Y = np.zeros_like(A)
+    for j in range(n):
+        Y[:, j] = (A[:, j] - Y[:, :j] @ R[:j, j]) / R[j, j]
+    return Y
+
+
+def sketch_and_apply(A, b, SA, Sb, tol=1e-14, max_iter=1000):
+    """SAA-SAS (named in Sec. 2.1 beside SAP-SAS; after Meier, Nakatsukasa,
+    Townsend & Webb 2023): R from the QR of SA, Y = A R^{-1} formed explicitly,
+    LSQR on min ||Y z - b|| started at z0 = R x^ (x^ the sketch-and-solve
+    solution), and x = R^{-1} z.  Returns x, the iteration count, LSQR's
+    estimate of ||Y^T r|| / (||Y||_F ||r||) and x^."""
+    xhat, R, _ = sketch_and_solve(SA, Sb)
+    n = R.shape[0]
+    Y = apply_inverse_r(A, R)
+    z, it, est = lsqr_preconditioned(Y, b, np.eye(n), R @ xhat, tol=tol, max_iter=max_iter)
+    return back_solve(R, z), it, est, xhat

@@ -129,3 +129,46 @@ def test_sap_fixed_point_is_exact_solution_ill_conditioned():
     # preconditioned LSQR needs far fewer iterations than plain LSQR here
     _, it_plain, _ = L.lsqr_preconditioned(A, b, np.eye(20), xhat, tol=1e-10, max_iter=200)
     assert it < it_plain
+
+
+# ---------------------------------------------------------------- sketch-and-apply (SAA-SAS)
+
+def test_apply_inverse_r_reconstructs_and_matches_triangular_solve():
+    from scipy.linalg import solve_triangular
+    A, _, _ = gaussian_problem(400, 9, seed=21)
+    _, R, _ = L.sketch_and_solve(S.countsketch_apply(A, 40, 3), S.countsketch_apply(np.ones(400), 40, 3))
+    Y = L.apply_inverse_r(A, R)
+    assert np.allclose(Y @ R, A, rtol=0, atol=1e-12 * np.abs(A).max())
+    # Y^T = R^{-T} A^T by the library's triangular solve
+    assert np.allclose(Y, solve_triangular(R, A.T, trans="T").T, rtol=1e-12, atol=1e-13)
+
+
+def test_saa_fixed_point_is_exact_solution_ill_conditioned():
+    A, b, _ = ill_conditioned_problem(3000, 20, seed=22, kappa=1e8, noise=1e-4, dtype=np.float64)
+    x_star, _ = L.exact_lstsq(A, b)
+    SA, Sb = S.countsketch_apply(A, 80, 1), S.countsketch_apply(b, 80, 1)
+    x, it, est, xhat = L.sketch_and_apply(A, b, SA, Sb, tol=1e-15, max_iter=200)
+    assert np.linalg.norm(x - x_star) / np.linalg.norm(x_star) < 1e8 * 1e-14
+    xr = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert L.eta(A, b, x) < 10 * L.eta(A, b, xr) + 1e-14
+
+
+def test_saa_iterates_equal_sap_iterates():
+    """LSQR on the explicit Y = A R^{-1} from z0 = R x^ and LSQR on the implicit
+    A R^{-1} from x^ build the same Krylov iterates: mapped back, the k-th
+    iterates agree (up to rounding at this moderate conditioning)."""
+    A, b, _ = ill_conditioned_problem(2000, 15, seed=23, kappa=1e3, noise=1e-2, dtype=np.float64)
+    SA, Sb = S.countsketch_apply(A, 60, 2), S.countsketch_apply(b, 60, 2)
+    for k in (1, 2, 5):
+        xa, ita, _, _ = L.sketch_and_apply(A, b, SA, Sb, tol=0.0, max_iter=k)
+        xp, itp, _, _ = L.sketch_and_precondition(A, b, SA, Sb, tol=0.0, max_iter=k)
+        assert ita == itp == k
+        assert np.linalg.norm(xa - xp) / np.linalg.norm(xp) < 1e-10
+
+
+def test_saa_preconditioned_matrix_is_well_conditioned():
+    """With d = 4n the sketch keeps the singular values of A R^{-1} near 1
+    (subspace embedding): kappa(Y) stays small whatever kappa(A) is."""
+    A, _, _ = ill_conditioned_problem(4000, 16, seed=24, kappa=1e8, noise=0.0, dtype=np.float64)
+    _, R, _ = L.sketch_and_solve(S.countsketch_apply(A, 64, 5), S.countsketch_apply(np.ones(4000), 64, 5))
+    assert np.linalg.cond(L.apply_inverse_r(A, R)) < 6.0
