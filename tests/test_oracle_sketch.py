@@ -160,11 +160,17 @@ def test_srht_isometry_in_expectation():
 @pytest.mark.parametrize("m,n,d", [(1000, 5, 64), (4097, 3, 100)])
 def test_single_row_forms_equal_the_full_sketches(m, n, d):
     """The one-row-at-a-time forms used to check full-size GPU results give the
-    same rows as the full Gaussian and SRHT sketches (themselves pinned above:
-    index layout, table quantiles, fast transform = dense product)."""
+    same rows as the full CountSketch, Gaussian and SRHT sketches (themselves
+    pinned above: dense product = scatter, index layout, table quantiles, fast
+    transform = dense product)."""
     rng = np.random.default_rng(m)
     A = rng.standard_normal((m, n))
     rows = [0, 1, d // 2, d - 1]
+    assert np.allclose(S.countsketch_rows(A, d, 4, rows), (S.countsketch_matrix(m, d, 4) @ A)[rows],
+                       rtol=0, atol=1e-12)
+    bb = rng.standard_normal(m)
+    assert np.allclose(S.countsketch_rows(bb, d, 4, rows), (S.countsketch_matrix(m, d, 4) @ bb)[rows],
+                       rtol=0, atol=1e-12)
     assert np.allclose(S.gaussian_rows(A, d, 5, rows), S.gaussian_apply(A, d, 5)[rows], rtol=0, atol=1e-12)
     assert np.allclose(S.gaussian_rows(A, d, 5, rows, bf16_operand=False),
                        S.gaussian_apply(A, d, 5, bf16_operand=False)[rows], rtol=0, atol=1e-12)

@@ -107,6 +107,60 @@ def test_eta_zero_at_solution_and_positive_elsewhere():
     assert L.eta(A, b, x + 1e-3) > 1e-6
 
 
+def test_eta_hand_computed_values():
+    """eta = ||A^T r|| / (||A||_F ||r||) on a 3 x 2 problem worked by hand:
+    A = [[3, 0], [0, 4], [0, 0]] has ||A||_F = 5; with b = (1, 1, 1):
+    x = 0 gives r = b, A^T r = (3, 4): eta = 5 / (5 sqrt 3);
+    x = (0, 1/4) gives r = (1, 0, 1), A^T r = (3, 0): eta = 3 / (5 sqrt 2);
+    x = (1/3, 1/4) is x* (r = (0, 0, 1) is orthogonal to range(A)): eta = 0."""
+    A = np.array([[3.0, 0.0], [0.0, 4.0], [0.0, 0.0]])
+    b = np.ones(3)
+    assert np.isclose(L.eta(A, b, np.zeros(2)), 1 / np.sqrt(3), rtol=1e-15)
+    assert np.isclose(L.eta(A, b, np.array([0.0, 0.25])), 3 / (5 * np.sqrt(2)), rtol=1e-15)
+    assert L.eta(A, b, np.array([1 / 3, 0.25])) < 1e-16
+
+
+def test_eta_closed_form_scaled_orthonormal_columns():
+    """A = c Q with Q^T Q = I (n columns), so ||A||_F = c sqrt(n).  With
+    b = A x + p + Q w, p orthogonal to range(Q): r = p + Q w, A^T r = c w, so
+    eta(x) = ||w|| / (sqrt(n) sqrt(||p||^2 + ||w||^2)), whatever c is.  Dividing
+    by ||A||_2 instead of ||A||_F, or by ||r||^2, changes the value."""
+    rng = np.random.default_rng(31)
+    m, n = 60, 4
+    Q, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    z = rng.standard_normal(m)
+    p = z - Q @ (Q.T @ z)
+    p *= 4.0 / np.linalg.norm(p)                     # ||p|| = 4
+    w = np.array([1.0, 2.0, 2.0, 0.0])               # ||w|| = 3
+    x = rng.standard_normal(n)
+    for c in (1.0, 7.5, 1e-3):
+        A = c * Q
+        b = A @ x + p + Q @ w
+        assert np.isclose(L.eta(A, b, x), 3.0 / (2.0 * 5.0), rtol=1e-12)   # 3 / (sqrt(4) * 5)
+
+
+def test_eta_scale_invariance():
+    """eta is a relative measure: scaling A and b together, or b and x
+    together, leaves it unchanged (a squared norm anywhere would not)."""
+    A, b, _ = gaussian_problem(300, 8, seed=32, noise=0.2)
+    x = np.random.default_rng(33).standard_normal(8)
+    e = L.eta(A, b, x)
+    assert np.isclose(L.eta(9.0 * A, 9.0 * b, x), e, rtol=1e-12)
+    assert np.isclose(L.eta(A, 0.01 * b, 0.01 * x), e, rtol=1e-12)
+
+
+def test_eta_matches_scipy_lsqr_recurrence():
+    """SciPy's LSQR carries ||A^T r_k|| (arnorm) and ||r_k|| (r1norm) of its
+    iterate through its own recurrences; at that iterate they give the same
+    eta as the oracle's direct computation."""
+    A, b, _ = gaussian_problem(400, 10, seed=34, noise=0.5)
+    fro = np.sqrt(np.sum(A * A))
+    for k in (2, 4, 7):
+        out = scipy_lsqr(A, b, atol=0, btol=0, iter_lim=k)
+        xk, r1norm, arnorm = out[0], out[3], out[7]
+        assert np.isclose(L.eta(A, b, xk), arnorm / (fro * r1norm), rtol=1e-8)
+
+
 def test_lsqr_iterates_match_scipy_lsqr():
     # with R = I the iteration is plain LSQR: compare iterates after k steps
     A, b, _ = gaussian_problem(300, 12, seed=5, noise=0.3)
