@@ -163,10 +163,23 @@ sns_status snsolve_sketch_workspace_size(const sns_problem* prob, const sns_sket
 /* SA = S A (d x n, row-major, leading dimension ldsa >= n) and Sb = S b
  * (d entries).  SA and Sb are float for F32/CSR input and double for F64 input.
  * Gaussian sketches multiply BF16-rounded A in the tensor cores with FP32
- * accumulation (F32 input only).  Asynchronous on `stream`. */
+ * accumulation (F32 input only).  Asynchronous on `stream`.
+ * Two sketch kernels wait on the device (the tensor-core Gaussian sketch and
+ * the bulk-copy CountSketch gather, selected by SNSOLVE_CS_GATHER=t); their
+ * waits are bounded, and one that gives up leaves SA/Sb incomplete and an
+ * error word in the workspace: snsolve_sketch_status reads it. */
 sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk,
                           void* SA, int64_t ldsa, void* Sb,
                           void* ws, size_t ws_bytes, void* stream);
+
+/* Outcome of the device-side waits of the last snsolve_sketch call made with
+ * this (prob, sk, ws): synchronizes `stream`, then returns SNS_ETIMEOUT if a
+ * bounded wait of that call gave up (its SA/Sb are then invalid) and SNS_OK
+ * otherwise (also for sketch kinds that never wait on the device).  The word
+ * lives in the workspace, so call this before the workspace is reused.
+ * SNS_EINVAL for invalid arguments, SNS_ECUDA if the synchronization fails. */
+sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc* sk, const void* ws,
+                                 size_t ws_bytes, void* stream);
 
 /* ---- Step 3 (Sec. 1.2) and SAP-SAS (Sec. 2.1) ------------------------------
  * Workspace bytes for snsolve_lstsq. */
@@ -237,7 +250,9 @@ sns_status snsolve_server_stats(sns_server* srv, int* running, int* pending, siz
  * Computes SA = S A (d x n FP32, row-major, leading dimension ldsa >= n) and
  * Sb = S b (d floats) for a dense FP32 problem with the deterministic
  * bucket-sorted CountSketch (the same kernels and results as snsolve_sketch
- * with kind SNS_COUNTSKETCH and variant SNS_CS_SORTED).  Its scratch is a fixed
+ * with kind SNS_COUNTSKETCH and variant SNS_CS_SORTED; always the warp gather,
+ * which has no device-side waits, so there is no timeout status to read
+ * afterwards).  Its scratch is a fixed
  * 16 MiB array inside the library's device image, held by every GPU that loads
  * the library until the process exits; no memory is allocated or freed.
  * Problems whose scratch need exceeds 16 MiB (roughly 8 bytes per row of A plus

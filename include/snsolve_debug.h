@@ -43,6 +43,17 @@ sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64
  * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array. */
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host);
 
+/* ---- Bounded device-side waits ----------------------------------------------
+ * The multi-CTA QR of snsolve_lstsq (q = n + 1 >= 32) hands each Householder
+ * reflector from the CTA that builds it to the others through device memory;
+ * every wait for one is bounded.  This sets how many polls such a wait makes
+ * before it gives up (polls <= 0 restores the default, 2^22).  A wait that
+ * gives up sets the factorisation's error word and carries on with zeros, later
+ * waits stop polling, the kernel ends, and snsolve_lstsq returns SNS_ETIMEOUT
+ * (the solve's outputs are then invalid).  Process-wide, read at each launch;
+ * meant for tests of the timeout path. */
+void snsolve_debug_set_qr_wait_limit(int64_t polls);
+
 /* ---- Measurement ----------------------------------------------------------
  * Number of kernel launches this library has issued in this process. */
 uint64_t snsolve_launch_count(void);

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("snsolve_version", C.c_int, []),
     ("snsolve_sketch_workspace_size", C.c_int, [P(sns_problem), P(sns_sketch_desc), P(sz)]),
     ("snsolve_sketch", C.c_int, [vp, P(sns_problem), P(sns_sketch_desc), vp, i64, vp, vp, sz, vp]),
+    ("snsolve_sketch_status", C.c_int, [P(sns_problem), P(sns_sketch_desc), vp, sz, vp]),
     ("snsolve_lstsq_workspace_size", C.c_int, [P(sns_problem), P(sns_opts), P(sz)]),
     ("snsolve_lstsq", C.c_int, [vp, P(sns_problem), P(sns_opts), vp, P(sns_info), vp, sz, vp]),
     ("snsolve_lstsq_batched_workspace_size", C.c_int, [P(sns_problem), P(sns_opts), C.c_int, P(sz)]),
@@ -76,6 +77,7 @@ SIGNATURES = [
     ("snsolve_profile_kernel_name", C.c_char_p, [C.c_int]),
     ("snsolve_profile_read", C.c_int, [P(C.c_double), P(C.c_uint64), C.c_int]),
     ("snsolve_tune_reset", None, []),
+    ("snsolve_debug_set_qr_wait_limit", None, [i64]),
 ]
 
 _lib = None

@@ -325,6 +325,27 @@ sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketc
   return run_sketch(prob, sk, SA, ldsa, Sb, 1, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
+sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc* sk, const void* ws,
+                                 size_t ws_bytes, void* stream) {
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_sketch(prob, sk);
+  if (s != SNS_OK) return s;
+  const void* word = sketch_err_word(prob, sk, static_cast<const uint8_t*>(ws));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!word) {
+    SNS_CUDA_TRY(cudaStreamSynchronize(st));
+    return SNS_OK;
+  }
+  if (!ws || ws_bytes < sketch_ws(prob, sk)) return SNS_EINVAL;
+  double* hp = thread_pinned();
+  if (!hp) return SNS_ENOMEM;
+  SNS_CUDA_TRY(cudaMemcpyAsync(hp + 20, word, 4, cudaMemcpyDeviceToHost, st));
+  SNS_CUDA_TRY(cudaStreamSynchronize(st));
+  int32_t e = 0;
+  memcpy(&e, hp + 20, 4);
+  return e ? SNS_ETIMEOUT : SNS_OK;
+}
+
 sns_status snsolve_lstsq_workspace_size(const sns_problem* prob, const sns_opts* opts, size_t* bytes) {
   if (!bytes) return SNS_EINVAL;
   sns_status s = validate_problem(prob);
@@ -509,6 +530,8 @@ sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes) {
   *bytes = ((size_t)d * 4 + 255) / 256 * 256 + (m2 + 255) / 256 * 256 + (m2 + 1) * 4;
   return SNS_OK;
 }
+void snsolve_debug_set_qr_wait_limit(int64_t polls) { set_qr_wait_limit((long long)polls); }
+
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host) {
   if (!bf16_bits_host) return SNS_EINVAL;
   gauss_table_host(bf16_bits_host);

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -592,15 +593,19 @@ cs_sparse_sign_dense(const float* __restrict__ A, int64_t lda, const float* __re
 
 // ---------------------------------------------------------------------------
 // Host launchers.
-static int g_num_sms = 0;
+// SM count of the current device, cached per device index (grids are sized
+// from it, so a process that drives several devices needs each one's own).
+constexpr int kMaxSmDevices = 64;
+static std::atomic<int> g_num_sms[kMaxSmDevices];
 int num_sms() {
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  std::atomic<int>* slot = dev < kMaxSmDevices ? &g_num_sms[dev] : nullptr;
+  int v = slot ? slot->load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  if (slot) slot->store(v, std::memory_order_relaxed);   // every racing writer stores the same value
+  return v;
 }
 
 static size_t sort_smem(int64_t d) { return (size_t)kSortWarps * d * 2 + (size_t)kRowsPerBlock * 2; }
@@ -648,7 +653,7 @@ static sns_status launch_gather(const DenseArgs& a, int64_t d, const CsLayout& L
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
-                                 int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
+                                 int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st, bool allow_bulk) {
   const CsLayout L = cs_layout(a.m, a.n, d, a.f64, false);
   if (ws_bytes < L.bytes) return SNS_ENOMEM;
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -660,7 +665,7 @@ sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, v
               : launch_gather<double, 1, 4>(a, d, L, w, SA, ldsa, Sb, sbs, st);
   }
   if (cs_tma_eligible(a))
-    return cs_tma_phase2(a, d, L, w, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, st);
+    return cs_tma_phase2(a, d, L, w, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, st, allow_bulk);
   const bool v4 = (a.lda % 4 == 0) && aligned(a.A, 16);
   if (L.ct == 128)
     return v4 ? launch_gather<float, 4, 1>(a, d, L, w, SA, ldsa, Sb, sbs, st)

@@ -9,7 +9,10 @@
 // library holds this array (kStaticScratchBytes) until the process exits.
 //
 // It runs the same bucket-sorted (deterministic) CountSketch kernels as
-// snsolve_sketch with variant SNS_CS_SORTED, on dense FP32 input only.
+// snsolve_sketch with variant SNS_CS_SORTED, on dense FP32 input only, and
+// always with the warp gather: that phase has no device-side waits, so a call
+// cannot time out on the device and leaves no status word behind (the
+// bulk-copy gather, which does wait, is never selected here).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -74,7 +77,7 @@ sns_status snsolve_sketch_countsketch_static(const sns_problem* prob, int64_t d,
   // from an earlier call need no clearing here.
   DenseArgs a{prob->A, prob->lda, prob->b, prob->m, prob->n, false};
   return cs_apply_dense_sorted(a, d, seed, SA, ldsa, Sb, 1, scratch, kStaticScratchBytes,
-                               static_cast<cudaStream_t>(stream));
+                               static_cast<cudaStream_t>(stream), /*allow_bulk=*/false);
 }
 
 }  // extern "C"

@@ -553,17 +553,17 @@ static sns_status launch_tma(const DenseArgs& a, int64_t d, const CsLayout& L, u
 }
 
 sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
-                         float* Sb, int64_t sbs, cudaStream_t st) {
+                         float* Sb, int64_t sbs, cudaStream_t st, bool allow_bulk) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + 7) / 8, (int64_t)num_sms() * 4));
   const size_t smem = (size_t)d * 8;
   SNS_CUDA_TRY(raise_smem_limit((const void*)cs_build_list));
   uint32_t* cbase = reinterpret_cast<uint32_t*>(ws + L.off_cbase);
   uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
-  static int use_tma = -1;
-  if (use_tma < 0) {
+  static const bool env_tma = [] {
     const char* e = getenv("SNSOLVE_CS_GATHER");
-    use_tma = (e && e[0] == 't') ? 1 : 0;
-  }
+    return e && e[0] == 't';
+  }();
+  const bool use_tma = allow_bulk && env_tma;
   {
     SNS_PROF(K_CS_SORT, st);
     cs_build_list<<<grid, 256, smem, st>>>((uint32_t)d, L.nblk, reinterpret_cast<const uint32_t*>(ws + L.off_sorted),

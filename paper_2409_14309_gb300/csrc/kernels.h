@@ -34,14 +34,16 @@ struct CsLayout {
 bool cs_tma_eligible(const DenseArgs& a);
 int64_t cs_tma_parts(int64_t m, int64_t d);
 int64_t cs_warp_max_chunks(int64_t m, int64_t d);
+// allow_bulk: the bulk-copy gather (selected by SNSOLVE_CS_GATHER=t) may be used;
+// otherwise the warp gather, which has no device-side waits, always runs.
 sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
-                         float* Sb, int64_t sbs, cudaStream_t st);
+                         float* Sb, int64_t sbs, cudaStream_t st, bool allow_bulk = true);
 CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr);
 int64_t cs_sorted_max_d();
 int num_sms();
 
 sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,
-                                 int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+                                 int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st, bool allow_bulk = true);
 // Sparse sign embedding, dense FP32 (1 <= zeta <= min(8, d)); zeroes SA and Sb.
 sns_status cs_apply_sparse_sign(const DenseArgs& a, int64_t d, int zeta, uint64_t seed, float* SA, int64_t ldsa,
                                 float* Sb, int64_t sbs, cudaStream_t st);
@@ -88,6 +90,8 @@ size_t qr_coop_ws_bytes(int64_t d, int64_t q);
 // Byte offset, within that workspace, of the int error word (nonzero: a wait timed out).
 size_t qr_coop_err_offset(int64_t d, int64_t q);
 sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st);
+// Polls a cooperative factorisation's waits make before giving up (<= 0: default).
+void set_qr_wait_limit(long long polls);
 sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cudaStream_t st);
 sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, double* RinvT, bool identity,
                       cudaStream_t st);

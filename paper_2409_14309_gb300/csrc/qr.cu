@@ -10,6 +10,8 @@
 // (x_0 = 0 counts as positive), v = x - alpha e_0 scaled so v_0 = 1,
 // tau = -v_0 / alpha; R[j, j] = alpha.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -119,6 +121,10 @@ sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cud
 // with zeros; later waits see the error word and stop polling, so a failed
 // factorisation ends quickly and the host reports it.
 constexpr long long kSpinLimit = 1LL << 22;
+// Poll limit of the next cooperative factorisations (0: kSpinLimit); set by
+// snsolve_debug_set_qr_wait_limit to exercise the timeout path.
+static std::atomic<long long> g_qr_wait_limit{0};
+void set_qr_wait_limit(long long polls) { g_qr_wait_limit.store(polls > 0 ? polls : 0, std::memory_order_relaxed); }
 constexpr int kCoopThreads = 128;
 constexpr int kCoopWarps = kCoopThreads / 32;
 constexpr int kCoopBatch = 8;                 // non-critical columns per batched reduction
@@ -142,7 +148,7 @@ SNS_D void st_relaxed(double* p, double v) {
 // Polls up to kSlots addresses (null = unused) until none holds the sentinel;
 // bounded as described above.
 template <int kSlots>
-SNS_D void coop_poll(const double* const (&addr)[kSlots], double (&val)[kSlots], int* err) {
+SNS_D void coop_poll(const double* const (&addr)[kSlots], double (&val)[kSlots], int* err, long long limit) {
   bool got[kSlots];
 #pragma unroll
   for (int u = 0; u < kSlots; ++u) got[u] = (addr[u] == nullptr);
@@ -156,7 +162,7 @@ SNS_D void coop_poll(const double* const (&addr)[kSlots], double (&val)[kSlots],
         all = all && got[u];
       }
     if (all) return;
-    const bool give_up = it >= kSpinLimit;
+    const bool give_up = it >= limit;
     if (give_up || ((it & 255) == 255 && ld_relaxed_int(err) != 0)) {
       if (give_up) atomicExch(err, 1);
 #pragma unroll
@@ -240,7 +246,7 @@ SNS_D void coop_batch(double* c0, int64_t cstride, int64_t d, int64_t j, double 
 template <bool kSmemCols>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict__ U, double* __restrict__ pub,
-               int* __restrict__ err) {
+               int* __restrict__ err, long long spin_limit) {
   extern __shared__ __align__(16) double qsm[];
   double* vsm = qsm;                                   // reflector rows (fixed row map)
   double* csm = qsm + d;                               // owned columns (kSmemCols)
@@ -342,7 +348,7 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
         double vv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) ad[u] = (i + u * kCoopThreads < d) ? uj + i + u * kCoopThreads : nullptr;
-        coop_poll<8>(ad, vv, err);
+        coop_poll<8>(ad, vv, err, spin_limit);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (ad[u]) vsm[i + u * kCoopThreads] = vv[u];
@@ -363,7 +369,7 @@ qr_coop_kernel(double* __restrict__ W, int64_t d, int64_t q, double* __restrict_
         } else {
           const double* ad[2] = {pub + 2 * j, pub + 2 * j + 1};
           double vv[2];
-          coop_poll<2>(ad, vv, err);
+          coop_poll<2>(ad, vv, err, spin_limit);
           beta = vv[0];
           v0 = vv[1];
         }
@@ -457,7 +463,9 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
   if (!fn) return SNS_EINVAL;
   double* W = o.W;
   int64_t d = o.d, q = o.q;
-  void* args[] = {&W, &d, &q, &U, &pub, &err};
+  long long limit = g_qr_wait_limit.load(std::memory_order_relaxed);
+  if (limit <= 0) limit = kSpinLimit;
+  void* args[] = {&W, &d, &q, &U, &pub, &err, &limit};
   {
     SNS_PROF(K_QR, st);
     SNS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, smem, st));

@@ -45,6 +45,61 @@ def test_sketch_and_solve_f32_matches_oracle(kind, m, n, d):
     assert err <= _xhat_tol(SA), err
 
 
+def _ls_perturbation_bound(M, f, dM, df):
+    """First-order bound on ||dx|| / ||x|| for min ||M x - f|| when M and f move
+    by dM and df (Golub & Van Loan, Matrix Computations, Thm 5.3.1):
+    eps (2 kappa / cos(theta) + tan(theta) kappa^2), eps = max(||dM||/||M||,
+    ||df||/||f||), sin(theta) = ||r|| / ||f||."""
+    s = np.linalg.svd(M, compute_uv=False)
+    kappa = s[0] / s[-1]
+    x = np.linalg.lstsq(M, f, rcond=None)[0]
+    sin_t = np.linalg.norm(f - M @ x) / np.linalg.norm(f)
+    cos_t = np.sqrt(max(1.0 - sin_t ** 2, 1e-300))
+    eps = max(np.linalg.norm(dM, 2) / s[0], np.linalg.norm(df) / np.linalg.norm(f))
+    return eps * (2 * kappa / cos_t + (sin_t / cos_t) * kappa ** 2), kappa
+
+
+@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian", "sparse_sign"])
+def test_xhat_parity_at_kappa_1e6(kind):
+    """Sketch-and-solve on a scaled copy of the benchmark problem (2^16 x 256,
+    kappa = 1e6, noise 1e-4, d = 1024) for every sketch kind.  The GPU's SA is
+    FP32, so x^ legitimately moves by what that rounding implies at this
+    conditioning ("1e-4 cond-scaled"); the checks are: (1) the GPU's FP64 QR and
+    back-solve equal the oracle's solve of the GPU's own [SA | Sb]; (2) SA matches
+    the oracle's SA; (3) x^ vs the oracle's x^ lies within the least-squares
+    perturbation bound of that SA difference.  The measured error is printed."""
+    c = ctx()
+    m, n, d = 1 << 16, 256, 1024
+    A, b, _ = ill_conditioned_problem(m, n, seed=1002, kappa=1e6, noise=1e-4)
+    variant = "4" if kind == "sparse_sign" else "auto"
+    Ad, bd = dev(A), dev(b)
+    SA_g, Sb_g = c.sketch(Ad, bd, d, kind=kind, seed=1, variant=variant)
+    x, info = c.lstsq(Ad, bd, d, kind=kind, seed=1, variant=variant)
+    assert info.status == 0
+    xg = x.cpu().numpy()
+    SA_g = SA_g.cpu().numpy().astype(np.float64)
+    Sb_g = Sb_g.cpu().numpy().astype(np.float64)
+    # (1) solve of the GPU's own sketch in FP64 by the oracle
+    x_own, _, _ = OL.sketch_and_solve(SA_g, Sb_g)
+    e_solve = np.linalg.norm(xg - x_own) / np.linalg.norm(x_own)
+    # (2) the oracle's sketch (BF16-rounded operand for the Gaussian)
+    if kind == "sparse_sign":
+        SA_r, Sb_r = OS.sparse_sign_apply(A, d, 4, 1), OS.sparse_sign_apply(b, d, 4, 1)
+    else:
+        SA_r, Sb_r = OS.sketch_apply(kind, A, d, 1), OS.sketch_apply(kind, b, d, 1)
+    scale = np.sqrt(np.linalg.norm(SA_r) ** 2 + np.linalg.norm(Sb_r) ** 2)
+    e_sa = np.sqrt(np.linalg.norm(SA_g - SA_r) ** 2 + np.linalg.norm(Sb_g - Sb_r) ** 2) / scale
+    # (3) x^ against the oracle's x^
+    x_ref, _, _ = OL.sketch_and_solve(SA_r, Sb_r)
+    e_x = np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref)
+    bound, kappa = _ls_perturbation_bound(SA_r, Sb_r, SA_g - SA_r, Sb_g - Sb_r)
+    print(f"{kind}: kappa(SA) {kappa:.3g}, |SA-SA_ref| {e_sa:.2e}, x^ vs own-SA solve {e_solve:.2e}, "
+          f"x^ vs oracle {e_x:.3e} (first-order bound {bound:.3e})")
+    assert e_solve <= 1e3 * kappa * 2.0 ** -53, e_solve
+    assert e_sa <= (1e-5 if kind == "gaussian" else 1e-6), e_sa
+    assert e_x <= max(1e-4, 2.0 * bound), (e_x, bound)
+
+
 def test_consistent_system_exact():
     c = ctx()
     A, _, xt = gaussian_problem(5000, 32, seed=3)

@@ -46,12 +46,17 @@ def test_static_scratch_matches_workspace_entry_point(m, n, d):
 
 
 def test_static_scratch_rejects_oversize_problem():
+    """A 2^23-row problem needs about 32 MiB of scratch: rejected with
+    SNS_ENOMEM before any launch.  The buffers are real (128 MiB of A), so the
+    call would stay in bounds even if the size check were missing."""
     import paper_2409_14309_gb300 as sns
     ctx()
-    A = torch.zeros((4, 4), device="cuda")
-    b = torch.zeros(4, device="cuda")
+    m, n, d = 1 << 23, 4, 16
+    A = torch.zeros((m, n), device="cuda")
+    b = torch.zeros(m, device="cuda")
     prob = sns.dense_problem(A, b)
-    prob.m = 1 << 23                       # needs ~32 MiB of scratch: rejected before any launch
-    SA = torch.zeros((16, 4), device="cuda")
-    Sb = torch.zeros(16, device="cuda")
-    assert _static_call(prob, 16, 1, SA, Sb) == 2       # SNS_ENOMEM
+    SA = torch.full((d, n), 7.0, device="cuda")
+    Sb = torch.full((d,), 7.0, device="cuda")
+    assert _static_call(prob, d, 1, SA, Sb) == 2       # SNS_ENOMEM
+    torch.cuda.synchronize()
+    assert bool(torch.all(SA == 7.0)) and bool(torch.all(Sb == 7.0))   # nothing was written
