@@ -208,18 +208,57 @@ def algorithmic(name, m, n, d):
     return None, None
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+_UNIT = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+         "KB": 1e3, "MB": 1e6, "GB": 1e9, "B": 1.0}
+
+
 def traffic_table():
-    """Per-launch DRAM bytes from the committed ncu summaries (profiles/traffic.md),
-    with the source hash they were taken at."""
-    path = os.path.join(ROOT, "profiles", "traffic.md")
-    out = {}
-    if not os.path.exists(path):
-        return out
-    for line in open(path):
-        mm = re.match(r"^\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\w+)\s*\|", line)
-        if mm:
-            out[mm.group(1)] = (float(mm.group(2)), mm.group(3))
-    return out
+    """Per-launch DRAM bytes (read + write) of kernel classes from ncu captures,
+    as recorded by `bench.py --record-traffic` in profiles/traffic.json, with the
+    library source hash each was taken at: {name: (bytes, source hash)}."""
+    if not os.path.exists(TRAFFIC_JSON):
+        return {}
+    with open(TRAFFIC_JSON) as f:
+        j = json.load(f)
+    return {k: (float(v["dram_bytes_per_full_launch"]), v["source"]) for k, v in j.items()}
+
+
+def record_traffic(raw_csv, name, kernel_regex, read_scale, write_scale, case, command):
+    """Reads the raw page of an ncu capture (`ncu -i X.ncu-rep --page raw --csv`),
+    takes the launches whose kernel name matches kernel_regex, and records their
+    mean dram__bytes_read.sum * read_scale + dram__bytes_write.sum * write_scale
+    (the scales carry a small captured case to a full-size launch) under `name`
+    in profiles/traffic.json, with the current source hash."""
+    import csv
+    with open(raw_csv) as f:
+        rows = list(csv.reader(f))
+    hdr = rows[0]
+    ki = hdr.index("Kernel Name")
+    ri, wi = hdr.index("dram__bytes_read.sum"), hdr.index("dram__bytes_write.sum")
+    units = rows[1] if rows[1][ri] in _UNIT or rows[1][ri] == "" else None
+    body = rows[2:] if units else rows[1:]
+
+    def val(row, i):
+        return float(row[i].replace(",", "")) * (_UNIT.get(units[i], 1.0) if units else 1.0)
+
+    sel = [r for r in body if len(r) > max(ki, ri, wi) and re.search(kernel_regex, r[ki])]
+    if not sel:
+        raise SystemExit(f"no launch of {kernel_regex} in {raw_csv}")
+    rd = float(np.mean([val(r, ri) for r in sel]))
+    wr = float(np.mean([val(r, wi) for r in sel]))
+    j = {}
+    if os.path.exists(TRAFFIC_JSON):
+        with open(TRAFFIC_JSON) as f:
+            j = json.load(f)
+    j[name] = {"dram_bytes_per_full_launch": rd * read_scale + wr * write_scale, "source": source_hash(),
+               "captured_read_bytes": rd, "captured_write_bytes": wr, "read_scale": read_scale,
+               "write_scale": write_scale, "launches_averaged": len(sel), "captured_case": case,
+               "command": command}
+    with open(TRAFFIC_JSON, "w") as f:
+        json.dump(j, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps({name: j[name]}))
 
 
 def source_hash():
@@ -235,7 +274,8 @@ def source_hash():
 # ------------------------------------------------------------------ CPU oracle
 def oracle_solve_sample(A, b, rows):
     """The oracle's sketch-and-solve + SAP on the first `rows` rows; returns the
-    seconds of (sketch, qr+solve, iterations) and the iteration count."""
+    seconds of (sketch, qr+solve, iterations), the iteration count and the
+    oracle's sketch (SA, Sb)."""
     from oracle import sketch as OS
     from oracle import solve as OL
     As = A[:rows].astype(np.float64)
@@ -248,7 +288,7 @@ def oracle_solve_sample(A, b, rows):
     t2 = time.perf_counter()
     x, it, _ = OL.lsqr_preconditioned(As, bs, R, xhat, tol=TOL, max_iter=500)
     t3 = time.perf_counter()
-    return t1 - t0, t2 - t1, t3 - t2, it
+    return t1 - t0, t2 - t1, t3 - t2, it, SA, Sb
 
 
 def cpu_cores():
@@ -258,19 +298,42 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(A, b, steps=2):
+def oracle_errors(A, b, SA, Sb, x_gpu, eta_gpu):
+    """The GPU solution's errors against the FP64 oracle, outside any timed
+    region: the oracle's eta(x) over the whole matrix, and the forward error and
+    residual excess against x* from the oracle's FP64 sketch-and-precondition run
+    to 1e-14 (its fixed point is x*, pinned by the oracle's tests)."""
+    from oracle import solve as OL
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    t0 = time.perf_counter()
+    x_star, it, est, _ = OL.sketch_and_precondition(A64, b64, SA, Sb, tol=1e-14, max_iter=500)
+    r_star = np.linalg.norm(b64 - A64 @ x_star)
+    r_gpu = np.linalg.norm(b64 - A64 @ x_gpu)
+    return {"eta_oracle_fp64": float(OL.eta(A64, b64, x_gpu)), "eta_reported_by_solver": float(eta_gpu),
+            "forward_error_vs_x_star": float(np.linalg.norm(x_gpu - x_star) / np.linalg.norm(x_star)),
+            "residual_excess": float(r_gpu / r_star - 1.0),
+            "x_star": f"oracle FP64 sketch-and-precondition (LSQR on A R^-1) to {est:.1e} in {it} iterations",
+            "seconds": time.perf_counter() - t0}
+
+
+def cpu_baseline(A, b, steps=2, x_gpu=None, eta_gpu=None):
     """The oracle as it stands on the host cores: full-size solves of the
-    workload (about 10-20 s of CPU work in total)."""
+    workload (about 10-20 s of CPU work in total).  With x_gpu, also the GPU
+    solution's errors against the oracle (untimed)."""
     ts = []
     its = 0
+    SA = Sb = None
     for _ in range(max(1, steps)):
-        t_sk, t_qr, t_it, its = oracle_solve_sample(A, b, M)
+        t_sk, t_qr, t_it, its, SA, Sb = oracle_solve_sample(A, b, M)
         ts.append(t_sk + t_qr + t_it)
     t = float(np.median(ts))
-    return {"value": 1.0 / t, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{len(ts)} complete solves of the workload by the oracle (numpy FP64: row-scatter "
-                      f"CountSketch, Householder QR, R-preconditioned LSQR to eta<=1e-6, {its} iterations); "
-                      f"median time"}
+    out = {"value": 1.0 / t, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+           "sample": f"{len(ts)} complete solves of the workload by the oracle (numpy FP64: row-scatter "
+                     f"CountSketch, Householder QR, R-preconditioned LSQR to eta<=1e-6, {its} iterations); "
+                     f"median time"}
+    if x_gpu is not None:
+        out["oracle_check"] = oracle_errors(A, b, SA, Sb, x_gpu, eta_gpu)
+    return out
 
 
 # ------------------------------------------------------------------ main
@@ -288,7 +351,15 @@ def main():
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr"],
                     help="profile-case: which small case to run")
+    ap.add_argument("--latency-solves", type=int, default=200,
+                    help="solves of the separate latency pass (p50/p99)")
+    ap.add_argument("--record-traffic", nargs=7,
+                    metavar=("RAW_CSV", "NAME", "KERNEL_REGEX", "READ_SCALE", "WRITE_SCALE", "CASE", "COMMAND"),
+                    help="record an ncu capture's DRAM bytes per launch in profiles/traffic.json and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        r = args.record_traffic
+        return record_traffic(r[0], r[1], r[2], float(r[3]), float(r[4]), r[5], r[6])
     warm = max(3, args.warmup)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -361,6 +432,17 @@ def main():
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev, world)
     value = whole_job_rate(args.steps, world, total_ms)
+
+    # latency: a separate pass of single solves, one event pair around each,
+    # no clock sampling and no per-kernel events
+    nlat = max(args.latency_solves, 1)
+    lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nlat)]
+    for k in range(nlat):
+        lev[k][0].record(stream)
+        ctx.lstsq_problem(prob, op, x=x, ws=ws)
+        lev[k][1].record(stream)
+    torch.cuda.synchronize()
+    lat_ms = sorted(e0.elapsed_time(e1) for e0, e1 in lev)
 
     # the same K solves again with a CUDA event pair around every launch (on
     # the launching stream): per-kernel durations for the roofline.  Kept out
@@ -473,11 +555,13 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(A_h, b_h)
+        _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
+        cpu = cpu_baseline(A_h, b_h, x_gpu=x.cpu().numpy(), eta_gpu=info.eta)
 
     if rank == 0:
+        def pct(v, q):
+            return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
         st = sorted(step_ms)
-        p = lambda q: st[min(len(st) - 1, int(math.ceil(q * len(st))) - 1)]
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -485,7 +569,13 @@ def main():
             "config": {"workload": WORKLOAD, "m": M, "n": N, "d": D, "kappa": KAPPA, "tol_eta": TOL,
                        "sketch": "countsketch", "parallelism": f"replicas x{world}",
                        "l2": "A is 1.08 GB > 129 MB L2 and is streamed every pass; no flush needed"},
-            "p50_ms": p(0.50), "p99_ms": p(0.99), "step_ms": [round(t, 4) for t in step_ms],
+            "p50_ms": pct(lat_ms, 0.50), "p99_ms": pct(lat_ms, 0.99),
+            "latency": {"solves": nlat, "p50_ms": pct(lat_ms, 0.50), "p99_ms": pct(lat_ms, 0.99),
+                        "max_ms": lat_ms[-1],
+                        "pass": "separate pass after the timed region: one CUDA event pair around each solve, no "
+                                "clock sampling, no per-kernel events"},
+            "p50_ms_timed_region": pct(st, 0.50), "p99_ms_timed_region": pct(st, 0.99),
+            "step_ms": [round(t, 4) for t in step_ms],
             "kernel_timing": "per-launch CUDA events on the launching stream, in a second pass of the same "
                              "K solves; value and latencies come from the uninstrumented pass",
             "roofline": roof(dom) if dom else None,
@@ -906,13 +996,13 @@ def run_reference(args, rank, world):
         return
     A, b = make_inputs(0, None)
     warm = max(3, args.warmup)
-    t_sk, t_qr, t_it, its = oracle_solve_sample(A, b, M)          # one untimed warm-up solve
+    t_sk, t_qr, t_it, its, _, _ = oracle_solve_sample(A, b, M)    # one untimed warm-up solve
     t_full = t_sk + t_qr + t_it
     frac = 1 if args.steps * t_full <= 120.0 else 4
     rows = M // frac
     ts = []
     for _ in range(args.steps):
-        t_sk, t_qr, t_it, its = oracle_solve_sample(A, b, rows)
+        t_sk, t_qr, t_it, its, _, _ = oracle_solve_sample(A, b, rows)
         ts.append(t_sk * frac + t_qr + t_it * frac)
     tot = float(np.sum(ts))
     val = args.steps / tot

@@ -67,7 +67,11 @@ def test_xhat_parity_at_kappa_1e6(kind):
     conditioning ("1e-4 cond-scaled"); the checks are: (1) the GPU's FP64 QR and
     back-solve equal the oracle's solve of the GPU's own [SA | Sb]; (2) SA matches
     the oracle's SA; (3) x^ vs the oracle's x^ lies within the least-squares
-    perturbation bound of that SA difference.  The measured error is printed."""
+    perturbation bound of that SA difference.  The measured error is printed.
+    Check (1) needs the sketch inside the solve to be the one fetched here, so it
+    runs for the bitwise-reproducible kinds (sorted CountSketch, SRHT); the
+    Gaussian and sparse sign sketches add with float reductions in a varying
+    order, and at kappa(SA) ~ 1e6 two runs' x^ differ by a few percent."""
     c = ctx()
     m, n, d = 1 << 16, 256, 1024
     A, b, _ = ill_conditioned_problem(m, n, seed=1002, kappa=1e6, noise=1e-4)
@@ -95,7 +99,8 @@ def test_xhat_parity_at_kappa_1e6(kind):
     bound, kappa = _ls_perturbation_bound(SA_r, Sb_r, SA_g - SA_r, Sb_g - Sb_r)
     print(f"{kind}: kappa(SA) {kappa:.3g}, |SA-SA_ref| {e_sa:.2e}, x^ vs own-SA solve {e_solve:.2e}, "
           f"x^ vs oracle {e_x:.3e} (first-order bound {bound:.3e})")
-    assert e_solve <= 1e3 * kappa * 2.0 ** -53, e_solve
+    if kind in ("countsketch", "srht"):
+        assert e_solve <= 1e3 * kappa * 2.0 ** -53, e_solve
     assert e_sa <= (1e-5 if kind == "gaussian" else 1e-6), e_sa
     assert e_x <= max(1e-4, 2.0 * bound), (e_x, bound)
 
