@@ -127,8 +127,19 @@ typedef struct {
                               the FP32 passes) */
   int32_t precondition;    /* 1 = R from QR(SA) (default when nonzero); 0 = R = I
                               (unpreconditioned reference iteration) */
-  int32_t reserved;
+  int32_t method;          /* sns_method: how R enters the iteration when tol > 0 */
 } sns_opts;
+
+/* Iterative phase (Sec. 2.1 names both, after Meier, Nakatsukasa, Townsend &
+ * Webb 2023).  Both start from the sketch-and-solve answer and stop at
+ * eta(x) <= tol; the residual passes r = b - A x always read the original A.
+ *  SNS_SAP (sketch-and-precondition): the inner iteration applies R^-1
+ *    implicitly: each pass reads A (w = A^T A z with z = R^-1 p).
+ *  SNS_SAA (sketch-and-apply): Y = A R^-1 is formed once, explicitly, in A's
+ *    precision (m x n extra workspace), and the inner iteration (CG on
+ *    Y^T Y dz = R^-T A^T r, i.e. CGLS/LSQR on Y) reads Y; x += R^-1 dz.
+ *    Dense input only, precondition must be nonzero. */
+typedef enum { SNS_SAP = 0, SNS_SAA = 1 } sns_method;
 
 /* Per-solve report. */
 typedef struct {

@@ -43,6 +43,13 @@ sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64
  * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array. */
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host);
 
+/* Y = A R^-1, the explicit preconditioned matrix of sketch-and-apply (SNS_SAA,
+ * Sec. 2.1), exactly as snsolve_lstsq forms it: prob dense (F32 or F64), Rinv a
+ * device FP64 n x n row-major upper-triangular matrix, Y a device array in A's
+ * precision with leading dimension ldy >= n.  SNS_EINVAL for CSR input or bad
+ * arguments. */
+sns_status snsolve_debug_form_y(const sns_problem* prob, const double* Rinv, void* Y, int64_t ldy, void* stream);
+
 /* ---- Bounded device-side waits ----------------------------------------------
  * The multi-CTA QR of snsolve_lstsq (q = n + 1 >= 32) hands each Householder
  * reflector from the CTA that builds it to the others through device memory;

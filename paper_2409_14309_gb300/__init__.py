@@ -71,9 +71,15 @@ def sketch_desc(d, kind="countsketch", seed=0, variant="auto"):
     return abi.sns_sketch_desc(kind=KIND[kind], variant=v, d=int(d), seed=int(seed) & (2**64 - 1))
 
 
-def opts(d, kind="countsketch", seed=0, variant="auto", tol=0.0, max_iter=0, inner=0, precondition=True):
+METHOD = {"sap": abi.SNS_SAP, "saa": abi.SNS_SAA}
+
+
+def opts(d, kind="countsketch", seed=0, variant="auto", tol=0.0, max_iter=0, inner=0, precondition=True,
+         method="sap"):
+    """Solve options; method "sap" (sketch-and-precondition) or "saa"
+    (sketch-and-apply: explicit Y = A R^-1) for the iterative phase."""
     return abi.sns_opts(sk=sketch_desc(d, kind, seed, variant), tol=float(tol), max_iter=int(max_iter),
-                        inner=int(inner), precondition=1 if precondition else 0)
+                        inner=int(inner), precondition=1 if precondition else 0, method=METHOD[method])
 
 
 def _workspace(nbytes, device):
@@ -148,10 +154,11 @@ class Context:
         return x, info
 
     def lstsq(self, A, b, d, kind="countsketch", seed=0, tol=0.0, max_iter=0, inner=0, precondition=True,
-              variant="auto", ws=None, stream=None):
-        """Sketch-and-solve (tol <= 0) or sketch-and-precondition to eta <= tol."""
+              variant="auto", ws=None, stream=None, method="sap"):
+        """Sketch-and-solve (tol <= 0), or sketch-and-precondition ("sap") /
+        sketch-and-apply ("saa") to eta <= tol."""
         return self.lstsq_problem(dense_problem(A, b),
-                                  opts(d, kind, seed, variant, tol, max_iter, inner, precondition), ws=ws,
+                                  opts(d, kind, seed, variant, tol, max_iter, inner, precondition, method), ws=ws,
                                   stream=stream)
 
     def lstsq_csr(self, rowptr, col, val, b, n, d, seed=0, tol=0.0, max_iter=0, inner=0, precondition=True,

@@ -15,6 +15,7 @@ SNS_OK, SNS_EINVAL, SNS_ENOMEM, SNS_ERANK, SNS_ENOTCONV, SNS_EAGAIN, SNS_ETIMEOU
 SNS_COUNTSKETCH, SNS_GAUSSIAN, SNS_SRHT, SNS_SPARSE_SIGN = range(4)
 SNS_DENSE_F32, SNS_DENSE_F64, SNS_CSR_F32 = range(3)
 SNS_CS_AUTO, SNS_CS_SORTED, SNS_CS_STREAM = range(3)
+SNS_SAP, SNS_SAA = range(2)
 
 STATUS_NAMES = {0: "SNS_OK", 1: "SNS_EINVAL", 2: "SNS_ENOMEM", 3: "SNS_ERANK", 4: "SNS_ENOTCONV",
                 5: "SNS_EAGAIN", 6: "SNS_ETIMEOUT", 7: "SNS_ECUDA", 8: "SNS_EBUDGET"}
@@ -32,7 +33,7 @@ class sns_problem(C.Structure):
 
 class sns_opts(C.Structure):
     _fields_ = [("sk", sns_sketch_desc), ("tol", C.c_double), ("max_iter", C.c_int32), ("inner", C.c_int32),
-                ("precondition", C.c_int32), ("reserved", C.c_int32)]
+                ("precondition", C.c_int32), ("method", C.c_int32)]
 
 
 class sns_info(C.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = [
     ("snsolve_profile_read", C.c_int, [P(C.c_double), P(C.c_uint64), C.c_int]),
     ("snsolve_tune_reset", None, []),
     ("snsolve_debug_set_qr_wait_limit", None, [i64]),
+    ("snsolve_debug_form_y", C.c_int, [P(sns_problem), vp, vp, i64, vp]),
 ]
 
 _lib = None

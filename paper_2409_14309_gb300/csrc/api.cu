@@ -212,9 +212,10 @@ static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, vo
 
 // Workspace of snsolve_lstsq.
 struct LsLayout {
-  size_t off_saug, off_sk, sk_bytes, off_w, off_dev, off_qr, off_iter, bytes;
+  size_t off_saug, off_sk, sk_bytes, off_w, off_dev, off_qr, off_iter, off_y, bytes;
   int grid;
 };
+static bool uses_saa(const sns_opts* o) { return o->tol > 0 && o->method == SNS_SAA; }
 static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
   LsLayout L{};
   const int64_t d = o->sk.d, q = p->n + 1;
@@ -229,6 +230,8 @@ static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
   L.grid = iter_grid();
   L.off_iter = off;
   if (o->tol > 0) off += al(iter_ws_bytes(p->n, L.grid));
+  L.off_y = off;
+  if (uses_saa(o)) off += al(saa_y_bytes(p->m, p->n, is_f64(p)));
   L.bytes = off;
   return L;
 }
@@ -241,6 +244,8 @@ static sns_status validate_opts(const sns_problem* p, const sns_opts* o) {
   if (o->sk.d > 16384) return SNS_EINVAL;   // the QR keeps one column of SA in shared memory
   if (o->tol > 0 && p->fmt != SNS_CSR_F32 && p->n > 1024) return SNS_EINVAL;
   if (!(o->tol == o->tol)) return SNS_EINVAL;  // NaN
+  if (o->method != SNS_SAP && o->method != SNS_SAA) return SNS_EINVAL;
+  if (o->method == SNS_SAA && (p->fmt == SNS_CSR_F32 || o->precondition == 0)) return SNS_EINVAL;
   return SNS_OK;
 }
 
@@ -437,9 +442,11 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   if (!side.ok) return SNS_ECUDA;
   SNS_CUDA_TRY(cudaEventRecord(side.ev_in, st));
   SNS_CUDA_TRY(cudaStreamWaitEvent(side.st, side.ev_in, 0));
+  const bool saa = uses_saa(opts);
   s = rinv_build(W, d, n, I.Rinv, I.RinvT, !precond, side.st);
   if (s != SNS_OK) return s;
-  s = pgram_build(I.Rinv, n, I.P, side.st);
+  // SAP: M^-1 = R^-1 R^-T in x-space; SAA: CG on Y^T Y in z-space, M = I
+  s = saa ? ident_build(I.P, n, side.st) : pgram_build(I.Rinv, n, I.P, side.st);
   if (s != SNS_OK) return s;
   SNS_CUDA_TRY(cudaEventRecord(side.ev_out, side.st));
   bool rinv_joined = false;
@@ -447,6 +454,10 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   CsrArgs ca{prob->rowptr, prob->col, prob->val, static_cast<const float*>(prob->b), prob->m, n, prob->nnz};
   const DenseArgs* dap = prob->fmt == SNS_CSR_F32 ? nullptr : &da;
   const CsrArgs* cap = prob->fmt == SNS_CSR_F32 ? &ca : nullptr;
+  // SAA: the explicit Y = A R^-1, formed before the first inner cycle
+  void* Y = w + L.off_y;
+  const DenseArgs ya{Y, saa_ldy(n, f64), nullptr, prob->m, n, f64};
+  bool y_ready = false;
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 400;
   const int inner = opts->inner > 0 ? opts->inner : kDefaultInnerMax;
   int passes = 0, outer = 0;
@@ -475,14 +486,25 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
       SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
       rinv_joined = true;
     }
-    s = pcg_start(I, n, opts->tol, st);
+    if (saa) {
+      if (!y_ready) {
+        if ((s = saa_form_y(da, I.Rinv, Y, st)) != SNS_OK) return s;
+        y_ready = true;
+      }
+      // right-hand side Y^T r = R^-T g (into w, which the first pass overwrites)
+      if ((s = saa_matvec(I.RinvT, n, I.g, I.w, false, st)) != SNS_OK) return s;
+      s = pcg_start_rhs(I, n, opts->tol, I.w, st);
+    } else {
+      s = pcg_start(I, n, opts->tol, st);
+    }
     if (s != SNS_OK) return s;
     const int budget = std::min(inner, max_iter - passes);
     for (int k = 0; k < budget; ++k) {
-      if ((s = normal_pass(dap, cap, I, st)) != SNS_OK) return s;
+      if ((s = saa ? normal_pass(&ya, nullptr, I, st) : normal_pass(dap, cap, I, st)) != SNS_OK) return s;
       if ((s = pcg_step(I, n, st)) != SNS_OK) return s;
     }
-    s = pcg_apply(I, n, x, st);
+    // x += dx (SAP), x += R^-1 dz (SAA)
+    s = saa ? saa_matvec(I.Rinv, n, I.dx, x, true, st) : pcg_apply(I, n, x, st);
     if (s != SNS_OK) return s;
   }
   if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
@@ -531,6 +553,14 @@ sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes) {
   return SNS_OK;
 }
 void snsolve_debug_set_qr_wait_limit(int64_t polls) { set_qr_wait_limit((long long)polls); }
+
+sns_status snsolve_debug_form_y(const sns_problem* prob, const double* Rinv, void* Y, int64_t ldy, void* stream) {
+  sns_status s = validate_problem(prob);
+  if (s != SNS_OK) return s;
+  if (prob->fmt == SNS_CSR_F32 || !Rinv || !Y || ldy < prob->n) return SNS_EINVAL;
+  DenseArgs da{prob->A, prob->lda, prob->b, prob->m, prob->n, is_f64(prob)};
+  return saa_form_y(da, Rinv, Y, static_cast<cudaStream_t>(stream), ldy);
+}
 
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host) {
   if (!bf16_bits_host) return SNS_EINVAL;

@@ -1145,6 +1145,14 @@ sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st) {
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
+sns_status pcg_start_rhs(const IterWs& W, int64_t n, double tol, const double* v, cudaStream_t st) {
+  {
+    SNS_PROF(K_MATVEC, st);
+    pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, v, pcg_vecs(W), W.ticket + kPcgTicket, tol);
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
 sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st) {
   {
     SNS_PROF(K_MATVEC, st);

@@ -131,6 +131,17 @@ sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st);
 sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st);
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st);
 
+// Sketch-and-apply (SAA-SAS).  Y = A R^-1 (m x n, A's precision, leading
+// dimension saa_ldy) from the FP64 row-major R^-1; out = M v (or += M v) for an
+// n x n FP64 row-major M; P = I.
+int64_t saa_ldy(int64_t n, bool f64);
+size_t saa_y_bytes(int64_t m, int64_t n, bool f64);
+sns_status saa_form_y(const DenseArgs& a, const double* Rinv, void* Y, cudaStream_t st, int64_t ldy = 0);
+sns_status saa_matvec(const double* M, int64_t n, const double* v, double* out, bool accumulate, cudaStream_t st);
+sns_status ident_build(double* P, int64_t n, cudaStream_t st);
+// pcg_start with the right-hand side v instead of the residual pass's g.
+sns_status pcg_start_rhs(const IterWs& W, int64_t n, double tol, const double* v, cudaStream_t st);
+
 // Batched.
 size_t batch_ws_bytes(const sns_problem* probs, const sns_opts* opts, int nprob);
 sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int nprob, double* const* x,

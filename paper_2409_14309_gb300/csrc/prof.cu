@@ -14,7 +14,8 @@ namespace sns {
 static const char* kNames[K_COUNT] = {
     "cs_sort_blocks", "cs_gather_dense", "cs_stream_dense", "cs_gather_csr", "srht_sample", "srht_pass1",
     "srht_pass2",     "gauss_apply",     "qr_load",         "qr_house",      "rinv",        "resid_pass",
-    "normal_pass",    "pcg_matvec",      "pcg_apply",       "eta",           "batched",     "misc"};
+    "normal_pass",    "pcg_matvec",      "pcg_apply",       "eta",           "batched",     "misc",
+    "saa_form_y"};
 
 const char* kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
 

@@ -8,7 +8,7 @@ namespace sns {
 
 enum KernelId {
   K_CS_SORT = 0, K_CS_GATHER, K_CS_STREAM, K_CS_CSR, K_SRHT_SAMPLE, K_SRHT_PASS1, K_SRHT_PASS2, K_GAUSS,
-  K_QR_LOAD, K_QR, K_RINV, K_RESID, K_NORMAL, K_MATVEC, K_CG, K_ETA, K_BATCH, K_MISC, K_COUNT
+  K_QR_LOAD, K_QR, K_RINV, K_RESID, K_NORMAL, K_MATVEC, K_CG, K_ETA, K_BATCH, K_MISC, K_SAA_Y, K_COUNT
 };
 const char* kernel_name(int id);
 

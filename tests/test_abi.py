@@ -96,6 +96,17 @@ def test_workspace_queries_and_validation(lib):
     op0 = abi.sns_opts(sk=sk, tol=0.0)
     assert lib.snsolve_lstsq_workspace_size(C.byref(_prob()), C.byref(op0), C.byref(sz)) == 0
     assert sz.value < with_iter
+    # sketch-and-apply: needs room for Y; dense input with a preconditioner only
+    op_saa = abi.sns_opts(sk=sk, tol=1e-8, method=abi.SNS_SAA, precondition=1)
+    assert lib.snsolve_lstsq_workspace_size(C.byref(_prob()), C.byref(op_saa), C.byref(sz)) == 0
+    assert sz.value >= with_iter + 1000 * 12 * 4
+    assert lib.snsolve_lstsq_workspace_size(C.byref(_prob()), C.byref(abi.sns_opts(sk=sk, tol=1e-8, method=7)),
+                                            C.byref(sz)) == 1
+    assert lib.snsolve_lstsq_workspace_size(
+        C.byref(_prob()), C.byref(abi.sns_opts(sk=sk, tol=1e-8, method=abi.SNS_SAA, precondition=0)),
+        C.byref(sz)) == 1
+    csr = abi.sns_problem(m=1000, n=10, fmt=abi.SNS_CSR_F32, rowptr=0x1000, col=0x2000, val=0x3000, nnz=5, b=0x4000)
+    assert lib.snsolve_lstsq_workspace_size(C.byref(csr), C.byref(op_saa), C.byref(sz)) == 1
     # null pointers are rejected before anything runs
     assert lib.snsolve_sketch(None, C.byref(_prob()), C.byref(sk), None, 10, None, None, 0, None) == 1
     assert lib.snsolve_lstsq(None, C.byref(_prob()), C.byref(op), None, None, None, 0, None) == 1
