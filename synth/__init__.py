@@ -12,6 +12,12 @@ Recipes:
   Haar-random orthogonal n x n (QR of a Gaussian with the signs of diag(R) moved
   into Q, Mezzadri 2007), sigma_j = kappa^(-j/(n-1)) (log-spaced from 1 to
   1/kappa), x_true iid N(0,1), b = A x_true + noise * N(0,1).
+* ``paper_problem``: the benchmark setup the paper follows (Epperly et al.
+  2024): A = U diag(sigma) V^T with U (m x n) and V (n x n) Haar-random
+  orthonormal, sigma_j = kappa^(-j/(n-1)); x* = w / ||w|| for Gaussian w;
+  r* = beta * P z / ||P z|| with z Gaussian and P = I - U U^T, so r* is
+  orthogonal to range(A); b = A x* + r*.  Then x* is the exact least-squares
+  solution and ||b - A x*|| = beta by construction.  FP64.
 * ``csr_problem``: per row a Binomial(n, density) count of uniformly random,
   distinct column positions with N(0,1) values, plus ``n_dense`` seeded rows that
   are fully dense and scaled by ``dense_scale`` (high-leverage rows);
@@ -73,6 +79,31 @@ def ill_conditioned_problem(m, n, seed, kappa=1e6, noise=1e-4, dtype=np.float32)
         A[r0:r1] = (G @ Mx).astype(dtype)
     x_true = rng.standard_normal(n)
     return A, _finish(A, x_true, noise, rng, dtype), x_true
+
+
+def paper_problem(m, n, seed, kappa=1e10, beta=1e-10):
+    """Ill-conditioned problem with a known solution; returns (A, b, x_star)."""
+    rng = _rng(seed)
+    U = haar_orthogonal_columns(m, n, rng)
+    V = haar_orthogonal(n, rng)
+    sigma = log_spaced_sigma(n, kappa)
+    A = (U * sigma[None, :]) @ V.T
+    w = rng.standard_normal(n)
+    x_star = w / np.linalg.norm(w)
+    z = rng.standard_normal(m)
+    z -= U @ (U.T @ z)
+    z -= U @ (U.T @ z)                  # twice: orthogonal to range(U) to rounding
+    r_star = beta * z / np.linalg.norm(z)
+    b = A @ x_star + r_star
+    return A, b, x_star
+
+
+def haar_orthogonal_columns(m, n, rng):
+    """m x n matrix with orthonormal columns, Haar-distributed (QR of an m x n
+    Gaussian with the signs of diag(R) moved into Q)."""
+    Z = rng.standard_normal((m, n))
+    Q, R = np.linalg.qr(Z)
+    return Q * np.sign(np.diag(R))[None, :]
 
 
 class CSR:
