@@ -347,7 +347,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cs-variant", default="auto", choices=["auto", "sorted", "stream"])
     ap.add_argument("--workload", default="solve",
-                    choices=["solve", "batched", "served", "sketches", "latency", "csr", "profile-case"])
+                    choices=["solve", "batched", "served", "sketches", "latency", "csr", "profile-case", "paper"])
+    ap.add_argument("--paper-m", default="5000,20000,100000,250000,500000,1000000",
+                    help="paper workload: rows of A to sweep")
+    ap.add_argument("--paper-passes", type=int, default=64, help="paper workload: passes budget per solve")
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr"],
                     help="profile-case: which small case to run")
@@ -380,6 +383,8 @@ def main():
         return run_csr(args)
     if args.workload == "profile-case":
         return run_profile_case(args)
+    if args.workload == "paper":
+        return run_paper(args)
 
     import torch
     import torch.distributed as dist
@@ -590,6 +595,81 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+# ------------------------------------------------------------------ paper workload
+def _paper_device(m, n, kappa, beta, gen, dev):
+    """The paper's benchmark problem generated on the device (FP64): A = U diag(sigma)
+    V^T, x* = w / ||w||, r* = beta P z / ||P z|| with P = I - U U^T, b = A x* + r*."""
+    import torch
+    G = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float64)
+    U, Rr = torch.linalg.qr(G)
+    U = U * torch.sign(torch.diagonal(Rr))[None, :]
+    del G, Rr
+    V = _haar(n, gen, dev)
+    sig = kappa ** (-torch.arange(n, device=dev, dtype=torch.float64) / max(n - 1, 1))
+    A = (U * sig[None, :]) @ V.T
+    w = torch.randn(n, generator=gen, device=dev, dtype=torch.float64)
+    x_star = w / torch.linalg.norm(w)
+    z = torch.randn(m, generator=gen, device=dev, dtype=torch.float64)
+    for _ in range(2):
+        z -= U @ (U.T @ z)
+    del U
+    b = A @ x_star + beta * z / torch.linalg.norm(z)
+    return A.contiguous(), b, x_star
+
+
+def run_paper(args):
+    """The paper's benchmark setup (Sec. 3.1, after Epperly et al. 2024) on one GPU:
+    FP64 A of m x 1000, kappa 1e10, beta 1e-10, m swept from 5e3 to 1e6.  Per m:
+    sketch-and-precondition (SAP), sketch-and-apply (SAA) and the unpreconditioned
+    iteration (R = I; the role of the paper's LSQR baseline), each with the same
+    budget of passes over the matrix, timed with CUDA events; forward error
+    ||x - x*|| / ||x*|| and residual error ||A (x - x*)|| / beta against the known
+    x* (the paper's Figs. 3-5 quantities).  CountSketch d = 4n."""
+    import torch
+    import paper_2409_14309_gb300 as sns
+    dev = torch.device("cuda", 0)
+    ctx = sns.Context(0)
+    n, kappa, beta = 1000, 1e10, 1e-10
+    budget = args.paper_passes
+    ms = [int(v) for v in args.paper_m.split(",")]
+    rows = []
+    for m in ms:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(4000 + m)
+        A, b, x_star = _paper_device(m, n, kappa, beta, gen, dev)
+        torch.cuda.synchronize()
+        prob = sns.dense_problem(A, b)
+        row = {"m": m}
+        for label, meth, pre in (("sap", "sap", True), ("saa", "saa", True), ("unpreconditioned", "sap", False)):
+            op = sns.opts(4 * n, "countsketch", 1, tol=1e-300, max_iter=budget, precondition=pre, method=meth)
+            ws = torch.empty(ctx.lstsq_workspace(prob, op), dtype=torch.uint8, device=dev)
+            x = torch.empty(n, dtype=torch.float64, device=dev)
+            ctx.lstsq_problem(prob, op, x=x, ws=ws)                   # warm-up
+            torch.cuda.synchronize()
+            reps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                _, info = ctx.lstsq_problem(prob, op, x=x, ws=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            d = x - x_star
+            row[label] = {"ms": e0.elapsed_time(e1) / reps, "passes": info.iters, "residual_passes": info.outer,
+                          "forward_error": float(torch.linalg.norm(d) / torch.linalg.norm(x_star)),
+                          "residual_error": float(torch.linalg.norm(A @ d) / beta), "eta": info.eta,
+                          "status": sns.status_name(info.status)}
+            del ws
+        rows.append(row)
+        del A, b, x_star, prob
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "paper", "config": {"n": n, "kappa": kappa, "beta": beta, "d": 4 * n,
+                                                      "dtype": "f64", "sketch": "countsketch",
+                                                      "passes_budget": budget,
+                                                      "stop": "fixed budget of passes (eta floors near 1e-7 "
+                                                              "in FP64 at this beta)"},
+                      "data": "synthetic (U diag(sigma) V^T, known x*)", "rows": rows}))
+
 
 # ------------------------------------------------------------------ batched workload
 def _haar(n, gen, dev):

@@ -192,6 +192,29 @@ sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketc
 sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc* sk, const void* ws,
                                  size_t ws_bytes, void* stream);
 
+/* ---- Rows of a larger matrix (row-sharded sketching) ------------------------
+ * Sketch of rows row0 .. row0 + m - 1 of a larger matrix [A_full | b_full]
+ * whose rows are split over several calls (or several GPUs): every row keeps
+ * its global index i, so S's column i is the same as in a sketch of the whole
+ * matrix, and S [A_full | b_full] is the sum of the parts' outputs (one sum,
+ * e.g. an all-reduce of the d x (n+1) partials).  prob describes the local
+ * rows (prob->m of them); the rest is as in snsolve_sketch.  CountSketch (all
+ * variants), Gaussian and sparse sign sketches; SRHT mixes all rows through
+ * its Hadamard transform and is rejected (SNS_EINVAL), as is row0 < 0. */
+sns_status snsolve_sketch_rows(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk, int64_t row0,
+                               void* SA, int64_t ldsa, void* Sb, void* ws, size_t ws_bytes, void* stream);
+
+/* Step 3 of Sec. 1.2 on a sketch the caller already holds (for example the
+ * sum of row-sharded partial sketches): FP64 Householder QR of the augmented
+ * [SA | Sb] (d x (n+1), row-major with leading dimension ld >= n + 1, FP32 if
+ * f64 == 0, else FP64; device) and x^ = R^-1 z into x (n doubles, device).
+ * info (host, may be NULL) gets the status and ||SA x^ - Sb||.  Synchronizes
+ * `stream`.  Returns SNS_ERANK on rank deficiency, SNS_ETIMEOUT if a bounded
+ * wait of the multi-CTA QR gave up. */
+sns_status snsolve_solve_sketched_workspace_size(int64_t d, int64_t n, size_t* bytes);
+sns_status snsolve_solve_sketched(sns_ctx* ctx, const void* SAaug, int64_t ld, int32_t f64, int64_t d, int64_t n,
+                                  double* x, sns_info* info, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- Step 3 (Sec. 1.2) and SAP-SAS (Sec. 2.1) ------------------------------
  * Workspace bytes for snsolve_lstsq. */
 sns_status snsolve_lstsq_workspace_size(const sns_problem* prob, const sns_opts* opts,

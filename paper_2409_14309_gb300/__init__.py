@@ -129,6 +129,39 @@ class Context:
         """SA = S A and Sb = S b for a dense CUDA matrix."""
         return self.sketch_problem(dense_problem(A, b), sketch_desc(d, kind, seed, variant), A.dtype, ws, stream)
 
+    def sketch_rows(self, A, b, row0, d, kind="countsketch", seed=0, variant="auto", ws=None, stream=None):
+        """Partial sketch of rows row0.. of a larger dense matrix (global row
+        indices); the sketch of the whole matrix is the sum of the parts'."""
+        prob, sk = dense_problem(A, b), sketch_desc(d, kind, seed, variant)
+        SA = torch.empty((sk.d, prob.n), dtype=A.dtype, device=self.device)
+        Sb = torch.empty((sk.d,), dtype=A.dtype, device=self.device)
+        need = self.sketch_workspace(prob, sk)
+        if ws is None or ws.numel() < need:
+            ws = _workspace(need, self.device)
+        _check(self._L.snsolve_sketch_rows(self.h, C.byref(prob), C.byref(sk), int(row0), _ptr(SA), SA.stride(0),
+                                           _ptr(Sb), _ptr(ws), ws.numel(), _stream(stream)), "snsolve_sketch_rows")
+        return SA, Sb
+
+    def solve_sketched(self, SAaug, ws=None, stream=None, check=True):
+        """x^ = argmin ||SA x - Sb|| from a d x (n+1) augmented [SA | Sb] on the
+        device (FP32 or FP64): FP64 Householder QR and back substitution."""
+        assert SAaug.is_cuda and SAaug.dim() == 2 and SAaug.stride(1) == 1
+        d, q = SAaug.shape
+        n = q - 1
+        sz = C.c_size_t()
+        _check(self._L.snsolve_solve_sketched_workspace_size(d, n, C.byref(sz)),
+               "snsolve_solve_sketched_workspace_size")
+        if ws is None or ws.numel() < sz.value:
+            ws = _workspace(sz.value, self.device)
+        x = torch.empty(n, dtype=torch.float64, device=self.device)
+        info = abi.sns_info()
+        code = self._L.snsolve_solve_sketched(self.h, _ptr(SAaug), SAaug.stride(0),
+                                              1 if SAaug.dtype == torch.float64 else 0, d, n, _ptr(x),
+                                              C.byref(info), _ptr(ws), ws.numel(), _stream(stream))
+        if check and code not in (abi.SNS_OK, abi.SNS_ERANK):
+            raise SnsError(code, "snsolve_solve_sketched")
+        return x, info
+
     def sketch_csr(self, rowptr, col, val, b, n, d, seed=0, variant="auto", ws=None, stream=None):
         return self.sketch_problem(csr_problem(rowptr, col, val, b, n), sketch_desc(d, "countsketch", seed, variant),
                                    torch.float32, ws, stream)

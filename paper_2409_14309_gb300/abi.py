@@ -56,6 +56,9 @@ SIGNATURES = [
     ("snsolve_sketch_workspace_size", C.c_int, [P(sns_problem), P(sns_sketch_desc), P(sz)]),
     ("snsolve_sketch", C.c_int, [vp, P(sns_problem), P(sns_sketch_desc), vp, i64, vp, vp, sz, vp]),
     ("snsolve_sketch_status", C.c_int, [P(sns_problem), P(sns_sketch_desc), vp, sz, vp]),
+    ("snsolve_sketch_rows", C.c_int, [vp, P(sns_problem), P(sns_sketch_desc), i64, vp, i64, vp, vp, sz, vp]),
+    ("snsolve_solve_sketched_workspace_size", C.c_int, [i64, i64, P(sz)]),
+    ("snsolve_solve_sketched", C.c_int, [vp, vp, i64, C.c_int32, i64, i64, vp, P(sns_info), vp, sz, vp]),
     ("snsolve_lstsq_workspace_size", C.c_int, [P(sns_problem), P(sns_opts), P(sz)]),
     ("snsolve_lstsq", C.c_int, [vp, P(sns_problem), P(sns_opts), vp, P(sns_info), vp, sz, vp]),
     ("snsolve_lstsq_batched_workspace_size", C.c_int, [P(sns_problem), P(sns_opts), C.c_int, P(sz)]),

@@ -184,12 +184,12 @@ static const void* sketch_err_word(const sns_problem* p, const sns_sketch_desc* 
 }
 
 static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, void* SA, int64_t ldsa, void* Sb,
-                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
-  DenseArgs da{p->A, p->lda, p->b, p->m, p->n, is_f64(p)};
+                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st, int64_t row0 = 0) {
+  DenseArgs da{p->A, p->lda, p->b, p->m, p->n, is_f64(p), row0};
   switch (sk->kind) {
     case SNS_COUNTSKETCH:
       if (p->fmt == SNS_CSR_F32) {
-        CsrArgs ca{p->rowptr, p->col, p->val, static_cast<const float*>(p->b), p->m, p->n, p->nnz};
+        CsrArgs ca{p->rowptr, p->col, p->val, static_cast<const float*>(p->b), p->m, p->n, p->nnz, row0};
         if (!cs_use_sorted(p, sk))
           return cs_apply_csr_stream(ca, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb),
                                      sbs, st);
@@ -328,6 +328,76 @@ sns_status snsolve_sketch(sns_ctx* ctx, const sns_problem* prob, const sns_sketc
   if (ws_bytes < sketch_ws(prob, sk) || (ws_bytes > 0 && !ws && sketch_ws(prob, sk) > 0)) return SNS_ENOMEM;
   if (ws && ((uintptr_t)ws % 256)) return SNS_EINVAL;
   return run_sketch(prob, sk, SA, ldsa, Sb, 1, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+sns_status snsolve_sketch_rows(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk, int64_t row0,
+                               void* SA, int64_t ldsa, void* Sb, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !SA || !Sb) return SNS_EINVAL;
+  sns_status s = validate_problem(prob);
+  if (s == SNS_OK) s = validate_sketch(prob, sk);
+  if (s != SNS_OK) return s;
+  if (row0 < 0 || row0 > ((int64_t)1 << 40) || sk->kind == SNS_SRHT || ldsa < prob->n) return SNS_EINVAL;
+  if (ws_bytes < sketch_ws(prob, sk) || (ws_bytes > 0 && !ws && sketch_ws(prob, sk) > 0)) return SNS_ENOMEM;
+  if (ws && ((uintptr_t)ws % 256)) return SNS_EINVAL;
+  return run_sketch(prob, sk, SA, ldsa, Sb, 1, ws, ws_bytes, static_cast<cudaStream_t>(stream), row0);
+}
+
+// Workspace of snsolve_solve_sketched: FP64 column-major copy, status words,
+// the multi-CTA QR's hand-off area.
+struct SolveLayout {
+  size_t off_w, off_dev, off_qr, bytes;
+};
+static SolveLayout solve_layout(int64_t d, int64_t n) {
+  SolveLayout L{};
+  const int64_t q = n + 1;
+  size_t off = 0;
+  L.off_w = off; off += al((size_t)d * q * 8);
+  L.off_dev = off; off += al(64);
+  L.off_qr = off; off += al(qr_coop_ws_bytes(d, q));
+  L.bytes = off;
+  return L;
+}
+
+sns_status snsolve_solve_sketched_workspace_size(int64_t d, int64_t n, size_t* bytes) {
+  if (!bytes || n < 1 || d < n || d > 16384) return SNS_EINVAL;
+  *bytes = solve_layout(d, n).bytes;
+  return SNS_OK;
+}
+
+sns_status snsolve_solve_sketched(sns_ctx* ctx, const void* SAaug, int64_t ld, int32_t f64, int64_t d, int64_t n,
+                                  double* x, sns_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !SAaug || !x || n < 1 || d < n || d > 16384 || ld < n + 1) return SNS_EINVAL;
+  const SolveLayout L = solve_layout(d, n);
+  if (!ws || ws_bytes < L.bytes) return SNS_ENOMEM;
+  if ((uintptr_t)ws % 256) return SNS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  const int64_t q = n + 1;
+  double* W = reinterpret_cast<double*>(w + L.off_w);
+  int32_t* dstatus = reinterpret_cast<int32_t*>(w + L.off_dev);
+  double* dsres = reinterpret_cast<double*>(w + L.off_dev + 8);
+  double* hp = thread_pinned();
+  if (!hp) return SNS_ENOMEM;
+  sns_status s = qr_load_colmajor(SAaug, ld, f64 != 0, d, q, W, st);
+  if (s != SNS_OK) return s;
+  QrOut o{W, d, q, x, dstatus, dsres};
+  const bool coop = q >= 32;
+  s = coop ? qr_solve_coop(o, w + L.off_qr, st) : qr_solve_one(o, st);
+  if (s != SNS_OK) return s;
+  SNS_CUDA_TRY(cudaMemcpyAsync(hp + 21, w + L.off_dev, 16, cudaMemcpyDeviceToHost, st));
+  if (coop) SNS_CUDA_TRY(cudaMemcpyAsync(hp + 23, w + L.off_qr + qr_coop_err_offset(d, q), 4,
+                                         cudaMemcpyDeviceToHost, st));
+  SNS_CUDA_TRY(cudaStreamSynchronize(st));
+  int32_t qs = 0, qerr = 0;
+  memcpy(&qs, hp + 21, 4);
+  if (coop) memcpy(&qerr, hp + 23, 4);
+  const int status = qerr ? SNS_ETIMEOUT : qs;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->sketch_resid = qerr ? 0.0 : hp[22];
+  }
+  return (sns_status)status;
 }
 
 sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc* sk, const void* ws,

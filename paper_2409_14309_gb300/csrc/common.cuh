@@ -33,6 +33,10 @@ SNS_HD uint64_t mix64(uint64_t z) {
 }
 SNS_HD uint64_t stream_state(uint64_t seed, uint64_t stream) { return seed ^ (stream << 56); }
 SNS_HD uint64_t splitmix_at(uint64_t s0, uint64_t idx) { return mix64(s0 + (idx + 1) * kGamma); }
+// State whose output i is output i + offset of the stream that starts at s0:
+// splitmix_at(shift_state(s0, o), i) == splitmix_at(s0, i + o).  A sketch of
+// rows row0.. of a larger matrix uses it so every row keeps its global index.
+SNS_HD uint64_t shift_state(uint64_t s0, uint64_t offset) { return s0 + offset * kGamma; }
 
 // Multiply-shift range reduction of the low 32 bits into [0, d) (Lemire 2019).
 SNS_HD uint32_t bucket_of(uint64_t key, uint64_t d) {

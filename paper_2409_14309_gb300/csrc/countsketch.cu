@@ -610,7 +610,8 @@ int num_sms() {
 
 static size_t sort_smem(int64_t d) { return (size_t)kSortWarps * d * 2 + (size_t)kRowsPerBlock * 2; }
 
-sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, cudaStream_t st) {
+sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, int64_t row0, const CsLayout& L, uint8_t* ws,
+                     cudaStream_t st) {
   const size_t smem = sort_smem(d);
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_btot, 0, (size_t)d * 4, st));
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));   // error word and phase-2 item counter
@@ -618,7 +619,8 @@ sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, const CsLayout& L, uin
   {
     SNS_PROF(K_CS_SORT, st);
   cs_sort_blocks<<<(unsigned)L.nblk, kSortWarps * 32, smem, st>>>(
-      m, (uint32_t)d, stream_state(seed, kStreamCountSketch), L.nblk, reinterpret_cast<uint32_t*>(ws + L.off_sorted),
+      m, (uint32_t)d, shift_state(stream_state(seed, kStreamCountSketch), row0), L.nblk,
+      reinterpret_cast<uint32_t*>(ws + L.off_sorted),
       reinterpret_cast<uint32_t*>(ws + L.off_seg), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
       L.nticket, reinterpret_cast<uint32_t*>(ws + L.off_btot));
   }
@@ -657,7 +659,7 @@ sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, v
   const CsLayout L = cs_layout(a.m, a.n, d, a.f64, false);
   if (ws_bytes < L.bytes) return SNS_ENOMEM;
   uint8_t* w = static_cast<uint8_t*>(ws);
-  sns_status s = cs_phase1(a.m, d, seed, L, w, st);
+  sns_status s = cs_phase1(a.m, d, seed, a.row0, L, w, st);
   if (s != SNS_OK) return s;
   if (a.f64) {
     const bool v2 = (a.lda % 2 == 0) && aligned(a.A, 16);
@@ -688,7 +690,7 @@ sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, v
     SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
   }
   const bool v4 = (a.lda % 4 == 0) && (ldsa % 4 == 0) && (a.n % 4 == 0) && aligned(a.A, 16) && aligned(SA, 16);
-  const uint64_t s0 = stream_state(seed, kStreamCountSketch);
+  const uint64_t s0 = shift_state(stream_state(seed, kStreamCountSketch), a.row0);
   const int grid = num_sms() * 8;
   if (v4)
     {
@@ -713,7 +715,7 @@ sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, i
   const CsLayout L = cs_layout(a.m, a.n, d, false, true);
   if (ws_bytes < L.bytes) return SNS_ENOMEM;
   uint8_t* w = static_cast<uint8_t*>(ws);
-  sns_status s = cs_phase1(a.m, d, seed, L, w, st);
+  sns_status s = cs_phase1(a.m, d, seed, a.row0, L, w, st);
   if (s != SNS_OK) return s;
   const size_t smem = (size_t)(a.n + 1) * 4;
   SNS_CUDA_TRY(raise_smem_limit((const void*)cs_gather_csr));
@@ -821,7 +823,8 @@ sns_status cs_apply_csr_stream(const CsrArgs& a, int64_t d, uint64_t seed, float
   {
     SNS_PROF(K_CS_CSR, st);
     cs_stream_csr<<<grid, 256, 0, st>>>(a.rowptr, a.col, a.val, a.b, a.m, a.n, (uint32_t)d,
-                                       stream_state(seed, kStreamCountSketch), SA, ldsa, Sb, sbs);
+                                       shift_state(stream_state(seed, kStreamCountSketch), a.row0), SA, ldsa,
+                                       Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -841,7 +844,9 @@ sns_status cs_apply_sparse_sign(const DenseArgs& a, int64_t d, int zeta, uint64_
     SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
   }
   const bool v4 = (a.lda % 4 == 0) && (ldsa % 4 == 0) && (a.n % 4 == 0) && aligned(a.A, 16) && aligned(SA, 16);
-  const uint64_t s0 = stream_state(seed, kStreamCountSketch), s4 = stream_state(seed, kStreamSparseSign);
+  // draw 0 of row i is output i of stream 0, draw z >= 1 output i (zeta - 1) + z - 1 of stream 4
+  const uint64_t s0 = shift_state(stream_state(seed, kStreamCountSketch), a.row0);
+  const uint64_t s4 = shift_state(stream_state(seed, kStreamSparseSign), (uint64_t)a.row0 * (uint64_t)(zeta - 1));
   const float scale = (float)(1.0 / std::sqrt((double)zeta));
   const int grid = num_sms() * 8;
   {

@@ -563,7 +563,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
       SNS_PROF(K_GAUSS, st);
       kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-          stream_state(seed, kStreamGaussian), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
+          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
           scratch, err);
     }
     SNS_CUDA_TRY(cudaGetLastError());
@@ -579,7 +579,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   {
     SNS_PROF(K_GAUSS, st);
   gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-                                   stream_state(seed, kStreamGaussian), dtab, kchunk,
+                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab, kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());

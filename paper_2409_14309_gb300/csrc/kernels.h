@@ -9,12 +9,15 @@
 
 namespace sns {
 
+// row0: global index of row 0 (the rows are rows row0.. of a larger matrix
+// whose sketch is the sum of the parts' sketches); 0 for a whole matrix.
 struct DenseArgs {
   const void* A;
   int64_t lda;
   const void* b;
   int64_t m, n;
   bool f64;
+  int64_t row0 = 0;
 };
 struct CsrArgs {
   const int64_t* rowptr;
@@ -22,6 +25,7 @@ struct CsrArgs {
   const float* val;
   const float* b;
   int64_t m, n, nnz;
+  int64_t row0 = 0;
 };
 
 // CountSketch workspace layout.
