@@ -647,7 +647,7 @@ def run_paper(args):
             x = torch.empty(n, dtype=torch.float64, device=dev)
             ctx.lstsq_problem(prob, op, x=x, ws=ws)                   # warm-up
             torch.cuda.synchronize()
-            reps = 3
+            reps = 2
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):

@@ -659,7 +659,14 @@ sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, v
   const CsLayout L = cs_layout(a.m, a.n, d, a.f64, false);
   if (ws_bytes < L.bytes) return SNS_ENOMEM;
   uint8_t* w = static_cast<uint8_t*>(ws);
-  sns_status s = cs_phase1(a.m, d, seed, a.row0, L, w, st);
+  sns_status s;
+  if (!a.f64 && allow_bulk && cs_tma_eligible(a) && !cs_bulk_gather_selected()) {
+    // one cooperative plan launch (bounded grid barriers) + the warp gather
+    bool used = false;
+    s = cs_coop_apply(a, d, seed, L, w, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, st, &used);
+    if (s != SNS_OK || used) return s;
+  }
+  s = cs_phase1(a.m, d, seed, a.row0, L, w, st);
   if (s != SNS_OK) return s;
   if (a.f64) {
     const bool v2 = (a.lda % 2 == 0) && aligned(a.A, 16);

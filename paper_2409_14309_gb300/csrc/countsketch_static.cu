@@ -10,9 +10,10 @@
 //
 // It runs the same bucket-sorted (deterministic) CountSketch kernels as
 // snsolve_sketch with variant SNS_CS_SORTED, on dense FP32 input only, and
-// always with the warp gather: that phase has no device-side waits, so a call
-// cannot time out on the device and leaves no status word behind (the
-// bulk-copy gather, which does wait, is never selected here).
+// always with the two-kernel plan and the warp gather: neither waits on the
+// device, so a call cannot time out there and leaves no status word behind
+// (the cooperative plan and the bulk-copy gather, which do wait, are never
+// selected here; the results are the same).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>

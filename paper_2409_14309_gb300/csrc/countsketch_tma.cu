@@ -173,6 +173,204 @@ cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, con
 }
 
 // ---------------------------------------------------------------------------
+// Phases 1 + 1b in one cooperative launch (one CTA per 4096-row block, all
+// co-resident): the same hash, per-warp histograms and stable per-block order
+// as cs_sort_blocks, and the same bucket-major list, chunk tables and
+// empty-bucket zeroing as cs_build_list, without the intermediate per-block
+// sorted array.  Two grid barriers separate the phases:
+//   A  per block: hash every row once (bucket | sign kept in shared memory),
+//      per-warp bucket histograms, block totals -> seg[k * nblk + blk];
+//   B  per bucket (buckets spread over the CTAs): exclusive scan of its block
+//      totals in block order (the bucket's start in each block), total -> btot;
+//   C  per CTA: bucket bases and chunk bases by scanning btot (each CTA scans
+//      all d totals itself), chunk table and zeroed SA rows for its buckets,
+//      then its block's rows scattered to list[bbase + block start + warp
+//      offset + rank], rows of a bucket in ascending order.
+// The grid barriers are bounded: a CTA whose wait gives up sets the error word
+// and skips its remaining work but still arrives at later barriers; every CTA
+// reads the word before scattering, positions are checked against m, and the
+// gather returns at once when the word is set.
+constexpr int kPlanWarps = 8;
+SNS_D uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+SNS_D int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Arrival counter `bar` grows monotonically; barrier number e waits for (e + 1) * G
+// arrivals.  Returns, identically in every thread of the CTA, whether the error
+// word was clear after the wait (one read by thread 0, broadcast through shared
+// memory, so the CTA's control flow stays uniform).
+SNS_D bool grid_barrier(uint32_t* bar, uint32_t target, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    bool ok = false;
+    for (long long it = 0; it < kWaitLimit; ++it) {
+      if (ld_acquire_u32(bar) >= target) {
+        ok = true;
+        break;
+      }
+      if (it >= 64) __nanosleep(64);
+    }
+    if (!ok) atomicExch(err, 1);
+    __threadfence();
+    s_ok = (ok && ld_acquire_i32(err) == 0) ? 1 : 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+// Exclusive scan over k < d of f(k) into out[k] (shared memory), every thread
+// owning a contiguous run of ceil(d / 256) buckets; returns the total.
+template <typename F>
+SNS_D uint32_t block_scan_buckets(uint32_t d, F&& f, uint32_t* out, uint32_t* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = ((int)d + blockDim.x - 1) / blockDim.x;
+  const int k0 = tid * per, k1 = min((int)d, k0 + per);
+  uint32_t local = 0;
+  for (int k = k0; k < k1; ++k) local += f(k);
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();                       // wsum free (an earlier scan may still read it)
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  uint32_t run = incl - local, total = 0;
+  for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+    if (ww < w) run += wsum[ww];
+    total += wsum[ww];
+  }
+  for (int k = k0; k < k1; ++k) {
+    out[k] = run;
+    run += f(k);
+  }
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kPlanWarps * 32)
+cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restrict__ seg,
+             uint32_t* __restrict__ ticket, int64_t nticket, uint32_t* __restrict__ btot, uint32_t* __restrict__ bbase,
+             uint32_t* __restrict__ list, uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab,
+             float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int64_t n,
+             uint32_t* __restrict__ bar, int* __restrict__ err) {
+  extern __shared__ __align__(16) uint8_t psm[];
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(psm);                 // [W][d] per-warp counts, then offsets
+  uint16_t* hb = cnt + (size_t)kPlanWarps * d;                       // [R] bucket | sign << 15
+  uint32_t* sb = reinterpret_cast<uint32_t*>(hb + kListRowsPerBlock);  // [d] bases (phase C)
+  __shared__ uint32_t wsum[kPlanWarps];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t blk = blockIdx.x;
+  const int64_t r0 = blk * kListRowsPerBlock;
+  const uint32_t G = gridDim.x;
+  constexpr int kRowsPerWarp = kListRowsPerBlock / kPlanWarps;
+  constexpr uint32_t kNone = 0xFFFFu;
+
+  // ---- A: hash, per-warp histograms, block totals
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < nticket; i += (int64_t)G * blockDim.x) ticket[i] = 0;
+  for (int i = tid; i < kPlanWarps * (int)d; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int j = 0; j < kRowsPerWarp; j += 32) {
+    const int loc = w * kRowsPerWarp + j + lane;
+    const int64_t row = r0 + loc;
+    uint32_t h = kNone, sgn = 0;
+    if (row < m) {
+      const uint64_t key = splitmix_at(s0, (uint64_t)row);
+      h = bucket_of(key, d);
+      sgn = (uint32_t)(key >> 63);
+    }
+    hb[loc] = (uint16_t)(h == kNone ? kNone : (h | (sgn << 15)));
+    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // block totals; per-warp counts become offsets within the block's bucket run
+  for (int k = tid; k < (int)d; k += blockDim.x) {
+    uint32_t tot = 0;
+    for (int ww = 0; ww < kPlanWarps; ++ww) {
+      const uint32_t c = cnt[ww * d + k];
+      cnt[ww * d + k] = (uint16_t)tot;
+      tot += c;
+    }
+    seg[(size_t)k * nblk + blk] = tot;
+  }
+  const bool ok1 = grid_barrier(bar, G, err);
+
+  // ---- B: per bucket, exclusive scan of the block totals; bucket totals
+  if (ok1) {
+    for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
+      uint32_t* sk = seg + (size_t)k * nblk;
+      uint32_t run = 0;
+      for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+        const int64_t b = b0 + lane;
+        const uint32_t c = b < nblk ? __ldcg(sk + b) : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (b < nblk) sk[b] = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) btot[k] = run;
+    }
+  }
+  if (!grid_barrier(bar, 2 * G, err)) return;           // CTA-uniform
+
+  // ---- C: bases, chunk tables, empty buckets, scatter
+  const uint32_t nchunks =
+      block_scan_buckets(d, [&](int k) { return (__ldcg(btot + k) + kChunkRows - 1) / kChunkRows; }, sb, wsum);
+  if (blockIdx.x == 0 && tid == 0) cbase[d] = nchunks;
+  for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
+    const uint32_t len = __ldcg(btot + k);
+    const uint32_t nch = (len + kChunkRows - 1) / kChunkRows;
+    for (uint32_t c = lane; c < nch; c += 32) ctab[sb[k] + c] = (uint32_t)k;
+    if (lane == 0) cbase[k] = sb[k];
+    if (len == 0) {
+      // a bucket no row hashed to has no gather item: its rows are zero
+      for (int64_t c = lane; c < n; c += 32) SA[k * ldsa + c] = 0.f;
+      if (lane == 0) Sb[k * sbs] = 0.f;
+    }
+  }
+  block_scan_buckets(d, [&](int k) { return __ldcg(btot + k); }, sb, wsum);
+  for (int k = tid; k < (int)d; k += blockDim.x) {
+    if (blockIdx.x == 0) bbase[k] = sb[k];
+    sb[k] += __ldcg(seg + (size_t)k * nblk + blk);            // this block's start in bucket k
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int j = 0; j < kRowsPerWarp; j += 32) {
+    const int loc = w * kRowsPerWarp + j + lane;
+    const int64_t row = r0 + loc;
+    const uint32_t hw = hb[loc];
+    const uint32_t h = hw == kNone ? kNone : (hw & 0x7FFFu);
+    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    if (h != kNone) {
+      const uint32_t pos = sb[h] + cnt[w * d + h] + __popc(peers & lt);
+      if (pos < (uint64_t)m) list[pos] = (uint32_t)row | ((hw >> 15) << 31);
+    }
+    __syncwarp();
+    if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
+    __syncwarp();
+  }
+}
+
+size_t cs_plan_smem(int64_t d) {
+  return (size_t)kPlanWarps * d * 2 + (size_t)kListRowsPerBlock * 2 + (size_t)d * 4;
+}
+
+// ---------------------------------------------------------------------------
 template <int CT>
 __global__ void __launch_bounds__((kTmaWC + 1) * 32)
 cs_gather_tma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t n, uint32_t d,
@@ -407,7 +605,9 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
                const uint32_t* __restrict__ bbase, const uint32_t* __restrict__ cbase,
                const uint32_t* __restrict__ ctab, uint32_t d, uint32_t* __restrict__ ticket,
                uint32_t* __restrict__ next_item, float* __restrict__ part, float* __restrict__ SA, int64_t ldsa,
-               float* __restrict__ Sb, int64_t sbs) {
+               float* __restrict__ Sb, int64_t sbs, const int* __restrict__ err) {
+  // a plan phase that gave up a bounded wait left its tables incomplete
+  if (*err != 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = cbase[d];
   const int64_t nitems = nchunks * ntile;
@@ -559,11 +759,7 @@ sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8
   SNS_CUDA_TRY(raise_smem_limit((const void*)cs_build_list));
   uint32_t* cbase = reinterpret_cast<uint32_t*>(ws + L.off_cbase);
   uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
-  static const bool env_tma = [] {
-    const char* e = getenv("SNSOLVE_CS_GATHER");
-    return e && e[0] == 't';
-  }();
-  const bool use_tma = allow_bulk && env_tma;
+  const bool use_tma = allow_bulk && cs_bulk_gather_selected();
   {
     SNS_PROF(K_CS_SORT, st);
     cs_build_list<<<grid, 256, smem, st>>>((uint32_t)d, L.nblk, reinterpret_cast<const uint32_t*>(ws + L.off_sorted),
@@ -588,7 +784,63 @@ sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8
         reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
         reinterpret_cast<const uint32_t*>(ws + L.off_bbase), cbase, ctab, (uint32_t)d,
         reinterpret_cast<uint32_t*>(ws + L.off_ticket), reinterpret_cast<uint32_t*>(ws + L.off_err) + 1,
-        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs);
+        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs, reinterpret_cast<const int*>(ws + L.off_err));
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+bool cs_bulk_gather_selected() {
+  static const bool sel = [] {
+    const char* e = getenv("SNSOLVE_CS_GATHER");
+    return e && e[0] == 't';
+  }();
+  return sel;
+}
+
+// Plan (cs_plan_coop, cooperative) + warp gather.  *used = false (nothing
+// launched) when the blocks cannot all be co-resident; the caller then runs
+// the two-kernel plan.  Error word layout (16 bytes at L.off_err): [0] error,
+// [1] gather item counter, [2] grid-barrier arrivals.
+sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, float* SA,
+                         int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st, bool* used) {
+  *used = false;
+  const size_t smem = cs_plan_smem(d);
+  SNS_CUDA_TRY(raise_smem_limit((const void*)cs_plan_coop));
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_plan_coop, kPlanWarps * 32, smem));
+  if ((int64_t)occ * num_sms() < L.nblk || L.nblk >= ((int64_t)1 << 31)) return SNS_OK;
+  *used = true;
+  SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));
+  int64_t m = a.m, nblk = L.nblk, nticket = L.nticket, n = a.n, ldsa_ = ldsa, sbs_ = sbs;
+  uint32_t dd = (uint32_t)d;
+  uint64_t s0 = shift_state(stream_state(seed, kStreamCountSketch), a.row0);
+  uint32_t* seg = reinterpret_cast<uint32_t*>(ws + L.off_seg);
+  uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + L.off_ticket);
+  uint32_t* btot = reinterpret_cast<uint32_t*>(ws + L.off_btot);
+  uint32_t* bbase = reinterpret_cast<uint32_t*>(ws + L.off_bbase);
+  uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.off_list);
+  uint32_t* cbase = reinterpret_cast<uint32_t*>(ws + L.off_cbase);
+  uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
+  uint32_t* bar = reinterpret_cast<uint32_t*>(ws + L.off_err) + 2;
+  int* err = reinterpret_cast<int*>(ws + L.off_err);
+  void* args[] = {&m, &dd, &s0, &nblk, &seg, &ticket, &nticket, &btot, &bbase, &list, &cbase, &ctab,
+                  &SA, &ldsa_, &Sb, &sbs_, &n, &bar, &err};
+  {
+    SNS_PROF(K_CS_SORT, st);
+    SNS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cs_plan_coop, dim3((unsigned)nblk), dim3(kPlanWarps * 32),
+                                             args, smem, st));
+  }
+  const int64_t ntile = (a.n + kWarpCT - 1) / kWarpCT;
+  int gocc = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gocc, cs_gather_warp, 256, 0));
+  const int64_t grid2 = (int64_t)num_sms() * std::max(gocc, 1);
+  {
+    SNS_PROF(K_CS_GATHER, st);
+    cs_gather_warp<<<(unsigned)grid2, 256, 0, st>>>(
+        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile, list, btot, bbase, cbase,
+        ctab, (uint32_t)d, ticket, reinterpret_cast<uint32_t*>(ws + L.off_err) + 1,
+        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs, err);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;

@@ -138,35 +138,37 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // ---------------------------------------------------------------------------
 // Tensor-core path (tcgen05, BF16 operands, FP32 accumulation in TMEM).
 //
-// CTA tile: 256 rows of G (two M = 128 MMA tiles) x up to 256 columns of A x a
-// range of K (rows of A).  Per 64-row chunk of A, all 256 threads write the
-// chunk's G tile (generated from the hash and the BF16 table) and the BF16
+// CTA tile: 128 rows of G (one M = 128 MMA tile) x up to 256 columns of A x a
+// range of K (rows of A).  Per 64-row chunk of A, the CTA's 512 threads write
+// the chunk's G tile (generated from the hash and the BF16 table) and the BF16
 // copy of A's chunk into shared memory in the canonical K-major layout without
 // swizzle (8 x 16-byte core matrices: element (r, k) at
-// ((r/8)*8 + k/8)*128 + (r%8)*16 + (k%8)*2), then one thread issues
-// 2 (M tiles) x 4 (K = 16 steps) MMAs of 128 x N x 16 and commits them to the
-// stage's mbarrier.  Two stages alternate, so writing chunk c+1 overlaps the
-// MMAs of chunk c.  The b column is accumulated on the CUDA cores from the same
-// BF16 G tile.  The epilogue reads TMEM (tcgen05.ld), scales by 1/sqrt(d) and
-// adds into SA / Sb with FP32 reductions (the K range is split over CTAs); it
-// also runs every kUFlush chunks into a per-CTA scratch tile, so no TMEM
-// accumulator sums more than 256 MMA steps.
+// ((r/8)*8 + k/8)*128 + (r%8)*16 + (k%8)*2), then one thread issues 4 MMAs of
+// 128 x N x 16 (K = 16 steps) and commits them to the stage's mbarrier.  Two
+// stages alternate, so writing chunk c+1 overlaps the MMAs of chunk c.  The b
+// column is accumulated on the CUDA cores from the same BF16 G tile.
+//
+// Accumulation.  The tensor cores add into the TMEM accumulator in FP32
+// without round-to-nearest (measured: relative error ~2^-24 per accumulated K
+// = 16 step, growing linearly with the steps of one accumulation run).  So the
+// accumulator D (TMEM columns 0..255) only ever holds kUFlush chunks (16 MMA
+// steps): then the CTA's warps add D into a running FP32 sum S held in TMEM
+// columns 256..511 (tcgen05.ld of both, round-to-nearest adds in registers,
+// tcgen05.st of S) and the next chunk restarts D.  The epilogue adds D and S,
+// scales by 1/sqrt(d) and adds into SA / Sb with FP32 reductions (the K range
+// is split over CTAs).
 // Waits are bounded; on expiry the CTA records an error, lets its issued MMAs
 // drain (bounded), frees its TMEM and returns.
-constexpr int kUG = 256;          // G rows per CTA
+constexpr int kUG = 128;          // G rows per CTA (one M = 128 tile)
 constexpr int kUKT = 64;          // K rows per stage
 constexpr int kUN = 256;          // max columns per CTA
 constexpr int kUKC = kUKT / 8;    // core matrices along K
-constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 32 KB
+constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 16 KB
 constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB
 constexpr uint32_t kUStaging = kUKT * kUN * 4;  // 64 KB of FP32 rows of A
+constexpr uint32_t kUSum = 256;                 // TMEM column of the running sum S
 constexpr long long kUWait = 1LL << 24;
-// The tensor cores accumulate into TMEM in FP32 without round-to-nearest
-// (measured: relative error ~2^-24 per accumulated K = 16 step at m = 2^20);
-// every kUFlush chunks (256 steps) the accumulators are added, with
-// round-to-nearest, into the CTA's own FP32 tile in the workspace (L2-resident)
-// and restarted; the final epilogue adds that tile.
-constexpr int64_t kUFlush = 64;
+constexpr int64_t kUFlush = 4;                  // chunks per accumulation run (16 MMA steps)
 
 SNS_D uint32_t u_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 SNS_D uint32_t kmaj_off(int r, int k) { return (uint32_t)(((r >> 3) * kUKC + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2); }
@@ -193,6 +195,29 @@ SNS_D bool u_wait(uint64_t* bar, uint32_t parity) {
 SNS_D uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
+}
+// 16 consecutive TMEM columns of this warp's 32 lanes (32x32b shape).
+SNS_D void tmem_ld16(uint32_t a, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(a));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+SNS_D void tmem_st16(uint32_t a, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(a),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Issues the bulk copies of rows [i0, i0 + rows) of A's column tile into the
@@ -221,7 +246,7 @@ template <bool BULK>
 __global__ void __launch_bounds__(kUThreads, 1)
 gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
            uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
-           int64_t ldsa, float* __restrict__ Sb, int64_t sbs, float* __restrict__ scratch, int* __restrict__ err) {
+           int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t usm[];
   uint8_t* stA[2] = {usm, usm + kUStageA + kUStageB};
   uint8_t* stB[2] = {usm + kUStageA, usm + 2 * kUStageA + kUStageB};
@@ -261,52 +286,34 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   const uint32_t taddr = tmem_base;
   const uint32_t idesc =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  float sb_acc = 0.f;                                            // b column, row r_base + tid
+  // b column: row tid mod 128, K quarter tid / 128; each chunk's 16 products
+  // are summed in a partial, partials go into a compensated (TwoSum) running sum
+  float sb_hi = 0.f, sb_lo = 0.f;
   const int64_t nchunks = (i_end - i_begin + kUKT - 1) / kUKT;
   int64_t issued = 0;                                            // chunks whose MMAs were issued
   if (BULK && nchunks > 0 && warp == 0)
     stage_rows(staging, A, lda, col0, ncols, i_begin, (int)min((int64_t)kUKT, i_end - i_begin), &rows_ready);
-  // TMEM accumulators: periodic flushes add them into the CTA's scratch tile
-  // (layout [column block of 16][256 rows][16], so a warp's accesses are
-  // contiguous); the final flush adds the scratch tile, scales and reduces
-  // into SA (and the b column's register sums into Sb)
-  float* cta_scratch =
-      scratch ? scratch + (((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (kUG * kUN)
-              : nullptr;
+  // D (columns 0..255) -> S (columns kUSum..): warp w reads TMEM lanes of
+  // quadrant w mod 4 (the hardware rule) and the 16-column blocks w / 4,
+  // w / 4 + 4, ...; the final pass adds D and S, scales and reduces into SA.
   int nflush = 0;
   auto tmem_flush = [&](bool final_pass) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // 16 warps: warp w reads TMEM lanes of quadrant w mod 4 (the hardware
-    // rule), tile (w / 4) mod 2, and one half of the columns (w / 8)
-    const int quarter = warp & 3, mt = (warp >> 2) & 1, chalf = warp >> 3;
-    const int halfc = ((npad / 16 + 1) / 2) * 16;
-    const int cbeg = chalf ? halfc : 0, cend = chalf ? npad : halfc;
-    const int rloc = mt * 128 + quarter * 32 + lane;
+    const int quarter = warp & 3, part = warp >> 2;
+    const int rloc = quarter * 32 + lane;
     const int64_t row = r_base + rloc;
-    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-      uint32_t vi[16];
-      const uint32_t a = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 256 + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
-            "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]),
-            "=r"(vi[15])
-          : "r"(a));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+    for (int c0 = part * 16; c0 < npad; c0 += 64) {
       float v[16];
+      tmem_ld16(taddr + lanes + (uint32_t)c0, v);
+      if (nflush > 0) {
+        float sacc[16];
+        tmem_ld16(taddr + lanes + kUSum + (uint32_t)c0, sacc);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(vi[j]);
-      float4* sp = cta_scratch ? reinterpret_cast<float4*>(cta_scratch + ((c0 / 16) * kUG + rloc) * 16) : nullptr;
-      if (sp && nflush > 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float4 t = sp[j];
-          v[4 * j] += t.x; v[4 * j + 1] += t.y; v[4 * j + 2] += t.z; v[4 * j + 3] += t.w;
-        }
+        for (int j = 0; j < 16; ++j) v[j] += sacc[j];
       }
       if (!final_pass) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) sp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        tmem_st16(taddr + lanes + kUSum + (uint32_t)c0, v);
         continue;
       }
       if (row < d) {
@@ -326,7 +333,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     }
     if (final_pass) {
       if (with_b && r_base + (tid & (kUG - 1)) < d)
-        atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, sb_acc * scale);
+        atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, (sb_hi + sb_lo) * scale);
     } else {
       ++nflush;
     }
@@ -384,48 +391,42 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     __syncthreads();                                             // staging consumed
     if (BULK && c + 1 < nchunks && warp == 0)
       stage_rows(staging, A, lda, col0, ncols, i0 + kUKT, (int)min((int64_t)kUKT, i_end - i0 - kUKT), &rows_ready);
-    // G tile: task (hash group gl, 8 consecutive k): 8 hashes give the 4 rows
-    // r = 32 (gl / 8) + gl % 8 + 8 q, q = 0..3 (field q) x 8 values.  The 8
-    // threads of a store phase take consecutive gl, hence 8 distinct r mod 8:
-    // 8 distinct 16-byte bank groups.
-    for (int t = tid; t < (kUG / 4) * kUKC; t += blockDim.x) {
-      const int gl = t % (kUG / 4), k8 = t / (kUG / 4);
+    // G tile: task (hash group gl, 4 consecutive k), one per thread: 4 hashes
+    // give the 4 rows r = 32 (gl / 8) + gl % 8 + 8 q, q = 0..3 (field q) x 4
+    // values, stored as 8 bytes per row.
+    for (int t = tid; t < (kUG / 4) * (kUKT / 4); t += blockDim.x) {
+      const int gl = t % (kUG / 4), k4 = t / (kUG / 4);
       const int64_t g = (r_base / 32) * 8 + gl;
       // outputs ctr0, ctr0 + groups, ... of the stream: the generator state
       // advances by groups * gamma between them (no multiply per output)
-      const uint64_t ctr0 = (uint64_t)(i0 + 8 * k8) * (uint64_t)groups + (uint64_t)g;
+      const uint64_t ctr0 = (uint64_t)(i0 + 4 * k4) * (uint64_t)groups + (uint64_t)g;
       uint64_t stt = s0 + (ctr0 + 1) * kGamma;
       const uint64_t step = (uint64_t)groups * kGamma;
-      uint64_t key[8];
+      uint64_t key[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 4; ++j) {
         key[j] = mix64(stt);
         stt += step;
       }
-      const int kvalid = rows - 8 * k8;                      // entries j < kvalid are rows of A
+      const int kvalid = rows - 4 * k4;                      // entries j < kvalid are rows of A
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = 32 * (gl >> 3) + (gl & 7) + 8 * q;
         const bool rowok = r_base + r < d;
-        uint32_t h[8];
+        uint32_t h[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
           const uint32_t word = (q < 2) ? (uint32_t)key[j] : (uint32_t)(key[j] >> 32);
           const uint32_t idx = (word >> ((q & 1) * 16 + 4)) & 0xFFFu;
           h[j] = (rowok && j < kvalid) ? (uint32_t)T[idx] : 0u;
         }
-        uint4 w;
-        w.x = h[0] | (h[1] << 16);
-        w.y = h[2] | (h[3] << 16);
-        w.z = h[4] | (h[5] << 16);
-        w.w = h[6] | (h[7] << 16);
-        *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * k8)) = w;
+        *reinterpret_cast<uint2*>(sA + kmaj_off(r, 4 * k4)) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (cta_scratch && c > c_acc0 && (c - c_acc0) % kUFlush == 0) {
-      // chunks c_acc0 .. c - 1 are in TMEM: wait for their MMAs, add, restart
+    if (c > c_acc0 && (c - c_acc0) % kUFlush == 0) {
+      // chunks c_acc0 .. c - 1 are in D: wait for their MMAs, add D into S, restart D
       const int64_t cl = c - 1;
       if (!u_wait(&mma_done[cl & 1], (uint32_t)((cl >> 1) & 1)) && lane == 0) atomicExch(&s_fail, 1);
       __syncthreads();
@@ -438,31 +439,30 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-        for (int ks = 0; ks < kUKT / 16; ++ks) {
-          const uint64_t ad = u_desc(u_smem(sA) + (uint32_t)mt * (kUStageA / 2) + (uint32_t)ks * 256u);
-          const uint64_t bd = u_desc(u_smem(sB) + (uint32_t)ks * 256u);
-          const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr + (uint32_t)mt * 256u),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
-        }
+      for (int ks = 0; ks < kUKT / 16; ++ks) {
+        const uint64_t ad = u_desc(u_smem(sA) + (uint32_t)ks * 256u);
+        const uint64_t bd = u_desc(u_smem(sB) + (uint32_t)ks * 256u);
+        const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        u_smem(&mma_done[s]))
                    : "memory");
     }
     issued = c + 1;
-    // b column on the CUDA cores: row tid mod 256 of the G tile times half of
-    // the BF16 b chunk (threads 256.. take the second half of K)
+    // b column on the CUDA cores: row tid mod 128 of the G tile times a quarter
+    // of the BF16 b chunk (K quarter tid / 128)
     if (with_b) {
       const float* bc = bst + s * kUKT;
-      const int grow = tid & (kUG - 1), kh = tid / kUG;
+      const int grow = tid & (kUG - 1), kq = tid / kUG;
+      constexpr int kPer = kUKC / (kUThreads / kUG);
+      float part = 0.f;
 #pragma unroll
-      for (int k8 = kh * (kUKC / 2); k8 < (kh + 1) * (kUKC / 2); ++k8) {
+      for (int k8 = kq * kPer; k8 < (kq + 1) * kPer; ++k8) {
         const uint4 w = *reinterpret_cast<const uint4*>(sA + kmaj_off(grow, 8 * k8));
         const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * k8);
         const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * k8 + 4);
@@ -470,10 +470,14 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          sb_acc = fmaf(__uint_as_float(ws[h] << 16), bv[2 * h], sb_acc);
-          sb_acc = fmaf(__uint_as_float(ws[h] & 0xFFFF0000u), bv[2 * h + 1], sb_acc);
+          part = fmaf(__uint_as_float(ws[h] << 16), bv[2 * h], part);
+          part = fmaf(__uint_as_float(ws[h] & 0xFFFF0000u), bv[2 * h + 1], part);
         }
       }
+      const float t = sb_hi + part;                              // TwoSum (Knuth)
+      const float bb = t - sb_hi;
+      sb_lo += (sb_hi - (t - bb)) + (part - bb);
+      sb_hi = t;
     }
   }
   // wait for the last issued chunk's MMAs (commits track all earlier MMAs)
@@ -514,17 +518,9 @@ static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
   g.ksplit = (m + g.kchunk - 1) / g.kchunk;
   return g;
 }
-// Scratch tiles (one 256 x 256 FP32 tile per CTA) when a CTA's K range is
-// longer than one flush period.
-static size_t gauss_scratch_bytes(int64_t m, int64_t n, int64_t d) {
-  const GaussGrid g = gauss_grid(m, n, d);
-  if (g.kchunk <= kUFlush * kUKT) return 0;
-  return (size_t)(g.mtiles * g.ksplit * g.ntiles) * kUG * kUN * 4;
-}
-constexpr size_t kGaussScratchOffset = 8192 + 256;
-size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
-  // the BF16 table (uploaded per call), an error word, the flush tiles
-  return kGaussScratchOffset + gauss_scratch_bytes(m, n, d);
+size_t gauss_ws_bytes(int64_t, int64_t, int64_t) {
+  // the BF16 table (uploaded per call) and the error word
+  return 8192 + 256;
 }
 
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
@@ -552,9 +548,6 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   if (!use_simt) {
     const GaussGrid gg = gauss_grid(a.m, a.n, d);
     const int64_t mtiles = gg.mtiles, ntiles = gg.ntiles, ksplit = gg.ksplit, kchunk = gg.kchunk;
-    float* scratch = gauss_scratch_bytes(a.m, a.n, d)
-                         ? reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + kGaussScratchOffset)
-                         : nullptr;
     const bool bulk = (a.n % 4 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.A % 16 == 0);
     auto kern = bulk ? gauss_umma<true> : gauss_umma<false>;
     SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
@@ -563,8 +556,8 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
       SNS_PROF(K_GAUSS, st);
       kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
-          scratch, err);
+          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab,
+          kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs, err);
     }
     SNS_CUDA_TRY(cudaGetLastError());
     return SNS_OK;
@@ -579,7 +572,8 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   {
     SNS_PROF(K_GAUSS, st);
   gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab, kchunk,
+                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab,
+          kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());

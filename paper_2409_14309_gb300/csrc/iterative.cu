@@ -1008,10 +1008,14 @@ constexpr int kSmallThreads = 128;
 // epilogue.  START (v = g): r = g, dx = 0, z = s, rr = g.s and the cycle's stop
 // level (the residual must drop by max(tol / (2 eta), kInnerFloor)).  STEP
 // (v = r): beta step as above, one more pass counted, done once rr' <= stop.
+// Factored form (rs_self): P is R^-1 and v = t = R^-T r, so s = R^-1 R^-T r
+// without forming R^-1 R^-T (whose condition number kappa(R)^2 ruins it in
+// FP64 beyond kappa ~ 1e7), and r.s = t.t >= 0; START then takes the residual
+// from rsrc (g) rather than from v.
 template <bool START>
 __global__ void __launch_bounds__(kSmallThreads)
 pcg_matvec(const double* __restrict__ P, int64_t n, const double* __restrict__ v, PcgVecs V,
-           uint32_t* __restrict__ ticket, double tol) {
+           uint32_t* __restrict__ ticket, double tol, const double* __restrict__ rsrc, int rs_self) {
   __shared__ double red[kSmallThreads / 32];
   __shared__ double s_beta;
   __shared__ int s_last;
@@ -1053,7 +1057,10 @@ pcg_matvec(const double* __restrict__ P, int64_t n, const double* __restrict__ v
   __threadfence();
   if (threadIdx.x == 0) *ticket = 0;
   double rs = 0.0;
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) rs = fma(__ldcg(v + c), __ldcg(V.s + c), rs);
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    const double vc = __ldcg(v + c);
+    rs = fma(vc, rs_self ? vc : __ldcg(V.s + c), rs);
+  }
   rs = cta_sum0(rs, red);
   if (threadIdx.x == 0) {
     if (START) {
@@ -1079,7 +1086,7 @@ pcg_matvec(const double* __restrict__ P, int64_t n, const double* __restrict__ v
     double zc;
     if (START) {
       zc = sc;
-      V.rx[c] = __ldcg(v + c);
+      V.rx[c] = __ldcg((rsrc ? rsrc : v) + c);
       V.dx[c] = 0.0;
     } else {
       zc = fma(beta, V.z[c], sc);
@@ -1137,10 +1144,19 @@ sns_status pgram_build(const double* Rinv, int64_t n, double* P, cudaStream_t st
 
 static int pcg_grid(int64_t n) { return (int)std::max<int64_t>(1, (n + kSmallThreads / 32 - 1) / (kSmallThreads / 32)); }
 
-sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st) {
+sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st, bool factored) {
+  if (factored) {
+    sns_status s = saa_matvec(W.RinvT, n, W.g, W.w, false, st);        // t = R^-T g
+    if (s != SNS_OK) return s;
+  }
   {
     SNS_PROF(K_MATVEC, st);
-    pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.g, pcg_vecs(W), W.ticket + kPcgTicket, tol);
+    if (factored)
+      pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.Rinv, n, W.w, pcg_vecs(W), W.ticket + kPcgTicket,
+                                                               tol, W.g, 1);
+    else
+      pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.g, pcg_vecs(W), W.ticket + kPcgTicket, tol,
+                                                               nullptr, 0);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
@@ -1148,16 +1164,65 @@ sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st) {
 sns_status pcg_start_rhs(const IterWs& W, int64_t n, double tol, const double* v, cudaStream_t st) {
   {
     SNS_PROF(K_MATVEC, st);
-    pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, v, pcg_vecs(W), W.ticket + kPcgTicket, tol);
+    pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, v, pcg_vecs(W), W.ticket + kPcgTicket, tol,
+                                                             nullptr, 0);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
-sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st) {
+sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st, bool factored) {
+  if (factored) {
+    // t = R^-T r into w (the pass's w is consumed by its own epilogue)
+    sns_status s = saa_matvec(W.RinvT, n, W.rx, W.w, false, st);
+    if (s != SNS_OK) return s;
+  }
   {
     SNS_PROF(K_MATVEC, st);
-    SNS_CUDA_TRY(launch_dependent(pcg_matvec<false>, dim3(pcg_grid(n)), dim3(kSmallThreads), 0, st, W.P, n, W.rx,
-                                  pcg_vecs(W), W.ticket + kPcgTicket, 0.0));
+    if (factored)
+      SNS_CUDA_TRY(launch_dependent(pcg_matvec<false>, dim3(pcg_grid(n)), dim3(kSmallThreads), 0, st, W.Rinv, n,
+                                    W.w, pcg_vecs(W), W.ticket + kPcgTicket, 0.0, (const double*)nullptr, 1));
+    else
+      SNS_CUDA_TRY(launch_dependent(pcg_matvec<false>, dim3(pcg_grid(n)), dim3(kSmallThreads), 0, st, W.P, n, W.rx,
+                                    pcg_vecs(W), W.ticket + kPcgTicket, 0.0, (const double*)nullptr, 0));
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+
+// max |R_ii| and min |R_ii| over i < n of the column-major W (leading dim ldw).
+__global__ void __launch_bounds__(kSmallThreads) diag_range_kernel(const double* __restrict__ W, int64_t ldw,
+                                                                   int64_t n, double* __restrict__ out) {
+  __shared__ double rmax[kSmallThreads / 32], rmin[kSmallThreads / 32];
+  double mx = 0.0, mn = INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs(W[i * ldw + i]);
+    mx = fmax(mx, a);
+    mn = fmin(mn, a);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rmax[threadIdx.x >> 5] = mx;
+    rmin[threadIdx.x >> 5] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kSmallThreads / 32; ++w) {
+      mx = fmax(mx, rmax[w]);
+      mn = fmin(mn, rmin[w]);
+    }
+    mx = fmax(mx, rmax[0]);
+    mn = fmin(mn, rmin[0]);
+    out[0] = mx;
+    out[1] = mn;
+  }
+}
+sns_status diag_range(const double* W, int64_t ldw, int64_t n, double* out, cudaStream_t st) {
+  {
+    SNS_PROF(K_QR, st);
+    diag_range_kernel<<<1, kSmallThreads, 0, st>>>(W, ldw, n, out);
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;

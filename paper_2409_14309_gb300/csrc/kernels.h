@@ -38,10 +38,16 @@ struct CsLayout {
 bool cs_tma_eligible(const DenseArgs& a);
 int64_t cs_tma_parts(int64_t m, int64_t d);
 int64_t cs_warp_max_chunks(int64_t m, int64_t d);
-// allow_bulk: the bulk-copy gather (selected by SNSOLVE_CS_GATHER=t) may be used;
-// otherwise the warp gather, which has no device-side waits, always runs.
+// allow_bulk: kernels with bounded device-side waits may run (the cooperative
+// plan with its grid barriers; the bulk-copy gather when SNSOLVE_CS_GATHER=t);
+// otherwise the two-kernel plan and the warp gather, which never wait, run.
 sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
                          float* Sb, int64_t sbs, cudaStream_t st, bool allow_bulk = true);
+// Single-launch plan (cooperative) + warp gather for dense FP32; *used = false
+// when the plan's blocks cannot all be co-resident (nothing launched then).
+sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, float* SA,
+                         int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st, bool* used);
+bool cs_bulk_gather_selected();
 CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr);
 int64_t cs_sorted_max_d();
 int num_sms();
@@ -130,8 +136,13 @@ sns_status iter_reset(const IterWs& W, cudaStream_t st);
 // iteration; the cycle ends on the device once the CG residual has dropped by
 // max(tol / (2 eta), 4e-3) (later launches return at once) or the host's
 // launch budget runs out.  pcg_apply adds dx to x.
-sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st);
-sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st);
+// factored: apply M^-1 as R^-1 (R^-T r) (two n x n products) instead of the
+// formed P = R^-1 R^-T, whose FP64 rounding (relative to kappa(R)^2) makes it
+// indefinite for badly conditioned R.
+sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st, bool factored = false);
+sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st, bool factored = false);
+// out[0] = max |R_ii|, out[1] = min |R_ii| (device), i < n, W column-major.
+sns_status diag_range(const double* W, int64_t ldw, int64_t n, double* out, cudaStream_t st);
 sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st);
 sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t st);
 

@@ -66,6 +66,47 @@ def test_countsketch_dense_f64(m, n, d):
     assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 3), scale) <= 1e-14
 
 
+@pytest.mark.parametrize("m,n,d", [(5, 4, 4), (4096, 64, 256), (1048577, 256, 1024), (300001, 36, 8192)])
+def test_single_launch_plan_equals_two_kernel_plan(m, n, d):
+    """The deterministic CountSketch's plan (hash, stable per-block bucket
+    order, bucket-major row list) runs as one cooperative launch in
+    snsolve_sketch and as two plain kernels in the allocation-free entry point;
+    both feed the same gather, so SA and Sb must agree bit for bit."""
+    import ctypes as C
+    import paper_2409_14309_gb300 as sns
+    from paper_2409_14309_gb300 import abi
+    c = ctx()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(m + d)
+    A = torch.randn(m, n, generator=g, device="cuda")
+    b = torch.randn(m, generator=g, device="cuda")
+    SA, Sb = c.sketch(A, b, d, seed=4, variant="sorted")
+    SA2 = torch.full_like(SA, float("nan"))
+    Sb2 = torch.full_like(Sb, float("nan"))
+    prob = sns.dense_problem(A, b)
+    code = abi.lib().snsolve_sketch_countsketch_static(
+        C.byref(prob), d, 4, C.c_void_p(SA2.data_ptr()), n, C.c_void_p(Sb2.data_ptr()),
+        C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if code == abi.SNS_ENOMEM:
+        pytest.skip("problem larger than the fixed scratch of the allocation-free entry point")
+    assert code == 0
+    torch.cuda.synchronize()
+    assert torch.equal(SA, SA2) and torch.equal(Sb, Sb2)
+
+
+def test_countsketch_many_plan_blocks():
+    """2^22 + 5 rows: 1025 plan blocks, all co-resident in the cooperative plan."""
+    c = ctx()
+    m, n, d = (1 << 22) + 5, 8, 1024
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    SA, Sb = c.sketch(dev(A), dev(b), d, seed=6, variant="sorted")
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
+    assert rel_fro(SA.cpu().numpy(), OS.countsketch_apply(A, d, 6), scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 6), scale) <= TOL32
+
+
 def test_sorted_variant_bitwise_reproducible():
     c = ctx()
     rng = np.random.default_rng(5)
@@ -185,8 +226,8 @@ def test_gaussian_sketch_tensor_core(m, n, d):
     ref = OS.gaussian_apply(A, d, 13, bf16_operand=True)
     refb = OS.gaussian_apply(b, d, 13, bf16_operand=True)
     scale = np.sqrt(np.linalg.norm(ref) ** 2 + np.linalg.norm(refb) ** 2)
-    assert rel_fro(SA.cpu().numpy(), ref, scale) <= 1e-5
-    assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-5
+    assert rel_fro(SA.cpu().numpy(), ref, scale) <= 1e-6
+    assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-6
 
 
 def test_gaussian_simt_variant_in_subprocess():

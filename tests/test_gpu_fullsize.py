@@ -91,8 +91,8 @@ def test_full_size_gaussian_sampled_rows(problem):
     ref = OS.gaussian_rows(A, D, 1, rows)
     refb = OS.gaussian_rows(b, D, 1, rows)
     # FP32 accumulation of 2^20 BF16 products per entry
-    assert rel_fro(SA.cpu().numpy()[rows], ref, np.linalg.norm(ref)) <= 1e-5
-    assert rel_fro(Sb.cpu().numpy()[rows], refb, np.linalg.norm(refb)) <= 1e-5
+    assert rel_fro(SA.cpu().numpy()[rows], ref, np.linalg.norm(ref)) <= 1e-6
+    assert rel_fro(Sb.cpu().numpy()[rows], refb, np.linalg.norm(refb)) <= 1e-6
 
 
 def test_full_size_srht_sampled_rows(problem):

@@ -45,7 +45,7 @@ def test_sorted_countsketch_parts_sum_exactly():
 
 
 @pytest.mark.parametrize("kind,variant,tol", [("countsketch", "stream", 1e-6), ("sparse_sign", "4", 1e-6),
-                                              ("gaussian", "auto", 1e-5)])
+                                              ("gaussian", "auto", 1e-6)])
 def test_float_reduction_sketches_parts_sum(kind, variant, tol):
     c = ctx()
     rng = np.random.default_rng(6)

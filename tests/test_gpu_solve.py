@@ -101,7 +101,7 @@ def test_xhat_parity_at_kappa_1e6(kind):
           f"x^ vs oracle {e_x:.3e} (first-order bound {bound:.3e})")
     if kind in ("countsketch", "srht"):
         assert e_solve <= 1e3 * kappa * 2.0 ** -53, e_solve
-    assert e_sa <= (1e-5 if kind == "gaussian" else 1e-6), e_sa
+    assert e_sa <= 1e-6, e_sa
     assert e_x <= max(1e-4, 2.0 * bound), (e_x, bound)
 
 
