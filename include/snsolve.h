@@ -84,9 +84,8 @@ typedef enum {
  * Flood 2014): output i of stream t is mix64((seed ^ (t << 56)) + (i+1)*gamma).
  * CountSketch (t = 0): h(i) = ((k mod 2^32) * d) >> 32, s(i) = bit 63 ? -1 : +1.
  * SRHT: signs from t = 1, d distinct rows of [0, m') by Floyd's algorithm on t = 2.
- * Gaussian: G[k, i] = T[top 12 bits of 16-bit field (k div 8) mod 4 of output
- * i*G + 8*(k div 32) + (k mod 8) of t = 3], G = 8*ceil(d/32),
- * T[j] = BF16(Phi^-1((j + 1/2)/4096)).
+ * Gaussian: G[k, i] = T[byte (i mod 8) of output (i div 8)*d + k of t = 3],
+ * T[j] = BF16(Phi^-1((j + 1/2)/256)).
  * Sparse sign: draw z of column i uses output i of t = 0 (z = 0; zeta = 1 is the
  * CountSketch) or output i*(zeta-1) + z-1 of t = 4; rows by Floyd's algorithm on
  * [0, d): u = ((k mod 2^32)*(J+1)) >> 32 with J = d - zeta + z, or J if an earlier
@@ -199,8 +198,9 @@ sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc*
  * matrix, and S [A_full | b_full] is the sum of the parts' outputs (one sum,
  * e.g. an all-reduce of the d x (n+1) partials).  prob describes the local
  * rows (prob->m of them); the rest is as in snsolve_sketch.  CountSketch (all
- * variants), Gaussian and sparse sign sketches; SRHT mixes all rows through
- * its Hadamard transform and is rejected (SNS_EINVAL), as is row0 < 0. */
+ * variants), Gaussian (row0 a multiple of 8: one hash serves 8 consecutive
+ * rows) and sparse sign sketches; SRHT mixes all rows through its Hadamard
+ * transform and is rejected (SNS_EINVAL), as is row0 < 0. */
 sns_status snsolve_sketch_rows(sns_ctx* ctx, const sns_problem* prob, const sns_sketch_desc* sk, int64_t row0,
                                void* SA, int64_t ldsa, void* Sb, void* ws, size_t ws_bytes, void* stream);
 

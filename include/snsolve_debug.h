@@ -39,8 +39,8 @@ sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes);
 sns_status snsolve_debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* idx, void* ws, size_t ws_bytes,
                                      void* stream);
 
-/* The 4096-entry BF16 normal-quantile table T of the Gaussian sketch
- * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array. */
+/* The 256-entry BF16 normal-quantile table T of the Gaussian sketch
+ * (Sec. 1.2.1), as raw BF16 bit patterns, written to a HOST array of 256. */
 sns_status snsolve_debug_gaussian_table(uint16_t* bf16_bits_host);
 
 /* Y = A R^-1, the explicit preconditioned matrix of sketch-and-apply (SNS_SAA,

@@ -7,13 +7,12 @@ Three families, as the paper lists them:
   per column of S, S[h(i), i] = s(i).  Reading: no scaling (E[S^T S] = I already,
   and a common scale does not change the minimiser).
 * Gaussian (Sec. 1.2.1): S = G / sqrt(d) with G iid Gaussian.  Reading (the paper
-  fixes no generator): G[k, i] = T[j], j a 12-bit index drawn from the hash
-  stream, T[j] the BF16-rounded normal quantile Phi^{-1}((j + 1/2) / 4096).  One
-  SplitMix64 output of stream 3 serves the four rows k = 32 b + l + 8 q
-  (q = 0..3) of group g = 8 b + l (l = k mod 8, b = k div 32): row k uses 16-bit
-  field q = (k div 8) mod 4 of output i * G + g, G = 8 ceil(d / 32), and j is the
-  top 12 bits of that field.  The tensor-core path multiplies BF16 operands, so
-  the oracle offers SA for both the exact A and the BF16-rounded A.
+  fixes no generator): G[k, i] = T[j], j an 8-bit index drawn from the hash
+  stream, T[j] the BF16-rounded normal quantile Phi^{-1}((j + 1/2) / 256).  One
+  SplitMix64 output of stream 3 serves eight consecutive columns of one row:
+  entry (k, i) uses byte (i mod 8) of output (i div 8) * d + k.  The
+  tensor-core path multiplies BF16 operands, so the oracle offers SA for both
+  the exact A and the BF16-rounded A.
 * Subsampled randomized Hadamard (Sec. 1.2.1): S = (1/sqrt(d)) P H D with
   m' = 2^ceil(log2 m) (rows m..m'-1 of [A | b] are zero), H the unnormalised
   Sylvester-Hadamard matrix H[p, i] = (-1)^popcount(p & i) applied by the fast
@@ -89,32 +88,24 @@ def round_to_bf16_via_f32(x):
 
 # ---------------------------------------------------------------- Gaussian
 
-GAUSS_TABLE_BITS = 12
+GAUSS_TABLE_BITS = 8
 
 
 def gaussian_table():
-    """T[j] = BF16(Phi^{-1}((j + 1/2) / 4096)), j = 0..4095, as FP64."""
+    """T[j] = BF16(Phi^{-1}((j + 1/2) / 256)), j = 0..255, as FP64."""
     n = 1 << GAUSS_TABLE_BITS
     q = ndtri((np.arange(n, dtype=np.float64) + 0.5) / n)
     return round_to_bf16(q)
 
 
-def gaussian_groups(d):
-    """Number of hash groups per column of G: 8 per block of 32 rows."""
-    return 8 * ((d + 31) // 32)
-
-
 def gaussian_indices(m, d, seed):
-    """Table index j[k, i] (d x m, int64) of every entry of G."""
-    groups = gaussian_groups(d)
+    """Table index j[k, i] (d x m, int64) of every entry of G: byte (i mod 8)
+    of output (i div 8) * d + k of stream 3."""
     i = np.arange(m, dtype=np.uint64)[None, :]
     k = np.arange(d, dtype=np.uint64)[:, None]
-    g = (k // np.uint64(32)) * np.uint64(8) + (k % np.uint64(8))
-    q = (k // np.uint64(8)) % np.uint64(4)
-    counter = i * np.uint64(groups) + g
+    counter = (i // np.uint64(8)) * np.uint64(d) + k
     key = H.splitmix64_at(H.stream_state(seed, H.STREAM_GAUSSIAN), counter)
-    field = (key >> (np.uint64(16) * q)) & np.uint64(0xFFFF)
-    return (field >> np.uint64(4)).astype(np.int64)
+    return ((key >> (np.uint64(8) * (i % np.uint64(8)))) & np.uint64(0xFF)).astype(np.int64)
 
 
 def gaussian_matrix(m, d, seed):
@@ -252,16 +243,12 @@ def gaussian_rows(A, d, seed, rows, bf16_operand=True):
     m = A.shape[0]
     Ause = round_to_bf16_via_f32(A) if bf16_operand else A.astype(np.float64)
     T = gaussian_table()
-    groups = gaussian_groups(d)
     i = np.arange(m, dtype=np.uint64)
     state = H.stream_state(seed, H.STREAM_GAUSSIAN)
     out = []
     for k in rows:
-        k = np.uint64(k)
-        g = (k // np.uint64(32)) * np.uint64(8) + (k % np.uint64(8))
-        q = (k // np.uint64(8)) % np.uint64(4)
-        key = H.splitmix64_at(state, i * np.uint64(groups) + g)
-        idx = ((key >> (np.uint64(16) * q)) & np.uint64(0xFFFF)) >> np.uint64(4)
+        key = H.splitmix64_at(state, (i // np.uint64(8)) * np.uint64(d) + np.uint64(k))
+        idx = (key >> (np.uint64(8) * (i % np.uint64(8)))) & np.uint64(0xFF)
         out.append(T[idx.astype(np.int64)] @ Ause / math.sqrt(d))
     return np.array(out)
 

@@ -308,7 +308,7 @@ class Server:
 
 
 def gaussian_table_bits():
-    """The library's BF16 normal-quantile table as 4096 raw uint16 values (host call)."""
-    buf = (C.c_uint16 * 4096)()
+    """The library's BF16 normal-quantile table as 256 raw uint16 values (host call)."""
+    buf = (C.c_uint16 * 256)()
     _check(abi.lib().snsolve_debug_gaussian_table(buf), "snsolve_debug_gaussian_table")
     return list(buf)

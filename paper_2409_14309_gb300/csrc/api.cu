@@ -343,6 +343,7 @@ sns_status snsolve_sketch_rows(sns_ctx* ctx, const sns_problem* prob, const sns_
   if (s == SNS_OK) s = validate_sketch(prob, sk);
   if (s != SNS_OK) return s;
   if (row0 < 0 || row0 > ((int64_t)1 << 40) || sk->kind == SNS_SRHT || ldsa < prob->n) return SNS_EINVAL;
+  if (sk->kind == SNS_GAUSSIAN && row0 % 8 != 0) return SNS_EINVAL;   // one hash serves 8 consecutive rows
   if (ws_bytes < sketch_ws(prob, sk) || (ws_bytes > 0 && !ws && sketch_ws(prob, sk) > 0)) return SNS_ENOMEM;
   if (ws && ((uintptr_t)ws % 256)) return SNS_EINVAL;
   return run_sketch(prob, sk, SA, ldsa, Sb, 1, ws, ws_bytes, static_cast<cudaStream_t>(stream), row0);

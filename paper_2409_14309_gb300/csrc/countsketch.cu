@@ -74,7 +74,8 @@ CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr) {
   const int64_t maxch = wg ? cs_warp_max_chunks(m, d) : 0;
   L.off_cbase = take(wg ? (size_t)(d + 1) * 4 : 0);
   L.off_ctab = take((size_t)maxch * 4);
-  L.off_wpart = take((size_t)maxch * ((n + 127) / 128) * (128 + 4) * 4);
+  // chunk partial rows of the warp gather, for either column tile (128 or 256)
+  L.off_wpart = take((size_t)maxch * std::max<int64_t>(((n + 127) / 128) * (128 + 4), ((n + 255) / 256) * (256 + 4)) * 4);
   L.bytes = off;
   return L;
 }

@@ -257,16 +257,28 @@ SNS_D uint32_t block_scan_buckets(uint32_t d, F&& f, uint32_t* out, uint32_t* ws
   return total;
 }
 
+// Lanes of the warp holding the same value v (< 2^nbits) as this lane: one
+// ballot per bit, the same mask __match_any_sync returns (warp multisplit).
+SNS_D unsigned equal_lanes(uint32_t v, int nbits) {
+  unsigned peers = 0xffffffffu;
+  for (int bit = 0; bit < nbits; ++bit) {
+    const bool set = (v >> bit) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, set);
+    peers &= set ? bal : ~bal;
+  }
+  return peers;
+}
+
 __global__ void __launch_bounds__(kPlanWarps * 32)
 cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restrict__ seg,
              uint32_t* __restrict__ ticket, int64_t nticket, uint32_t* __restrict__ btot, uint32_t* __restrict__ bbase,
              uint32_t* __restrict__ list, uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab,
              float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int64_t n,
-             uint32_t* __restrict__ bar, int* __restrict__ err) {
+             uint32_t* __restrict__ bar, int* __restrict__ err, int nbits) {
   extern __shared__ __align__(16) uint8_t psm[];
   uint16_t* cnt = reinterpret_cast<uint16_t*>(psm);                 // [W][d] per-warp counts, then offsets
   uint16_t* hb = cnt + (size_t)kPlanWarps * d;                       // [R] bucket | sign << 15
-  uint32_t* sb = reinterpret_cast<uint32_t*>(hb + kListRowsPerBlock);  // [d] bases (phase C)
+  uint32_t* sb = reinterpret_cast<uint32_t*>(hb + kListRowsPerBlock);  // [d] bases, then [d] totals (phase C)
   __shared__ uint32_t wsum[kPlanWarps];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t blk = blockIdx.x;
@@ -274,6 +286,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
   const uint32_t G = gridDim.x;
   constexpr int kRowsPerWarp = kListRowsPerBlock / kPlanWarps;
   constexpr uint32_t kNone = 0xFFFFu;
+  const uint32_t kOut = (1u << nbits) - 1u;        // >= d: groups the rows past m in the masks
 
   // ---- A: hash, per-warp histograms, block totals
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < nticket; i += (int64_t)G * blockDim.x) ticket[i] = 0;
@@ -289,7 +302,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
       sgn = (uint32_t)(key >> 63);
     }
     hb[loc] = (uint16_t)(h == kNone ? kNone : (h | (sgn << 15)));
-    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    const unsigned peers = equal_lanes(h == kNone ? kOut : h, nbits);
     if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
     __syncwarp();
   }
@@ -307,33 +320,48 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
   const bool ok1 = grid_barrier(bar, G, err);
 
   // ---- B: per bucket, exclusive scan of the block totals; bucket totals
+  // (the block totals of 8 rounds of 32 blocks are loaded at once)
   if (ok1) {
+    constexpr int kAhead = 8;
     for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
       uint32_t* sk = seg + (size_t)k * nblk;
       uint32_t run = 0;
-      for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
-        const int64_t b = b0 + lane;
-        const uint32_t c = b < nblk ? __ldcg(sk + b) : 0u;
-        uint32_t incl = c;
+      for (int64_t b0 = 0; b0 < nblk; b0 += 32 * kAhead) {
+        uint32_t cv[kAhead];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
+        for (int r = 0; r < kAhead; ++r) {
+          const int64_t b = b0 + r * 32 + lane;
+          cv[r] = b < nblk ? __ldcg(sk + b) : 0u;
         }
-        if (b < nblk) sk[b] = run + incl - c;
-        run += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+        for (int r = 0; r < kAhead; ++r) {
+          const int64_t b = b0 + r * 32 + lane;
+          const uint32_t c = cv[r];
+          uint32_t incl = c;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+          }
+          if (b < nblk) sk[b] = run + incl - c;
+          run += __shfl_sync(0xffffffffu, incl, 31);
+        }
       }
       if (lane == 0) btot[k] = run;
     }
   }
   if (!grid_barrier(bar, 2 * G, err)) return;           // CTA-uniform
 
-  // ---- C: bases, chunk tables, empty buckets, scatter
+  // ---- C: bases, chunk tables, empty buckets, scatter.  The bucket totals
+  // are read from L2 once, into shared memory beside the bases.
+  uint32_t* stot = sb + d;
+  for (int k = tid; k < (int)d; k += blockDim.x) stot[k] = __ldcg(btot + k);
+  __syncthreads();
   const uint32_t nchunks =
-      block_scan_buckets(d, [&](int k) { return (__ldcg(btot + k) + kChunkRows - 1) / kChunkRows; }, sb, wsum);
+      block_scan_buckets(d, [&](int k) { return (stot[k] + kChunkRows - 1) / kChunkRows; }, sb, wsum);
   if (blockIdx.x == 0 && tid == 0) cbase[d] = nchunks;
   for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
-    const uint32_t len = __ldcg(btot + k);
+    const uint32_t len = stot[k];
     const uint32_t nch = (len + kChunkRows - 1) / kChunkRows;
     for (uint32_t c = lane; c < nch; c += 32) ctab[sb[k] + c] = (uint32_t)k;
     if (lane == 0) cbase[k] = sb[k];
@@ -343,7 +371,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
       if (lane == 0) Sb[k * sbs] = 0.f;
     }
   }
-  block_scan_buckets(d, [&](int k) { return __ldcg(btot + k); }, sb, wsum);
+  block_scan_buckets(d, [&](int k) { return stot[k]; }, sb, wsum);
   for (int k = tid; k < (int)d; k += blockDim.x) {
     if (blockIdx.x == 0) bbase[k] = sb[k];
     sb[k] += __ldcg(seg + (size_t)k * nblk + blk);            // this block's start in bucket k
@@ -355,7 +383,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
     const int64_t row = r0 + loc;
     const uint32_t hw = hb[loc];
     const uint32_t h = hw == kNone ? kNone : (hw & 0x7FFFu);
-    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    const unsigned peers = equal_lanes(h == kNone ? kOut : h, nbits);
     if (h != kNone) {
       const uint32_t pos = sb[h] + cnt[w * d + h] + __popc(peers & lt);
       if (pos < (uint64_t)m) list[pos] = (uint32_t)row | ((hw >> 15) << 31);
@@ -367,7 +395,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
 }
 
 size_t cs_plan_smem(int64_t d) {
-  return (size_t)kPlanWarps * d * 2 + (size_t)kListRowsPerBlock * 2 + (size_t)d * 4;
+  return (size_t)kPlanWarps * d * 2 + (size_t)kListRowsPerBlock * 2 + (size_t)d * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -597,9 +625,11 @@ cs_gather_tma(const float* __restrict__ A, int64_t lda, const float* __restrict_
 // warp to finish a (bucket, tile) (ticket) adds the bucket's chunk rows in
 // chunk order.  A bucket with one chunk is written directly.  Which warp runs
 // an item does not change its arithmetic, so results are deterministic.
+// VPL float4 per lane per row (column tile CT = 128 VPL: 512 B or whole 1 KB
+// rows at n = 256), U rows in flight per warp.
 constexpr int kWarpCT = 128;
-constexpr int kWarpU = 8;
-__global__ void __launch_bounds__(256, 3)
+template <int VPL, int U>
+__global__ void __launch_bounds__(256, VPL == 1 ? 3 : 2)
 cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t n, int64_t ntile,
                const uint32_t* __restrict__ list, const uint32_t* __restrict__ btot,
                const uint32_t* __restrict__ bbase, const uint32_t* __restrict__ cbase,
@@ -641,9 +671,16 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
     const int64_t g = cur.g, t = g % ntile;
     const uint32_t k = cur.k;
     const int64_t len = cur.len, lo = cur.lo, hi = cur.hi;
-    const int64_t col0 = t * kWarpCT;
-    const bool okc = col0 + lane * 4 < n;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), e0 = a0;   // even / odd rows
+    constexpr int CT = 128 * VPL;
+    const int64_t col0 = t * CT;
+    bool okc[VPL];
+    float4 a0[VPL], e0[VPL];                                 // even / odd rows
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      okc[v] = col0 + v * 128 + lane * 4 < n;
+      a0[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+      e0[v] = a0[v];
+    }
     float accb = 0.f;
     uint32_t rid_next = (lo + lane < hi) ? __ldg(list + lo + lane) : 0u;
     for (int64_t j0 = lo; j0 < hi; j0 += 32) {
@@ -655,40 +692,53 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
         const float bv = __ldg(b + (rid_l & 0x7FFFFFFFu));
         accb += (rid_l >> 31) ? -bv : bv;
       }
-      for (int r = 0; r < nr; r += kWarpU) {
-        float4 x[kWarpU];
-        uint32_t rid[kWarpU];
+      for (int r = 0; r < nr; r += U) {
+        float4 x[U][VPL];
+        uint32_t rid[U];
 #pragma unroll
-        for (int u = 0; u < kWarpU; ++u) {
+        for (int u = 0; u < U; ++u) {
           rid[u] = __shfl_sync(0xffffffffu, rid_l, (r + u) & 31);
-          const bool ok = ((r + u) < nr) && okc;
           const float* rp = A + (int64_t)(rid[u] & 0x7FFFFFFFu) * lda + col0 + lane * 4;
-          x[u] = ok ? __ldg(reinterpret_cast<const float4*>(rp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) {
+            const bool ok = ((r + u) < nr) && okc[v];
+            x[u][v] = ok ? __ldg(reinterpret_cast<const float4*>(rp + v * 128)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
 #pragma unroll
-        for (int u = 0; u < kWarpU; ++u) {
+        for (int u = 0; u < U; ++u) {
           const float sg = (rid[u] >> 31) ? -1.f : 1.f;
-          float4& p0 = (u & 1) ? e0 : a0;
-          p0.x = fmaf(sg, x[u].x, p0.x);
-          p0.y = fmaf(sg, x[u].y, p0.y);
-          p0.z = fmaf(sg, x[u].z, p0.z);
-          p0.w = fmaf(sg, x[u].w, p0.w);
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) {
+            float4& p0 = (u & 1) ? e0[v] : a0[v];
+            p0.x = fmaf(sg, x[u][v].x, p0.x);
+            p0.y = fmaf(sg, x[u][v].y, p0.y);
+            p0.z = fmaf(sg, x[u][v].z, p0.z);
+            p0.w = fmaf(sg, x[u][v].w, p0.w);
+          }
         }
       }
     }
-    a0.x += e0.x; a0.y += e0.y; a0.z += e0.z; a0.w += e0.w;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      a0[v].x += e0[v].x; a0[v].y += e0[v].y; a0[v].z += e0[v].z; a0[v].w += e0[v].w;
+    }
     accb = warp_sum(accb);
     const int64_t nch_k = (len + kChunkRows - 1) / kChunkRows;
     if (nch_k == 1) {
-      float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
-      if (okc) { out[0] = a0.x; out[1] = a0.y; out[2] = a0.z; out[3] = a0.w; }
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        float* out = SA + (int64_t)k * ldsa + col0 + v * 128 + lane * 4;
+        if (okc[v]) { out[0] = a0[v].x; out[1] = a0[v].y; out[2] = a0[v].z; out[3] = a0[v].w; }
+      }
       if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = accb;
       cur = nxt;
       continue;
     }
-    float* pr = part + (size_t)g * (kWarpCT + 4);
-    reinterpret_cast<float4*>(pr)[lane] = a0;
-    if (lane == 0) pr[kWarpCT] = accb;
+    float* pr = part + (size_t)g * (CT + 4);
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) reinterpret_cast<float4*>(pr)[v * 32 + lane] = a0[v];
+    if (lane == 0) pr[CT] = accb;
     __threadfence();
     __syncwarp();
     uint32_t old = 0;
@@ -701,16 +751,24 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
     __threadfence();
     // last warp of bucket k, tile t: add the chunk rows in chunk order
     const int64_t g0 = (int64_t)__ldg(cbase + k) * ntile + t;
-    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 s0[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) s0[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     float sb = 0.f;
     for (int64_t q = 0; q < nch_k; ++q) {
-      const float* pq = part + (size_t)(g0 + q * ntile) * (kWarpCT + 4);
-      const float4 v0 = __ldcg(reinterpret_cast<const float4*>(pq) + lane);
-      s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
-      sb += __ldcg(pq + kWarpCT);
+      const float* pq = part + (size_t)(g0 + q * ntile) * (CT + 4);
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const float4 v0 = __ldcg(reinterpret_cast<const float4*>(pq) + v * 32 + lane);
+        s0[v].x += v0.x; s0[v].y += v0.y; s0[v].z += v0.z; s0[v].w += v0.w;
+      }
+      sb += __ldcg(pq + CT);
     }
-    float* out = SA + (int64_t)k * ldsa + col0 + lane * 4;
-    if (okc) { out[0] = s0.x; out[1] = s0.y; out[2] = s0.z; out[3] = s0.w; }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      float* out = SA + (int64_t)k * ldsa + col0 + v * 128 + lane * 4;
+      if (okc[v]) { out[0] = s0[v].x; out[1] = s0[v].y; out[2] = s0[v].z; out[3] = s0[v].w; }
+    }
     if (t == 0 && lane == 0) Sb[(int64_t)k * sbs] = sb;
     cur = nxt;
   }
@@ -752,6 +810,53 @@ static sns_status launch_tma(const DenseArgs& a, int64_t d, const CsLayout& L, u
   return SNS_OK;
 }
 
+// Column tile of the warp gather: 1 = 512-byte half rows (128 columns), 2 =
+// whole 1 KB rows (256 columns) per work item.  Default: whole rows when n > 128
+// (measured at 2^20 x 256: gather 0.177 ms vs 0.184 ms with half rows, 0.186 ms
+// with whole rows and 4 rows in flight); SNSOLVE_CS_WARP_TILE=128|256|256u4
+// overrides it.
+static int warp_tile_choice() {
+  static const int sel = [] {
+    const char* e = getenv("SNSOLVE_CS_WARP_TILE");
+    if (!e) return 0;
+    if (e[0] == '2' && e[3] == 'u') return 3;
+    return e[0] == '2' ? 2 : 1;
+  }();
+  return sel;
+}
+template <int VPL, int U>
+static sns_status launch_warp_gather_t(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA,
+                                       int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st) {
+  constexpr int CT = 128 * VPL;
+  const int64_t ntile = (a.n + CT - 1) / CT;
+  auto kern = cs_gather_warp<VPL, U>;
+  int occ = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
+  const int64_t grid2 = (int64_t)num_sms() * std::max(occ, 1);
+  {
+    SNS_PROF(K_CS_GATHER, st);
+    kern<<<(unsigned)grid2, 256, 0, st>>>(
+        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile,
+        reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
+        reinterpret_cast<const uint32_t*>(ws + L.off_bbase), reinterpret_cast<const uint32_t*>(ws + L.off_cbase),
+        reinterpret_cast<const uint32_t*>(ws + L.off_ctab), (uint32_t)d, reinterpret_cast<uint32_t*>(ws + L.off_ticket),
+        reinterpret_cast<uint32_t*>(ws + L.off_err) + 1, reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb,
+        sbs, reinterpret_cast<const int*>(ws + L.off_err));
+  }
+  SNS_CUDA_TRY(cudaGetLastError());
+  return SNS_OK;
+}
+static sns_status launch_warp_gather(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA,
+                                     int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st) {
+  int choice = warp_tile_choice();
+  if (choice == 0) choice = a.n > 128 ? 2 : 1;
+  switch (choice) {
+    case 2: return launch_warp_gather_t<2, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+    case 3: return launch_warp_gather_t<2, 4>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+    default: return launch_warp_gather_t<1, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+  }
+}
+
 sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA, int64_t ldsa,
                          float* Sb, int64_t sbs, cudaStream_t st, bool allow_bulk) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + 7) / 8, (int64_t)num_sms() * 4));
@@ -773,21 +878,7 @@ sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8
   if (use_tma)
     return a.n <= 128 ? launch_tma<128>(a, d, L, ws, SA, ldsa, Sb, sbs, st)
                       : launch_tma<256>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
-  const int64_t ntile = (a.n + kWarpCT - 1) / kWarpCT;
-  int occ = 0;
-  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_gather_warp, 256, 0));
-  const int64_t grid2 = (int64_t)num_sms() * std::max(occ, 1);
-  {
-    SNS_PROF(K_CS_GATHER, st);
-    cs_gather_warp<<<(unsigned)grid2, 256, 0, st>>>(
-        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile,
-        reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
-        reinterpret_cast<const uint32_t*>(ws + L.off_bbase), cbase, ctab, (uint32_t)d,
-        reinterpret_cast<uint32_t*>(ws + L.off_ticket), reinterpret_cast<uint32_t*>(ws + L.off_err) + 1,
-        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs, reinterpret_cast<const int*>(ws + L.off_err));
-  }
-  SNS_CUDA_TRY(cudaGetLastError());
-  return SNS_OK;
+  return launch_warp_gather(a, d, L, ws, SA, ldsa, Sb, sbs, st);
 }
 
 bool cs_bulk_gather_selected() {
@@ -824,26 +915,16 @@ sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsL
   uint32_t* ctab = reinterpret_cast<uint32_t*>(ws + L.off_ctab);
   uint32_t* bar = reinterpret_cast<uint32_t*>(ws + L.off_err) + 2;
   int* err = reinterpret_cast<int*>(ws + L.off_err);
+  int nbits = 1;                                   // bit length of d
+  while (((int64_t)1 << nbits) <= d) ++nbits;
   void* args[] = {&m, &dd, &s0, &nblk, &seg, &ticket, &nticket, &btot, &bbase, &list, &cbase, &ctab,
-                  &SA, &ldsa_, &Sb, &sbs_, &n, &bar, &err};
+                  &SA, &ldsa_, &Sb, &sbs_, &n, &bar, &err, &nbits};
   {
     SNS_PROF(K_CS_SORT, st);
     SNS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cs_plan_coop, dim3((unsigned)nblk), dim3(kPlanWarps * 32),
                                              args, smem, st));
   }
-  const int64_t ntile = (a.n + kWarpCT - 1) / kWarpCT;
-  int gocc = 0;
-  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gocc, cs_gather_warp, 256, 0));
-  const int64_t grid2 = (int64_t)num_sms() * std::max(gocc, 1);
-  {
-    SNS_PROF(K_CS_GATHER, st);
-    cs_gather_warp<<<(unsigned)grid2, 256, 0, st>>>(
-        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile, list, btot, bbase, cbase,
-        ctab, (uint32_t)d, ticket, reinterpret_cast<uint32_t*>(ws + L.off_err) + 1,
-        reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb, sbs, err);
-  }
-  SNS_CUDA_TRY(cudaGetLastError());
-  return SNS_OK;
+  return launch_warp_gather(a, d, L, ws, SA, ldsa, Sb, sbs, st);
 }
 
 }  // namespace sns

@@ -1,9 +1,8 @@
 // Gaussian sketch (Sec. 1.2.1: dense sketch with iid Gaussian entries):
 //   S [A | b] = (1/sqrt(d)) G [A | b],
-// G[k, i] = T[j], j = top 12 bits of 16-bit field q = (k div 8) mod 4 of
-// SplitMix64 output i * Gn + g of stream 3, g = 8 (k div 32) + (k mod 8),
-// Gn = 8 ceil(d / 32) (one output serves rows k, k + 8, k + 16, k + 24), and
-// T[j] = BF16(Phi^-1((j + 1/2)/4096)).
+// G[k, i] = T[j], j = byte (i mod 8) of SplitMix64 output (i div 8) * d + k of
+// stream 3 (one output serves the eight columns 8t .. 8t + 7 of row k), and
+// T[j] = BF16(Phi^-1((j + 1/2)/256)).
 // G is never stored: tiles are generated where they are consumed.  The operand
 // [A | b] is rounded to BF16 (round to nearest even) and products accumulate in
 // FP32, the precision of a BF16 tensor-core contraction.
@@ -47,10 +46,10 @@ static uint16_t bf16_bits_rne(double x) {
   return (uint16_t)(u >> 16);
 }
 void gauss_table_host(uint16_t* out) {
-  for (int j = 0; j < 4096; ++j) out[j] = bf16_bits_rne(norm_quantile((j + 0.5) / 4096.0));
+  for (int j = 0; j < kGaussLevels; ++j) out[j] = bf16_bits_rne(norm_quantile((j + 0.5) / kGaussLevels));
 }
 
-static uint16_t g_table[4096];
+static uint16_t g_table[kGaussLevels];
 static bool g_table_ready = false;
 static const uint16_t* table_host() {
   if (!g_table_ready) {
@@ -69,36 +68,30 @@ __global__ void __launch_bounds__(256)
 gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
            uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
            int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
-  __shared__ float T[4096];
+  __shared__ float T[kGaussLevels];
   __shared__ float Gs[kGKc][kGMt + 1];
   __shared__ float As[kGKc][kGNt + 1];
   const int tid = threadIdx.x;
-  for (int j = tid; j < 4096; j += blockDim.x) T[j] = __uint_as_float((uint32_t)table[j] << 16);
+  for (int j = tid; j < kGaussLevels; j += blockDim.x) T[j] = __uint_as_float((uint32_t)table[j] << 16);
   const int64_t q = n + 1;
   const int64_t ntn = (q + kGNt - 1) / kGNt;
   const int64_t tm = blockIdx.x / ntn, tn = blockIdx.x % ntn;
   const int64_t k0 = tm * kGMt, j0 = tn * kGNt;
   const int64_t i_begin = (int64_t)blockIdx.y * kchunk;
   const int64_t i_end = std::min<int64_t>(m, i_begin + kchunk);
-  const int64_t groups = 8 * ((d + 31) / 32);
   const int tx = tid % 16, ty = tid / 16;
   float acc[4][4] = {};
   __syncthreads();
   for (int64_t i0 = i_begin; i0 < i_end; i0 += kGKc) {
-    // G tile: kGKc rows of A (i) x kGMt rows of G (k); one hash per 4 rows
-    // (k, k + 8, k + 16, k + 24) of a 32-row block
-    for (int e = tid; e < kGKc * (kGMt / 4); e += blockDim.x) {
-      const int il = e / (kGMt / 4), gl = e % (kGMt / 4);
-      const int64_t i = i0 + il;
-      const int64_t g = (k0 / 32) * 8 + gl;
-      uint64_t key = 0;
-      if (i < i_end) key = splitmix_at(s0, (uint64_t)i * (uint64_t)groups + (uint64_t)g);
+    // G tile: kGKc rows of A (i) x kGMt rows of G (k); one hash per row k and
+    // 8 consecutive i (i0 is a multiple of 8)
+    for (int e = tid; e < (kGKc / 8) * kGMt; e += blockDim.x) {
+      const int g8 = e / kGMt, kl = e % kGMt;
+      const int64_t i = i0 + 8 * g8, k = k0 + kl;
+      const uint64_t key = (i < i_end && k < d) ? splitmix_at(s0, (uint64_t)(i >> 3) * (uint64_t)d + (uint64_t)k) : 0;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int kl = 32 * (gl / 8) + (gl % 8) + 8 * t;
-        const uint32_t idx = (uint32_t)((key >> (16 * t + 4)) & 0xFFFu);
-        Gs[il][kl] = (i < i_end && k0 + kl < d) ? T[idx] : 0.f;
-      }
+      for (int t = 0; t < 8; ++t)
+        Gs[8 * g8 + t][kl] = (i + t < i_end && k < d) ? T[(uint32_t)(key >> (8 * t)) & 0xFFu] : 0.f;
     }
     // operand tile: BF16-rounded [A | b]
     for (int e = tid; e < kGKc * kGNt; e += blockDim.x) {
@@ -145,8 +138,10 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // swizzle (8 x 16-byte core matrices: element (r, k) at
 // ((r/8)*8 + k/8)*128 + (r%8)*16 + (k%8)*2), then one thread issues 4 MMAs of
 // 128 x N x 16 (K = 16 steps) and commits them to the stage's mbarrier.  Two
-// stages alternate, so writing chunk c+1 overlaps the MMAs of chunk c.  The b
-// column is accumulated on the CUDA cores from the same BF16 G tile.
+// stages alternate, so writing chunk c+1 overlaps the MMAs of chunk c.  G is
+// generated one hash per (row, 8 consecutive k): 8 lookups in a per-bank copy
+// of the FP32 table, one 16-byte store; the b column is accumulated on the
+// CUDA cores from the same looked-up values.
 //
 // Accumulation.  The tensor cores add into the TMEM accumulator in FP32
 // without round-to-nearest (measured: relative error ~2^-24 per accumulated K
@@ -251,8 +246,10 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   uint8_t* stA[2] = {usm, usm + kUStageA + kUStageB};
   uint8_t* stB[2] = {usm + kUStageA, usm + 2 * kUStageA + kUStageB};
   float* staging = reinterpret_cast<float*>(usm + 2 * (kUStageA + kUStageB));
-  uint16_t* T = reinterpret_cast<uint16_t*>(usm + 2 * (kUStageA + kUStageB) + (BULK ? kUStaging : 0));
-  float* bst = reinterpret_cast<float*>(T + 4096);                                 // [2][kUKT]
+  // the table as FP32, replicated once per bank: entry j of lane l at sT[j * 32 + l],
+  // so a warp's 32 random lookups never conflict
+  float* sT = reinterpret_cast<float*>(usm + 2 * (kUStageA + kUStageB) + (BULK ? kUStaging : 0));
+  float* bst = sT + kGaussLevels * 32;                                             // [2][kUKT]
   __shared__ __align__(8) uint64_t mma_done[2];
   __shared__ __align__(8) uint64_t rows_ready;
   __shared__ uint32_t tmem_base;
@@ -265,8 +262,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   const bool with_b = (blockIdx.z == 0);
   const int64_t i_begin = (int64_t)blockIdx.y * kchunk;
   const int64_t i_end = min(m, i_begin + kchunk);
-  const int64_t groups = 8 * ((d + 31) / 32);
-  for (int j = tid; j < 4096; j += blockDim.x) T[j] = table[j];
+  for (int j = tid; j < kGaussLevels * 32; j += blockDim.x) sT[j] = __uint_as_float((uint32_t)table[j >> 5] << 16);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[1])) : "memory");
@@ -391,36 +387,52 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     __syncthreads();                                             // staging consumed
     if (BULK && c + 1 < nchunks && warp == 0)
       stage_rows(staging, A, lda, col0, ncols, i0 + kUKT, (int)min((int64_t)kUKT, i_end - i0 - kUKT), &rows_ready);
-    // G tile: task (hash group gl, 4 consecutive k), one per thread: 4 hashes
-    // give the 4 rows r = 32 (gl / 8) + gl % 8 + 8 q, q = 0..3 (field q) x 4
-    // values, stored as 8 bytes per row.
-    for (int t = tid; t < (kUG / 4) * (kUKT / 4); t += blockDim.x) {
-      const int gl = t % (kUG / 4), k4 = t / (kUG / 4);
-      const int64_t g = (r_base / 32) * 8 + gl;
-      // outputs ctr0, ctr0 + groups, ... of the stream: the generator state
-      // advances by groups * gamma between them (no multiply per output)
-      const uint64_t ctr0 = (uint64_t)(i0 + 4 * k4) * (uint64_t)groups + (uint64_t)g;
-      uint64_t stt = s0 + (ctr0 + 1) * kGamma;
-      const uint64_t step = (uint64_t)groups * kGamma;
-      uint64_t key[4];
+    // G tile and b column: task (row r, group q of 8 consecutive k), two per
+    // thread (q and q + 4): one hash gives the row's 8 entries (byte t of output
+    // (i div 8) d + k is entry i = 8 (i0 / 8 + q) + t), 8 conflict-free table
+    // lookups, one 16-byte store into the K-major tile, and 8 FMAs of the b
+    // column in the same registers.  Rows past d and columns past the chunk's
+    // rows of A need no masking: their products never reach SA (rows past d are
+    // not written out; A and b are zero there).
+    {
+      const int r = tid & (kUG - 1);
+      const uint64_t kg = (uint64_t)(r_base + r);
+      float part = 0.f;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        key[j] = mix64(stt);
-        stt += step;
-      }
-      const int kvalid = rows - 4 * k4;                      // entries j < kvalid are rows of A
+      for (int e = 0; e < (kUKT / 8) / (kUThreads / kUG); ++e) {
+        const int q = (tid >> 7) + e * (kUThreads / kUG);
+        const uint64_t key = splitmix_at(s0, ((uint64_t)(i0 >> 3) + (uint64_t)q) * (uint64_t)d + kg);
+        const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
+        float v[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = 32 * (gl >> 3) + (gl & 7) + 8 * q;
-        const bool rowok = r_base + r < d;
-        uint32_t h[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t word = (q < 2) ? (uint32_t)key[j] : (uint32_t)(key[j] >> 32);
-          const uint32_t idx = (word >> ((q & 1) * 16 + 4)) & 0xFFFu;
-          h[j] = (rowok && j < kvalid) ? (uint32_t)T[idx] : 0u;
+        for (int t = 0; t < 4; ++t) {
+          v[t] = sT[((lo >> (8 * t)) & 0xFFu) * 32 + lane];
+          v[4 + t] = sT[((hi >> (8 * t)) & 0xFFu) * 32 + lane];
         }
-        *reinterpret_cast<uint2*>(sA + kmaj_off(r, 4 * k4)) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        uint4 w;
+        w.x = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
+        w.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
+        w.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
+        w.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
+        *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * q)) = w;
+        if (with_b) {
+          const float4 b0 = *reinterpret_cast<const float4*>(bst + s * kUKT + 8 * q);
+          const float4 b1 = *reinterpret_cast<const float4*>(bst + s * kUKT + 8 * q + 4);
+          part = fmaf(v[0], b0.x, part);
+          part = fmaf(v[1], b0.y, part);
+          part = fmaf(v[2], b0.z, part);
+          part = fmaf(v[3], b0.w, part);
+          part = fmaf(v[4], b1.x, part);
+          part = fmaf(v[5], b1.y, part);
+          part = fmaf(v[6], b1.z, part);
+          part = fmaf(v[7], b1.w, part);
+        }
+      }
+      if (with_b) {
+        const float t = sb_hi + part;                              // TwoSum (Knuth)
+        const float bb = t - sb_hi;
+        sb_lo += (sb_hi - (t - bb)) + (part - bb);
+        sb_hi = t;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -454,31 +466,6 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
                    : "memory");
     }
     issued = c + 1;
-    // b column on the CUDA cores: row tid mod 128 of the G tile times a quarter
-    // of the BF16 b chunk (K quarter tid / 128)
-    if (with_b) {
-      const float* bc = bst + s * kUKT;
-      const int grow = tid & (kUG - 1), kq = tid / kUG;
-      constexpr int kPer = kUKC / (kUThreads / kUG);
-      float part = 0.f;
-#pragma unroll
-      for (int k8 = kq * kPer; k8 < (kq + 1) * kPer; ++k8) {
-        const uint4 w = *reinterpret_cast<const uint4*>(sA + kmaj_off(grow, 8 * k8));
-        const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * k8);
-        const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * k8 + 4);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          part = fmaf(__uint_as_float(ws[h] << 16), bv[2 * h], part);
-          part = fmaf(__uint_as_float(ws[h] & 0xFFFF0000u), bv[2 * h + 1], part);
-        }
-      }
-      const float t = sb_hi + part;                              // TwoSum (Knuth)
-      const float bb = t - sb_hi;
-      sb_lo += (sb_hi - (t - bb)) + (part - bb);
-      sb_hi = t;
-    }
   }
   // wait for the last issued chunk's MMAs (commits track all earlier MMAs)
   bool ok = true;
@@ -500,7 +487,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 }
 
 size_t gauss_umma_smem(bool bulk) {
-  return 2 * (size_t)(kUStageA + kUStageB) + (bulk ? kUStaging : 0) + 4096 * 2 + 2 * kUKT * 4;
+  return 2 * (size_t)(kUStageA + kUStageB) + (bulk ? kUStaging : 0) + (size_t)kGaussLevels * 32 * 4 + 2 * kUKT * 4;
 }
 
 // Launch shape of gauss_umma: row tiles of G x K splits x column tiles, one
@@ -527,7 +514,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
                              int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (!ws || ws_bytes < gauss_ws_bytes(a.m, a.n, d)) return SNS_ENOMEM;
   uint16_t* dtab = static_cast<uint16_t*>(ws);
-  SNS_CUDA_TRY(cudaMemcpyAsync(dtab, table_host(), 4096 * 2, cudaMemcpyHostToDevice, st));
+  SNS_CUDA_TRY(cudaMemcpyAsync(dtab, table_host(), kGaussLevels * 2, cudaMemcpyHostToDevice, st));
   if (ldsa == a.n) {
     SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
   } else {
@@ -556,7 +543,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
       SNS_PROF(K_GAUSS, st);
       kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
           static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab,
+          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d), dtab,
           kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs, err);
     }
     SNS_CUDA_TRY(cudaGetLastError());
@@ -572,7 +559,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   {
     SNS_PROF(K_GAUSS, st);
   gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)a.row0 * (uint64_t)(8 * ((d + 31) / 32))), dtab,
+                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d), dtab,
           kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }

@@ -82,7 +82,9 @@ size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d);
 size_t gauss_err_offset();
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
                              int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
-void gauss_table_host(uint16_t* out4096);
+// Levels of the BF16 normal-quantile table T of the Gaussian sketch.
+constexpr int kGaussLevels = 256;
+void gauss_table_host(uint16_t* out);
 
 // QR / triangular solves (FP64).  W is column-major d x q with leading dim d.
 struct QrOut {

@@ -56,34 +56,33 @@ def test_bf16_rounding_matches_torch():
 def test_gaussian_table_is_normal_quantiles():
     T = S.gaussian_table()
     n = T.size
-    assert n == 4096
+    assert n == 256
     assert np.array_equal(T, -T[::-1])                           # symmetric
-    assert np.all(np.diff(T) >= 0)                               # monotone
+    assert np.all(np.diff(T) > 0)                                # strictly monotone
     # each entry is a BF16 number within half a BF16 ulp of the exact quantile:
-    # Phi(T[j]) brackets (j + 1/2)/4096 between the neighbouring BF16 values
+    # Phi(T[j]) brackets (j + 1/2)/256 between the neighbouring BF16 values
     p = (np.arange(n) + 0.5) / n
     ulp = np.ldexp(1.0, np.frexp(T)[1] - 8)
     assert np.all(ndtr(T - ulp / 2) <= p + 1e-15)
     assert np.all(ndtr(T + ulp / 2) >= p - 1e-15)
-    assert abs(T.mean()) < 1e-12 and abs((T ** 2).mean() - 1) < 2e-3
+    # 256 quantile midpoints: mean 0, second moment 1 - O(log(n) / n)
+    assert abs(T.mean()) < 1e-12 and abs((T ** 2).mean() - 1) < 1e-2
 
 
-def test_gaussian_indices_uniform_and_field_layout():
-    d, m = 10, 2000
+def test_gaussian_indices_uniform_and_byte_layout():
+    d, m = 10, 2003
     j = S.gaussian_indices(m, d, seed=5)
-    assert j.shape == (d, m) and j.min() >= 0 and j.max() < 4096
-    counts = np.bincount(j.ravel() >> 6, minlength=64)          # 64 coarse bins
+    assert j.shape == (d, m) and j.min() >= 0 and j.max() < 256
+    counts = np.bincount(j.ravel() >> 2, minlength=64)           # 64 coarse bins
     e = j.size / 64
     assert ((counts - e) ** 2 / e).sum() < 64 + 6 * math.sqrt(128)
-    # row k = 32 b + l + 8 q uses the top 12 bits of 16-bit field q of output
-    # i * G + (8 b + l), G = 8 * ceil(d / 32); d = 10: G = 8, row 9 -> l = 1, q = 1
-    key = H.splitmix64_at(H.stream_state(5, 3), np.array([7 * 8 + 1], dtype=np.uint64))
-    assert j[9, 7] == (int(key[0]) >> (16 * 1 + 4)) & 0xFFF
-    # every output feeds four rows 8 apart: rows 1, 9 (and 17, 25 when present)
-    jj = S.gaussian_indices(40, 64, seed=5)
-    key = H.splitmix64_at(H.stream_state(5, 3), np.array([3 * 16 + 8 + 2], dtype=np.uint64))   # i=3, b=1, l=2
-    for q in range(4):
-        assert jj[32 + 2 + 8 * q, 3] == (int(key[0]) >> (16 * q + 4)) & 0xFFF
+    # entry (k, i) is byte i mod 8 of output (i div 8) * d + k of stream 3
+    for k, i in [(9, 7), (0, 0), (3, 2002), (5, 1608)]:
+        key = int(H.splitmix64_at(H.stream_state(5, 3), np.array([(i // 8) * d + k], dtype=np.uint64))[0])
+        assert j[k, i] == (key >> (8 * (i % 8))) & 0xFF
+    # one output feeds the eight columns 8t .. 8t+7 of one row
+    key = int(H.splitmix64_at(H.stream_state(5, 3), np.array([11 * d + 4], dtype=np.uint64))[0])
+    assert [j[4, 88 + b] for b in range(8)] == [(key >> (8 * b)) & 0xFF for b in range(8)]
 
 
 def test_gaussian_sketch_and_solve_expected_residual():
