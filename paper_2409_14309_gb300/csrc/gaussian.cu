@@ -131,17 +131,20 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // ---------------------------------------------------------------------------
 // Tensor-core path (tcgen05, BF16 operands, FP32 accumulation in TMEM).
 //
-// CTA tile: 128 rows of G (one M = 128 MMA tile) x up to 256 columns of A x a
-// range of K (rows of A).  Per 64-row chunk of A, the CTA's 512 threads write
-// the chunk's G tile (generated from the hash and the BF16 table) and the BF16
-// copy of A's chunk into shared memory in the canonical K-major layout without
-// swizzle (8 x 16-byte core matrices: element (r, k) at
-// ((r/8)*8 + k/8)*128 + (r%8)*16 + (k%8)*2), then one thread issues 4 MMAs of
-// 128 x N x 16 (K = 16 steps) and commits them to the stage's mbarrier.  Two
-// stages alternate, so writing chunk c+1 overlaps the MMAs of chunk c.  G is
-// generated one hash per (row, 8 consecutive k): 8 lookups in a per-bank copy
-// of the FP32 table, one 16-byte store; the b column is accumulated on the
-// CUDA cores from the same looked-up values.
+// Two kernels.  gauss_convert streams [A | b] once: it rounds A to BF16
+// (round to nearest even) and writes it as ready-made MMA operand tiles, one
+// per (64-row chunk, 256-column tile), in the canonical K-major layout without
+// swizzle (8 x 16-byte core matrices: element (column nn, row k) at
+// ((nn/8)*8 + k/8)*128 + (nn%8)*16 + (k%8)*2), beside each chunk's 64
+// BF16-rounded b values as FP32.  gauss_umma then never touches FP32 A: per
+// chunk it takes the tile with one bulk copy into a 3-stage shared-memory ring
+// (issued two chunks ahead), generates the chunk's 128 x 64 tile of G, and one
+// thread issues 4 MMAs of 128 x N x 16 (K = 16 steps).  Every A tile is read
+// by the d / 128 row-tile CTAs of its K range, mostly from L2.
+//
+// G: one hash per (row, 8 consecutive k) gives 8 lookups in a per-bank copy of
+// the FP32 table and one 16-byte store; the b column is accumulated on the CUDA
+// cores from the same looked-up values.
 //
 // Accumulation.  The tensor cores add into the TMEM accumulator in FP32
 // without round-to-nearest (measured: relative error ~2^-24 per accumulated K
@@ -152,18 +155,21 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // tcgen05.st of S) and the next chunk restarts D.  The epilogue adds D and S,
 // scales by 1/sqrt(d) and adds into SA / Sb with FP32 reductions (the K range
 // is split over CTAs).
-// Waits are bounded; on expiry the CTA records an error, lets its issued MMAs
-// drain (bounded), frees its TMEM and returns.
+// Waits are bounded; on expiry the CTA records an error, lets its issued
+// copies and MMAs land (bounded), frees its TMEM and returns.
 constexpr int kUG = 128;          // G rows per CTA (one M = 128 tile)
-constexpr int kUKT = 64;          // K rows per stage
+constexpr int kUKT = 64;          // K rows per chunk
 constexpr int kUN = 256;          // max columns per CTA
 constexpr int kUKC = kUKT / 8;    // core matrices along K
-constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 16 KB
-constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB
-constexpr uint32_t kUStaging = kUKT * kUN * 4;  // 64 KB of FP32 rows of A
+constexpr int kUStages = 3;       // chunk ring depth (tile copies run two chunks ahead)
+constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 16 KB: G tile
+constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB: A tile (BF16)
+constexpr uint32_t kUStageBb = kUKT * 4;        // 256 B: b values of the chunk
+constexpr uint32_t kUStage = (kUStageA + kUStageB + kUStageBb + 1023) / 1024 * 1024;   // 1 KB aligned stages
+constexpr size_t kUTileBytes = (size_t)kUStageB + kUStageBb;   // one converted (chunk, tile) in the workspace
 constexpr uint32_t kUSum = 256;                 // TMEM column of the running sum S
 constexpr long long kUWait = 1LL << 24;
-constexpr int64_t kUFlush = 4;                  // chunks per accumulation run (16 MMA steps)
+constexpr int kUFlush = 4;                      // chunks per accumulation run (16 MMA steps)
 
 SNS_D uint32_t u_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 SNS_D uint32_t kmaj_off(int r, int k) { return (uint32_t)(((r >> 3) * kUKC + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2); }
@@ -214,59 +220,91 @@ SNS_D void tmem_st16(uint32_t a, const float (&v)[16]) {
       : "memory");
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
-
-// Issues the bulk copies of rows [i0, i0 + rows) of A's column tile into the
-// staging buffer (row k at staging + k * ncols floats); warp 0 only.
-SNS_D void stage_rows(float* staging, const float* A, int64_t lda, int64_t col0, int ncols, int64_t i0, int rows,
-                      uint64_t* bar) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t rbytes = (uint32_t)ncols * 4u;
-  if (lane == 0)
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(u_smem(bar)),
-                 "r"(rbytes * (uint32_t)rows)
-                 : "memory");
-  __syncwarp();
-  for (int k = lane; k < rows; k += 32)
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            u_smem(staging + (size_t)k * ncols)),
-        "l"(A + (i0 + k) * lda + col0), "r"(rbytes), "r"(u_smem(bar))
-        : "memory");
+SNS_D void u_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(u_smem(bar)), "r"(bytes) : "memory");
+}
+SNS_D void u_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(u_smem(dst)),
+      "l"(src), "r"(bytes), "r"(u_smem(bar))
+      : "memory");
 }
 
-// BULK: rows of A arrive by cp.async.bulk one chunk ahead (needs 16-byte
-// aligned rows and ncols % 4 == 0); otherwise each thread loads its elements.
+// [A | b] -> BF16 operand tiles.  Tile (chunk c, column tile z) lives at
+// tiles + (c * ntiles + z) * kUTileBytes: the K-major BF16 block of rows
+// 64c .. 64c + 63 and columns 256z .. 256z + npad_z - 1 (zero past m and n),
+// then (z = 0 only meaningful) the chunk's 64 b values rounded to BF16, as FP32.
+// Task = (chunk, tile, column nn, 8 consecutive rows): 8 loads that consecutive
+// threads make for consecutive columns, one 16-byte store.
+__global__ void __launch_bounds__(256)
+gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
+              int64_t nchunks, int64_t ntiles, uint8_t* __restrict__ tiles) {
+  const int64_t per_tile = (int64_t)kUKC * kUN + kUKT;   // A tasks, then b entries
+  const int64_t total = nchunks * ntiles * per_tile;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ct = t / per_tile, e = t % per_tile;
+    const int64_t c = ct / ntiles, z = ct % ntiles;
+    uint8_t* tile = tiles + (size_t)ct * kUTileBytes;
+    const int64_t r0 = c * kUKT;
+    if (e < (int64_t)kUKC * kUN) {
+      const int nn = (int)(e % kUN), k8 = (int)(e / kUN);
+      const int64_t col = z * kUN + nn;
+      float f[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t row = r0 + 8 * k8 + j;
+        f[j] = (row < m && col < n) ? __ldg(A + row * lda + col) : 0.f;
+      }
+      uint4 w;
+      w.x = pack_bf16(f[0], f[1]);
+      w.y = pack_bf16(f[2], f[3]);
+      w.z = pack_bf16(f[4], f[5]);
+      w.w = pack_bf16(f[6], f[7]);
+      *reinterpret_cast<uint4*>(tile + kmaj_off(nn, 8 * k8)) = w;
+    } else {
+      const int kk = (int)(e - (int64_t)kUKC * kUN);
+      const int64_t row = r0 + kk;
+      reinterpret_cast<float*>(tile + kUStageB)[kk] =
+          (row < m && z == 0) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + row))) : 0.f;
+    }
+  }
+}
+
 constexpr int kUThreads = 512;    // 16 warps: G generation is the instruction-heavy part
-template <bool BULK>
 __global__ void __launch_bounds__(kUThreads, 1)
-gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n, int64_t d,
-           uint64_t s0, const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA,
-           int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int* __restrict__ err) {
+gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t n, int64_t d, uint64_t s0,
+           const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA, int64_t ldsa,
+           float* __restrict__ Sb, int64_t sbs, int* __restrict__ err, int flush_every) {
   extern __shared__ __align__(1024) uint8_t usm[];
-  uint8_t* stA[2] = {usm, usm + kUStageA + kUStageB};
-  uint8_t* stB[2] = {usm + kUStageA, usm + 2 * kUStageA + kUStageB};
-  float* staging = reinterpret_cast<float*>(usm + 2 * (kUStageA + kUStageB));
+  // stage s: G tile (kUStageA), A tile (kUStageB), b values (kUStageBb)
+  auto stA = [&](int s) { return usm + (size_t)s * kUStage; };
+  auto stB = [&](int s) { return usm + (size_t)s * kUStage + kUStageA; };
+  auto stb = [&](int s) { return reinterpret_cast<const float*>(usm + (size_t)s * kUStage + kUStageA + kUStageB); };
   // the table as FP32, replicated once per bank: entry j of lane l at sT[j * 32 + l],
   // so a warp's 32 random lookups never conflict
-  float* sT = reinterpret_cast<float*>(usm + 2 * (kUStageA + kUStageB) + (BULK ? kUStaging : 0));
-  float* bst = sT + kGaussLevels * 32;                                             // [2][kUKT]
-  __shared__ __align__(8) uint64_t mma_done[2];
-  __shared__ __align__(8) uint64_t rows_ready;
+  float* sT = reinterpret_cast<float*>(usm + (size_t)kUStages * kUStage);
+  __shared__ __align__(8) uint64_t mma_done[kUStages];
+  __shared__ __align__(8) uint64_t tile_ready[kUStages];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t r_base = (int64_t)blockIdx.x * kUG;            // first G row of this CTA
-  const int64_t col0 = (int64_t)blockIdx.z * kUN;              // first column of A
+  const int64_t z = blockIdx.z;                                // column tile
+  const int64_t col0 = z * kUN;                                // first column of A
   const int ncols = (int)min((int64_t)kUN, n - col0);
   const int npad = ((ncols + 15) / 16) * 16;                   // MMA N (multiple of 16)
-  const bool with_b = (blockIdx.z == 0);
-  const int64_t i_begin = (int64_t)blockIdx.y * kchunk;
+  const bool with_b = (z == 0);
+  const int64_t i_begin = (int64_t)blockIdx.y * kchunk;        // a multiple of kUKT
   const int64_t i_end = min(m, i_begin + kchunk);
+  const int64_t nchunks = (i_end - i_begin + kUKT - 1) / kUKT;
+  const int64_t c_base = i_begin / kUKT;                       // global chunk index of chunk 0
+  const uint32_t copy_bytes = (uint32_t)npad * 128u + (with_b ? kUStageBb : 0u);
   for (int j = tid; j < kGaussLevels * 32; j += blockDim.x) sT[j] = __uint_as_float((uint32_t)table[j >> 5] << 16);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[1])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&rows_ready)) : "memory");
+    for (int s = 0; s < kUStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&tile_ready[s])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -282,13 +320,21 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   const uint32_t taddr = tmem_base;
   const uint32_t idesc =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  // b column: row tid mod 128, K quarter tid / 128; each chunk's 16 products
-  // are summed in a partial, partials go into a compensated (TwoSum) running sum
+  // b column: row tid mod 128; each chunk's 16 products are summed in a
+  // partial, partials go into a compensated (TwoSum) running sum
   float sb_hi = 0.f, sb_lo = 0.f;
-  const int64_t nchunks = (i_end - i_begin + kUKT - 1) / kUKT;
-  int64_t issued = 0;                                            // chunks whose MMAs were issued
-  if (BULK && nchunks > 0 && warp == 0)
-    stage_rows(staging, A, lda, col0, ncols, i_begin, (int)min((int64_t)kUKT, i_end - i_begin), &rows_ready);
+  // chunk c's tile (and b values) into stage c mod kUStages; thread 0 only
+  int64_t copied = 0;                                          // chunks whose copies were issued
+  auto issue_copy = [&](int64_t c) {
+    const int s = (int)(c % kUStages);
+    const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * kUTileBytes;
+    u_expect(&tile_ready[s], copy_bytes);
+    u_copy(stB(s), src, (uint32_t)npad * 128u, &tile_ready[s]);
+    if (with_b) u_copy(stB(s) + kUStageB, src + kUStageB, kUStageBb, &tile_ready[s]);
+    copied = c + 1;
+  };
+  if (tid == 0)
+    for (int64_t c = 0; c < kUStages - 1 && c < nchunks; ++c) issue_copy(c);
   // D (columns 0..255) -> S (columns kUSum..): warp w reads TMEM lanes of
   // quadrant w mod 4 (the hardware rule) and the 16-column blocks w / 4,
   // w / 4 + 4, ...; the final pass adds D and S, scales and reduces into SA.
@@ -335,68 +381,26 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     }
   };
   int64_t c_acc0 = 0;                                            // first chunk since the last flush
+  int64_t issued = 0;                                            // chunks whose MMAs were issued
   for (int64_t c = 0; c < nchunks; ++c) {
-    const int s = (int)(c & 1);
-    const int64_t u = c >> 1;                                    // use index of stage s
+    const int s = (int)(c % kUStages);
+    const int64_t u = c / kUStages;                              // use index of stage s
     const int64_t i0 = i_begin + c * kUKT;
-    const int rows = (int)min((int64_t)kUKT, i_end - i0);
-    if (u >= 1 && !u_wait(&mma_done[s], (uint32_t)((u - 1) & 1))) {
-      if (lane == 0) atomicExch(&s_fail, 1);
-    }
-    if (BULK && !u_wait(&rows_ready, (uint32_t)(c & 1))) {
-      if (lane == 0) atomicExch(&s_fail, 1);
-    }
+    if (!u_wait(&tile_ready[s], (uint32_t)(u & 1)) && lane == 0) atomicExch(&s_fail, 1);
     __syncthreads();
     if (s_fail) break;
-    uint8_t* sA = stA[s];
-    uint8_t* sB = stB[s];
-    // A chunk -> BF16, K-major: task (column nn, 8 consecutive k): one 16-byte
-    // store per task; consecutive threads take consecutive columns (distinct
-    // 16-byte bank groups)
-    const bool full = BULK && rows == kUKT && ncols == npad;     // no padding in this chunk
-    for (int t = tid; t < kUKC * npad; t += blockDim.x) {
-      const int nn = t % npad, k8 = t / npad;
-      float f[8];
-      if (full) {
-        const float* src = staging + (size_t)(8 * k8) * ncols + nn;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) f[j] = src[(size_t)j * ncols];
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int k = 8 * k8 + j;
-          float v = 0.f;
-          if (nn < ncols && k < rows) {
-            if (BULK) v = staging[(size_t)k * ncols + nn];
-            else v = __ldg(A + (i0 + k) * lda + col0 + nn);
-          }
-          f[j] = v;
-        }
-      }
-      uint4 w;
-      w.x = pack_bf16(f[0], f[1]);
-      w.y = pack_bf16(f[2], f[3]);
-      w.z = pack_bf16(f[4], f[5]);
-      w.w = pack_bf16(f[6], f[7]);
-      *reinterpret_cast<uint4*>(sB + kmaj_off(nn, 8 * k8)) = w;
-    }
-    if (with_b && tid < kUKT) {
-      const int64_t i = i0 + tid;
-      bst[s * kUKT + tid] = (tid < rows) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + i))) : 0.f;
-    }
-    __syncthreads();                                             // staging consumed
-    if (BULK && c + 1 < nchunks && warp == 0)
-      stage_rows(staging, A, lda, col0, ncols, i0 + kUKT, (int)min((int64_t)kUKT, i_end - i0 - kUKT), &rows_ready);
+    uint8_t* sA = stA(s);
     // G tile and b column: task (row r, group q of 8 consecutive k), two per
     // thread (q and q + 4): one hash gives the row's 8 entries (byte t of output
     // (i div 8) d + k is entry i = 8 (i0 / 8 + q) + t), 8 conflict-free table
     // lookups, one 16-byte store into the K-major tile, and 8 FMAs of the b
-    // column in the same registers.  Rows past d and columns past the chunk's
-    // rows of A need no masking: their products never reach SA (rows past d are
-    // not written out; A and b are zero there).
+    // column in the same registers.  Rows past d and columns past m need no
+    // masking: their products never reach SA (rows past d are not written out;
+    // the converted A and b are zero there).
     {
       const int r = tid & (kUG - 1);
       const uint64_t kg = (uint64_t)(r_base + r);
+      const float* bc = stb(s);
       float part = 0.f;
 #pragma unroll
       for (int e = 0; e < (kUKT / 8) / (kUThreads / kUG); ++e) {
@@ -416,8 +420,8 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
         w.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
         *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * q)) = w;
         if (with_b) {
-          const float4 b0 = *reinterpret_cast<const float4*>(bst + s * kUKT + 8 * q);
-          const float4 b1 = *reinterpret_cast<const float4*>(bst + s * kUKT + 8 * q + 4);
+          const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * q);
+          const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * q + 4);
           part = fmaf(v[0], b0.x, part);
           part = fmaf(v[1], b0.y, part);
           part = fmaf(v[2], b0.z, part);
@@ -437,10 +441,10 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (c > c_acc0 && (c - c_acc0) % kUFlush == 0) {
+    if (c > c_acc0 && (c - c_acc0) % flush_every == 0) {
       // chunks c_acc0 .. c - 1 are in D: wait for their MMAs, add D into S, restart D
       const int64_t cl = c - 1;
-      if (!u_wait(&mma_done[cl & 1], (uint32_t)((cl >> 1) & 1)) && lane == 0) atomicExch(&s_fail, 1);
+      if (!u_wait(&mma_done[cl % kUStages], (uint32_t)((cl / kUStages) & 1)) && lane == 0) atomicExch(&s_fail, 1);
       __syncthreads();
       if (s_fail) break;
       tmem_flush(false);
@@ -453,7 +457,7 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 #pragma unroll
       for (int ks = 0; ks < kUKT / 16; ++ks) {
         const uint64_t ad = u_desc(u_smem(sA) + (uint32_t)ks * 256u);
-        const uint64_t bd = u_desc(u_smem(sB) + (uint32_t)ks * 256u);
+        const uint64_t bd = u_desc(u_smem(stB(s)) + (uint32_t)ks * 256u);
         const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -464,6 +468,14 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        u_smem(&mma_done[s]))
                    : "memory");
+      // the copy two chunks ahead goes into the stage chunk c - 1 used: its MMAs must be done
+      const int64_t cn = c + kUStages - 1;
+      if (cn < nchunks) {
+        bool free_ok = true;
+        if (c >= 1) free_ok = u_wait(&mma_done[(c - 1) % kUStages], (uint32_t)(((c - 1) / kUStages) & 1));
+        if (free_ok) issue_copy(cn);
+        else atomicExch(&s_fail, 1);
+      }
     }
     issued = c + 1;
   }
@@ -471,10 +483,11 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   bool ok = true;
   if (issued > 0) {
     const int64_t cl = issued - 1;
-    ok = u_wait(&mma_done[cl & 1], (uint32_t)((cl >> 1) & 1));
+    ok = u_wait(&mma_done[cl % kUStages], (uint32_t)((cl / kUStages) & 1));
   }
-  // a staged chunk that was never consumed (failure path) must land before exit
-  if (BULK && s_fail && issued < nchunks) u_wait(&rows_ready, (uint32_t)(issued & 1));
+  // copies that were issued but never consumed (failure path) must land before exit
+  if (tid == 0)
+    for (int64_t c = issued; c < copied; ++c) u_wait(&tile_ready[c % kUStages], (uint32_t)((c / kUStages) & 1));
   __syncthreads();
   if (!ok || s_fail) {
     if (tid == 0) atomicExch(err, 1);
@@ -486,14 +499,12 @@ gauss_umma(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
 }
 
-size_t gauss_umma_smem(bool bulk) {
-  return 2 * (size_t)(kUStageA + kUStageB) + (bulk ? kUStaging : 0) + (size_t)kGaussLevels * 32 * 4 + 2 * kUKT * 4;
-}
+size_t gauss_umma_smem() { return (size_t)kUStages * kUStage + (size_t)kGaussLevels * 32 * 4; }
 
 // Launch shape of gauss_umma: row tiles of G x K splits x column tiles, one
 // CTA per SM; K ranges in whole chunks.
 struct GaussGrid {
-  int64_t mtiles, ntiles, ksplit, kchunk;
+  int64_t mtiles, ntiles, ksplit, kchunk, nchunks;
 };
 static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
   GaussGrid g;
@@ -503,11 +514,14 @@ static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
   g.kchunk = (m + g.ksplit - 1) / g.ksplit;
   g.kchunk = ((g.kchunk + kUKT - 1) / kUKT) * kUKT;
   g.ksplit = (m + g.kchunk - 1) / g.kchunk;
+  g.nchunks = (m + kUKT - 1) / kUKT;
   return g;
 }
-size_t gauss_ws_bytes(int64_t, int64_t, int64_t) {
-  // the BF16 table (uploaded per call) and the error word
-  return 8192 + 256;
+constexpr size_t kGaussTilesOffset = 8192 + 256;
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t) {
+  // the BF16 table (uploaded per call), the error word, the converted [A | b] tiles
+  const int64_t nchunks = (m + kUKT - 1) / kUKT, ntiles = (n + kUN - 1) / kUN;
+  return kGaussTilesOffset + (size_t)nchunks * ntiles * kUTileBytes;
 }
 
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
@@ -525,6 +539,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   } else {
     SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
   }
+  // SNSOLVE_GAUSS=simt selects the CUDA-core kernel
   static int use_simt = -1;
   if (use_simt < 0) {
     const char* e = getenv("SNSOLVE_GAUSS");
@@ -532,19 +547,24 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   }
   int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + gauss_err_offset());
   SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
+  const uint64_t s0 = shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d);
   if (!use_simt) {
     const GaussGrid gg = gauss_grid(a.m, a.n, d);
-    const int64_t mtiles = gg.mtiles, ntiles = gg.ntiles, ksplit = gg.ksplit, kchunk = gg.kchunk;
-    const bool bulk = (a.n % 4 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.A % 16 == 0);
-    auto kern = bulk ? gauss_umma<true> : gauss_umma<false>;
-    SNS_CUDA_TRY(raise_smem_limit((const void*)kern));
-    dim3 grid((unsigned)mtiles, (unsigned)ksplit, (unsigned)ntiles);
+    uint8_t* tiles = static_cast<uint8_t*>(ws) + kGaussTilesOffset;
     {
       SNS_PROF(K_GAUSS, st);
-      kern<<<grid, kUThreads, gauss_umma_smem(bulk), st>>>(
-          static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-          shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d), dtab,
-          kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs, err);
+      gauss_convert<<<num_sms() * 8, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda,
+                                                   static_cast<const float*>(a.b), a.m, a.n, gg.nchunks, gg.ntiles,
+                                                   tiles);
+    }
+    SNS_CUDA_TRY(cudaGetLastError());
+    SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
+    dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
+    {
+      SNS_PROF(K_GAUSS, st);
+      gauss_umma<<<grid, kUThreads, gauss_umma_smem(), st>>>(tiles, gg.ntiles, a.m, a.n, d, s0, dtab, gg.kchunk,
+                                                             (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
+                                                             err, kUFlush);
     }
     SNS_CUDA_TRY(cudaGetLastError());
     return SNS_OK;
@@ -559,8 +579,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   {
     SNS_PROF(K_GAUSS, st);
   gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-                                   shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d), dtab,
-          kchunk,
+                                   s0, dtab, kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
   SNS_CUDA_TRY(cudaGetLastError());
