@@ -161,11 +161,12 @@ constexpr int kUG = 128;          // G rows per CTA (one M = 128 tile)
 constexpr int kUKT = 64;          // K rows per chunk
 constexpr int kUN = 256;          // max columns per CTA
 constexpr int kUKC = kUKT / 8;    // core matrices along K
-constexpr int kUStages = 3;       // chunk ring depth (tile copies run two chunks ahead)
+constexpr int kUGStages = 2;      // G tile ring: chunk c + 1 is generated while chunk c's MMAs run
+constexpr int kUBStages = 5;      // A tile ring: copies run four chunks ahead
 constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 16 KB: G tile
 constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB: A tile (BF16)
 constexpr uint32_t kUStageBb = kUKT * 4;        // 256 B: b values of the chunk
-constexpr uint32_t kUStage = (kUStageA + kUStageB + kUStageBb + 1023) / 1024 * 1024;   // 1 KB aligned stages
+constexpr uint32_t kUBStage = kUStageB + kUStageBb;             // one A tile stage (16-byte multiple)
 constexpr size_t kUTileBytes = (size_t)kUStageB + kUStageBb;   // one converted (chunk, tile) in the workspace
 constexpr uint32_t kUSum = 256;                 // TMEM column of the running sum S
 constexpr long long kUWait = 1LL << 24;
@@ -270,24 +271,35 @@ gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict_
   }
 }
 
-constexpr int kUThreads = 512;    // 16 warps: G generation is the instruction-heavy part
+// Warp roles: warps 0..15 generate G (and the b column) and move D into S at
+// the flush points; warp 16 issues the MMAs and the tile copies.  They meet
+// only at mbarriers: tile_ready (copy landed), g_ready (16 generator warps
+// arrived: the chunk's G tile is written and, at a flush point, D has been
+// added into S), gfree / bfree (the chunk's MMAs completed: its G stage / A
+// stage may be refilled; two commits after each chunk).  Phases never alias:
+// a barrier's next phase cannot complete before its current one was waited for.
+constexpr int kUGenWarps = 16;
+constexpr int kUThreads = 32 * (kUGenWarps + 1);
 __global__ void __launch_bounds__(kUThreads, 1)
 gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t n, int64_t d, uint64_t s0,
            const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA, int64_t ldsa,
            float* __restrict__ Sb, int64_t sbs, int* __restrict__ err, int flush_every) {
   extern __shared__ __align__(1024) uint8_t usm[];
-  // stage s: G tile (kUStageA), A tile (kUStageB), b values (kUStageBb)
-  auto stA = [&](int s) { return usm + (size_t)s * kUStage; };
-  auto stB = [&](int s) { return usm + (size_t)s * kUStage + kUStageA; };
-  auto stb = [&](int s) { return reinterpret_cast<const float*>(usm + (size_t)s * kUStage + kUStageA + kUStageB); };
+  // G stages (kUStageA each), then A stages (A tile kUStageB, b values kUStageBb)
+  auto stA = [&](int s) { return usm + (size_t)s * kUStageA; };
+  auto stB = [&](int s) { return usm + (size_t)kUGStages * kUStageA + (size_t)s * kUBStage; };
+  auto stb = [&](int s) { return reinterpret_cast<const float*>(stB(s) + kUStageB); };
   // the table as FP32, replicated once per bank: entry j of lane l at sT[j * 32 + l],
   // so a warp's 32 random lookups never conflict
-  float* sT = reinterpret_cast<float*>(usm + (size_t)kUStages * kUStage);
-  __shared__ __align__(8) uint64_t mma_done[kUStages];
-  __shared__ __align__(8) uint64_t tile_ready[kUStages];
+  float* sT = reinterpret_cast<float*>(usm + (size_t)kUGStages * kUStageA + (size_t)kUBStages * kUBStage);
+  __shared__ __align__(8) uint64_t tile_ready[kUBStages];     // copy of chunk c landed (stage c mod kUBStages)
+  __shared__ __align__(8) uint64_t bfree[kUBStages];          // MMAs of chunk c done (A stage reusable)
+  __shared__ __align__(8) uint64_t g_ready[kUGStages];        // G tile of chunk c written (stage c mod kUGStages)
+  __shared__ __align__(8) uint64_t gfree[kUGStages];          // MMAs of chunk c done (G stage reusable)
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = (warp == kUGenWarps);
   const int64_t r_base = (int64_t)blockIdx.x * kUG;            // first G row of this CTA
   const int64_t z = blockIdx.z;                                // column tile
   const int64_t col0 = z * kUN;                                // first column of A
@@ -301,9 +313,13 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   const uint32_t copy_bytes = (uint32_t)npad * 128u + (with_b ? kUStageBb : 0u);
   for (int j = tid; j < kGaussLevels * 32; j += blockDim.x) sT[j] = __uint_as_float((uint32_t)table[j >> 5] << 16);
   if (tid == 0) {
-    for (int s = 0; s < kUStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&mma_done[s])) : "memory");
+    for (int s = 0; s < kUBStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&tile_ready[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&bfree[s])) : "memory");
+    }
+    for (int s = 0; s < kUGStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(u_smem(&g_ready[s])), "r"(kUGenWarps) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&gfree[s])) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
@@ -320,32 +336,21 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   const uint32_t taddr = tmem_base;
   const uint32_t idesc =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  // b column: row tid mod 128; each chunk's 16 products are summed in a
-  // partial, partials go into a compensated (TwoSum) running sum
-  float sb_hi = 0.f, sb_lo = 0.f;
-  // chunk c's tile (and b values) into stage c mod kUStages; thread 0 only
-  int64_t copied = 0;                                          // chunks whose copies were issued
-  auto issue_copy = [&](int64_t c) {
-    const int s = (int)(c % kUStages);
-    const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * kUTileBytes;
-    u_expect(&tile_ready[s], copy_bytes);
-    u_copy(stB(s), src, (uint32_t)npad * 128u, &tile_ready[s]);
-    if (with_b) u_copy(stB(s) + kUStageB, src + kUStageB, kUStageBb, &tile_ready[s]);
-    copied = c + 1;
-  };
-  if (tid == 0)
-    for (int64_t c = 0; c < kUStages - 1 && c < nchunks; ++c) issue_copy(c);
-  // D (columns 0..255) -> S (columns kUSum..): warp w reads TMEM lanes of
-  // quadrant w mod 4 (the hardware rule) and the 16-column blocks w / 4,
-  // w / 4 + 4, ...; the final pass adds D and S, scales and reduces into SA.
+  auto fail = [&]() { s_fail = 1; };
+
+  // D (columns 0..255) -> S (columns kUSum..), by the generator warps: warp w
+  // reads TMEM lanes of quadrant w mod 4 (the hardware rule) and the 16-column
+  // blocks w / 4, w / 4 + 4, ...; the final pass adds D and S, scales and
+  // reduces into SA.  nflush counts the flushes done (uniform over the warps).
   int nflush = 0;
+  float sb_hi = 0.f, sb_lo = 0.f;                              // b column (generator threads)
   auto tmem_flush = [&](bool final_pass) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int quarter = warp & 3, part = warp >> 2;
     const int rloc = quarter * 32 + lane;
     const int64_t row = r_base + rloc;
     const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
-    for (int c0 = part * 16; c0 < npad; c0 += 64) {
+    for (int c0 = part * 16; c0 < npad; c0 += 16 * (kUGenWarps / 4)) {
       float v[16];
       tmem_ld16(taddr + lanes + (uint32_t)c0, v);
       if (nflush > 0) {
@@ -380,126 +385,167 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
       ++nflush;
     }
   };
-  int64_t c_acc0 = 0;                                            // first chunk since the last flush
-  int64_t issued = 0;                                            // chunks whose MMAs were issued
-  for (int64_t c = 0; c < nchunks; ++c) {
-    const int s = (int)(c % kUStages);
-    const int64_t u = c / kUStages;                              // use index of stage s
-    const int64_t i0 = i_begin + c * kUKT;
-    if (!u_wait(&tile_ready[s], (uint32_t)(u & 1)) && lane == 0) atomicExch(&s_fail, 1);
-    __syncthreads();
-    if (s_fail) break;
-    uint8_t* sA = stA(s);
-    // G tile and b column: task (row r, group q of 8 consecutive k), two per
-    // thread (q and q + 4): one hash gives the row's 8 entries (byte t of output
-    // (i div 8) d + k is entry i = 8 (i0 / 8 + q) + t), 8 conflict-free table
-    // lookups, one 16-byte store into the K-major tile, and 8 FMAs of the b
-    // column in the same registers.  Rows past d and columns past m need no
-    // masking: their products never reach SA (rows past d are not written out;
-    // the converted A and b are zero there).
-    {
-      const int r = tid & (kUG - 1);
-      const uint64_t kg = (uint64_t)(r_base + r);
-      const float* bc = stb(s);
-      float part = 0.f;
+
+  __shared__ long long s_issued;                               // chunks whose MMAs the MMA warp issued
+  if (mma_warp) {
+    if (lane == 0) {
+      // chunk c's tile (and b values) into A stage c mod kUBStages
+      int64_t copied = 0;
+      auto issue_copy = [&](int64_t c) {
+        const int s = (int)(c % kUBStages);
+        const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * kUTileBytes;
+        u_expect(&tile_ready[s], copy_bytes);
+        u_copy(stB(s), src, (uint32_t)npad * 128u, &tile_ready[s]);
+        if (with_b) u_copy(stB(s) + kUStageB, src + kUStageB, kUStageBb, &tile_ready[s]);
+        copied = c + 1;
+      };
+      for (int64_t c = 0; c < kUBStages - 1 && c < nchunks; ++c) issue_copy(c);
+      int64_t c_acc0 = 0, issued = 0;
+      for (int64_t c = 0; c < nchunks; ++c) {
+        const int sg = (int)(c % kUGStages), s = (int)(c % kUBStages);
+        if (!u_wait(&g_ready[sg], (uint32_t)((c / kUGStages) & 1))) { fail(); break; }
+        if (s_fail) break;
+        if (c > c_acc0 && (c - c_acc0) % flush_every == 0) c_acc0 = c;   // D was moved into S
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int e = 0; e < (kUKT / 8) / (kUThreads / kUG); ++e) {
-        const int q = (tid >> 7) + e * (kUThreads / kUG);
-        const uint64_t key = splitmix_at(s0, ((uint64_t)(i0 >> 3) + (uint64_t)q) * (uint64_t)d + kg);
-        const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
-        float v[8];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          v[t] = sT[((lo >> (8 * t)) & 0xFFu) * 32 + lane];
-          v[4 + t] = sT[((hi >> (8 * t)) & 0xFFu) * 32 + lane];
+        for (int ks = 0; ks < kUKT / 16; ++ks) {
+          const uint64_t ad = u_desc(u_smem(stA(sg)) + (uint32_t)ks * 256u);
+          const uint64_t bd = u_desc(u_smem(stB(s)) + (uint32_t)ks * 256u);
+          const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
         }
-        uint4 w;
-        w.x = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
-        w.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
-        w.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
-        w.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
-        *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * q)) = w;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         u_smem(&gfree[sg]))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         u_smem(&bfree[s]))
+                     : "memory");
+        issued = c + 1;
+        // the copy kUBStages - 1 chunks ahead goes into the A stage chunk c - 1 used
+        const int64_t cn = c + kUBStages - 1;
+        if (cn < nchunks) {
+          if (c >= 1 && !u_wait(&bfree[(c - 1) % kUBStages], (uint32_t)(((c - 1) / kUBStages) & 1))) {
+            fail();
+            break;
+          }
+          issue_copy(cn);
+        }
+      }
+      s_issued = issued;
+      // the last issued chunk's commit tracks all earlier MMAs; TMEM stays allocated until then
+      if (issued > 0 && !u_wait(&bfree[(issued - 1) % kUBStages], (uint32_t)(((issued - 1) / kUBStages) & 1)))
+        fail();
+      // copies issued but never consumed (failure path) land before the CTA exits: a
+      // stage's copies complete in order, so its last one covers the earlier ones
+      for (int64_t c = max((int64_t)0, copied - kUBStages); c < copied; ++c)
+        if (!u_wait(&tile_ready[c % kUBStages], (uint32_t)((c / kUBStages) & 1))) fail();
+    }
+    __syncwarp();
+  } else {
+    // generator warps
+    int64_t c_acc0 = 0;                                          // first chunk since the last flush
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int sg = (int)(c % kUGStages), s = (int)(c % kUBStages);
+      const int64_t i0 = i_begin + c * kUKT;
+      // G stage sg is free once chunk c - kUGStages's MMAs are done; the b values come with the tile
+      const bool ok = (c < kUGStages || u_wait(&gfree[sg], (uint32_t)(((c - kUGStages) / kUGStages) & 1))) &&
+                      u_wait(&tile_ready[s], (uint32_t)((c / kUBStages) & 1));
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        break;
+      }
+      uint8_t* sA = stA(sg);
+      // G tile and b column: task (row r, group q of 8 consecutive k), two per
+      // thread (q and q + 4): one hash gives the row's 8 entries (byte t of output
+      // (i div 8) d + k is entry i = 8 (i0 / 8 + q) + t), 8 conflict-free table
+      // lookups, one 16-byte store into the K-major tile, and 8 FMAs of the b
+      // column in the same registers.  Rows past d and columns past m need no
+      // masking: their products never reach SA (rows past d are not written out;
+      // the converted A and b are zero there).
+      {
+        const int r = tid & (kUG - 1);
+        const uint64_t kg = (uint64_t)(r_base + r);
+        const float* bc = stb(s);
+        float part = 0.f;
+        constexpr int kGenThreads = 32 * kUGenWarps;
+#pragma unroll
+        for (int e = 0; e < (kUKT / 8) / (kGenThreads / kUG); ++e) {
+          const int q = (tid >> 7) + e * (kGenThreads / kUG);
+          const uint64_t key = splitmix_at(s0, ((uint64_t)(i0 >> 3) + (uint64_t)q) * (uint64_t)d + kg);
+          const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
+          float v[8];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            v[t] = sT[((lo >> (8 * t)) & 0xFFu) * 32 + lane];
+            v[4 + t] = sT[((hi >> (8 * t)) & 0xFFu) * 32 + lane];
+          }
+          uint4 w;
+          w.x = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
+          w.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
+          w.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
+          w.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
+          *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * q)) = w;
+          if (with_b) {
+            const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * q);
+            const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * q + 4);
+            part = fmaf(v[0], b0.x, part);
+            part = fmaf(v[1], b0.y, part);
+            part = fmaf(v[2], b0.z, part);
+            part = fmaf(v[3], b0.w, part);
+            part = fmaf(v[4], b1.x, part);
+            part = fmaf(v[5], b1.y, part);
+            part = fmaf(v[6], b1.z, part);
+            part = fmaf(v[7], b1.w, part);
+          }
+        }
         if (with_b) {
-          const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * q);
-          const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * q + 4);
-          part = fmaf(v[0], b0.x, part);
-          part = fmaf(v[1], b0.y, part);
-          part = fmaf(v[2], b0.z, part);
-          part = fmaf(v[3], b0.w, part);
-          part = fmaf(v[4], b1.x, part);
-          part = fmaf(v[5], b1.y, part);
-          part = fmaf(v[6], b1.z, part);
-          part = fmaf(v[7], b1.w, part);
+          const float t = sb_hi + part;                            // TwoSum (Knuth)
+          const float bb = t - sb_hi;
+          sb_lo += (sb_hi - (t - bb)) + (part - bb);
+          sb_hi = t;
         }
       }
-      if (with_b) {
-        const float t = sb_hi + part;                              // TwoSum (Knuth)
-        const float bb = t - sb_hi;
-        sb_lo += (sb_hi - (t - bb)) + (part - bb);
-        sb_hi = t;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (c > c_acc0 && (c - c_acc0) % flush_every == 0) {
+        // chunks c_acc0 .. c - 1 are in D: wait for their MMAs, add D into S; the
+        // MMA warp restarts D with chunk c only after every warp has arrived
+        const int64_t cl = c - 1;
+        if (!__all_sync(0xffffffffu, u_wait(&gfree[cl % kUGStages], (uint32_t)((cl / kUGStages) & 1)))) {
+          if (lane == 0) fail();
+          break;
+        }
+        tmem_flush(false);
+        c_acc0 = c;
       }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (c > c_acc0 && (c - c_acc0) % flush_every == 0) {
-      // chunks c_acc0 .. c - 1 are in D: wait for their MMAs, add D into S, restart D
-      const int64_t cl = c - 1;
-      if (!u_wait(&mma_done[cl % kUStages], (uint32_t)((cl / kUStages) & 1)) && lane == 0) atomicExch(&s_fail, 1);
-      __syncthreads();
-      if (s_fail) break;
-      tmem_flush(false);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      c_acc0 = c;
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(u_smem(&g_ready[sg])) : "memory");
     }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int ks = 0; ks < kUKT / 16; ++ks) {
-        const uint64_t ad = u_desc(u_smem(sA) + (uint32_t)ks * 256u);
-        const uint64_t bd = u_desc(u_smem(stB(s)) + (uint32_t)ks * 256u);
-        const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       u_smem(&mma_done[s]))
-                   : "memory");
-      // the copy two chunks ahead goes into the stage chunk c - 1 used: its MMAs must be done
-      const int64_t cn = c + kUStages - 1;
-      if (cn < nchunks) {
-        bool free_ok = true;
-        if (c >= 1) free_ok = u_wait(&mma_done[(c - 1) % kUStages], (uint32_t)(((c - 1) / kUStages) & 1));
-        if (free_ok) issue_copy(cn);
-        else atomicExch(&s_fail, 1);
-      }
-    }
-    issued = c + 1;
   }
-  // wait for the last issued chunk's MMAs (commits track all earlier MMAs)
-  bool ok = true;
-  if (issued > 0) {
-    const int64_t cl = issued - 1;
-    ok = u_wait(&mma_done[cl % kUStages], (uint32_t)((cl / kUStages) & 1));
-  }
-  // copies that were issued but never consumed (failure path) must land before exit
-  if (tid == 0)
-    for (int64_t c = issued; c < copied; ++c) u_wait(&tile_ready[c % kUStages], (uint32_t)((c / kUStages) & 1));
   __syncthreads();
-  if (!ok || s_fail) {
-    if (tid == 0) atomicExch(err, 1);
-  } else if (issued > 0) {
-    tmem_flush(true);
+  const int64_t issued = s_issued;
+  if (!mma_warp && issued > 0 && !s_fail) {
+    // the last issued chunk's commit tracks all earlier MMAs
+    const int64_t cl = issued - 1;
+    if (__all_sync(0xffffffffu, u_wait(&gfree[cl % kUGStages], (uint32_t)((cl / kUGStages) & 1)))) {
+      if (issued == nchunks) tmem_flush(true);
+    } else if (lane == 0) {
+      fail();
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (tid == 0 && (s_fail || issued != nchunks)) atomicExch(err, 1);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
 }
 
-size_t gauss_umma_smem() { return (size_t)kUStages * kUStage + (size_t)kGaussLevels * 32 * 4; }
+size_t gauss_umma_smem() {
+  return (size_t)kUGStages * kUStageA + (size_t)kUBStages * kUBStage + (size_t)kGaussLevels * 32 * 4;
+}
 
 // Launch shape of gauss_umma: row tiles of G x K splits x column tiles, one
 // CTA per SM; K ranges in whole chunks.
