@@ -231,56 +231,81 @@ SNS_D void u_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
       : "memory");
 }
 
+// Stage and phase parity of a ring position, advanced one chunk at a time (no
+// divisions in the chunk loops).
+template <int N>
+struct RingPos {
+  int s = 0;
+  uint32_t ph = 0;
+  SNS_D void next() {
+    if (++s == N) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
 // [A | b] -> BF16 operand tiles.  Tile (chunk c, column tile z) lives at
 // tiles + (c * ntiles + z) * kUTileBytes: the K-major BF16 block of rows
 // 64c .. 64c + 63 and columns 256z .. 256z + npad_z - 1 (zero past m and n),
 // then (z = 0 only meaningful) the chunk's 64 b values rounded to BF16, as FP32.
-// Task = (chunk, tile, column nn, 8 consecutive rows): 8 loads that consecutive
-// threads make for consecutive columns, one 16-byte store.
+// A block converts whole tiles; a thread takes 8 rows x 4 columns (16-byte
+// loads that consecutive threads make for consecutive column quads) and writes
+// the 4 columns' 8-row runs as four 16-byte stores.
 __global__ void __launch_bounds__(256)
 gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
               int64_t nchunks, int64_t ntiles, uint8_t* __restrict__ tiles) {
-  const int64_t per_tile = (int64_t)kUKC * kUN + kUKT;   // A tasks, then b entries
-  const int64_t total = nchunks * ntiles * per_tile;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ct = t / per_tile, e = t % per_tile;
-    const int64_t c = ct / ntiles, z = ct % ntiles;
+  const bool vec = (lda & 3) == 0 && ((uintptr_t)A & 15) == 0;
+  const int64_t units = nchunks * ntiles;
+  for (int64_t ct = blockIdx.x; ct < units; ct += gridDim.x) {
+    const int64_t c = ct / ntiles, z = ct - c * ntiles;
     uint8_t* tile = tiles + (size_t)ct * kUTileBytes;
     const int64_t r0 = c * kUKT;
-    if (e < (int64_t)kUKC * kUN) {
-      const int nn = (int)(e % kUN), k8 = (int)(e / kUN);
+    for (int t = threadIdx.x; t < kUKC * (kUN / 4); t += blockDim.x) {
+      const int nn = 4 * (t % (kUN / 4)), k8 = t / (kUN / 4);
       const int64_t col = z * kUN + nn;
-      float f[8];
+      float f[8][4];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int64_t row = r0 + 8 * k8 + j;
-        f[j] = (row < m && col < n) ? __ldg(A + row * lda + col) : 0.f;
+        if (vec && row < m && col + 3 < n) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(A + row * lda + col));
+          f[j][0] = v.x;
+          f[j][1] = v.y;
+          f[j][2] = v.z;
+          f[j][3] = v.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) f[j][q] = (row < m && col + q < n) ? __ldg(A + row * lda + col + q) : 0.f;
+        }
       }
-      uint4 w;
-      w.x = pack_bf16(f[0], f[1]);
-      w.y = pack_bf16(f[2], f[3]);
-      w.z = pack_bf16(f[4], f[5]);
-      w.w = pack_bf16(f[6], f[7]);
-      *reinterpret_cast<uint4*>(tile + kmaj_off(nn, 8 * k8)) = w;
-    } else {
-      const int kk = (int)(e - (int64_t)kUKC * kUN);
-      const int64_t row = r0 + kk;
-      reinterpret_cast<float*>(tile + kUStageB)[kk] =
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 w;
+        w.x = pack_bf16(f[0][q], f[1][q]);
+        w.y = pack_bf16(f[2][q], f[3][q]);
+        w.z = pack_bf16(f[4][q], f[5][q]);
+        w.w = pack_bf16(f[6][q], f[7][q]);
+        *reinterpret_cast<uint4*>(tile + kmaj_off(nn + q, 8 * k8)) = w;
+      }
+    }
+    if (threadIdx.x < kUKT) {
+      const int64_t row = r0 + threadIdx.x;
+      reinterpret_cast<float*>(tile + kUStageB)[threadIdx.x] =
           (row < m && z == 0) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + row))) : 0.f;
     }
   }
 }
 
-// Warp roles: warps 0..15 generate G (and the b column) and move D into S at
-// the flush points; warp 16 issues the MMAs and the tile copies.  They meet
-// only at mbarriers: tile_ready (copy landed), g_ready (16 generator warps
+// Warp roles: warps 0..GW-1 generate G (and the b column) and move D into S
+// at the flush points; warp GW issues the MMAs and the tile copies.  They meet
+// only at mbarriers: tile_ready (copy landed), g_ready (all GW generator warps
 // arrived: the chunk's G tile is written and, at a flush point, D has been
 // added into S), gfree / bfree (the chunk's MMAs completed: its G stage / A
 // stage may be refilled; two commits after each chunk).  Phases never alias:
 // a barrier's next phase cannot complete before its current one was waited for.
-constexpr int kUGenWarps = 16;
-constexpr int kUThreads = 32 * (kUGenWarps + 1);
-__global__ void __launch_bounds__(kUThreads, 1)
+constexpr int kUGenWarps = 16;   // 32 would exceed 1024 threads with the MMA warp
+__global__ void __launch_bounds__(32 * (kUGenWarps + 1), 1)
 gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t n, int64_t d, uint64_t s0,
            const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA, int64_t ldsa,
            float* __restrict__ Sb, int64_t sbs, int* __restrict__ err, int flush_every) {
@@ -391,8 +416,10 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
     if (lane == 0) {
       // chunk c's tile (and b values) into A stage c mod kUBStages
       int64_t copied = 0;
+      RingPos<kUBStages> cpos;                                   // chunk `copied` in the A ring
       auto issue_copy = [&](int64_t c) {
-        const int s = (int)(c % kUBStages);
+        const int s = cpos.s;
+        cpos.next();
         const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * kUTileBytes;
         u_expect(&tile_ready[s], copy_bytes);
         u_copy(stB(s), src, (uint32_t)npad * 128u, &tile_ready[s]);
@@ -400,18 +427,21 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
         copied = c + 1;
       };
       for (int64_t c = 0; c < kUBStages - 1 && c < nchunks; ++c) issue_copy(c);
-      int64_t c_acc0 = 0, issued = 0;
+      int64_t issued = 0;
+      int since = 0;                                             // chunks in D since the last flush
+      RingPos<kUGStages> g;                                      // chunk c in the G ring
+      RingPos<kUBStages> t, tp;                                  // chunk c and c - 1 in the A ring
       for (int64_t c = 0; c < nchunks; ++c) {
-        const int sg = (int)(c % kUGStages), s = (int)(c % kUBStages);
-        if (!u_wait(&g_ready[sg], (uint32_t)((c / kUGStages) & 1))) { fail(); break; }
+        const int sg = g.s, s = t.s;
+        if (!u_wait(&g_ready[sg], g.ph)) { fail(); break; }
         if (s_fail) break;
-        if (c > c_acc0 && (c - c_acc0) % flush_every == 0) c_acc0 = c;   // D was moved into S
+        if (since == flush_every) since = 0;                     // D was moved into S
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int ks = 0; ks < kUKT / 16; ++ks) {
           const uint64_t ad = u_desc(u_smem(stA(sg)) + (uint32_t)ks * 256u);
           const uint64_t bd = u_desc(u_smem(stB(s)) + (uint32_t)ks * 256u);
-          const uint32_t acc = (c > c_acc0 || ks > 0) ? 1u : 0u;
+          const uint32_t acc = (since > 0 || ks > 0) ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
@@ -425,15 +455,19 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
                          u_smem(&bfree[s]))
                      : "memory");
         issued = c + 1;
+        ++since;
         // the copy kUBStages - 1 chunks ahead goes into the A stage chunk c - 1 used
         const int64_t cn = c + kUBStages - 1;
         if (cn < nchunks) {
-          if (c >= 1 && !u_wait(&bfree[(c - 1) % kUBStages], (uint32_t)(((c - 1) / kUBStages) & 1))) {
+          if (c >= 1 && !u_wait(&bfree[tp.s], tp.ph)) {
             fail();
             break;
           }
           issue_copy(cn);
         }
+        tp = t;
+        g.next();
+        t.next();
       }
       s_issued = issued;
       // the last issued chunk's commit tracks all earlier MMAs; TMEM stays allocated until then
@@ -446,14 +480,28 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
     }
     __syncwarp();
   } else {
-    // generator warps
-    int64_t c_acc0 = 0;                                          // first chunk since the last flush
+    // generator warps.  Thread (r, q) hashes outputs (i_begin / 8 + 8 c + q) d + r_base + r
+    // of the stream, q = tid / 128 + e * (threads / 128): the counter state advances by
+    // 8 d gamma per chunk
+    constexpr int kGenThreads = 32 * kUGenWarps;
+    constexpr int kPer = (kUKT / 8) / (kGenThreads / kUG);       // hashes per thread and chunk
+    static_assert(kPer >= 1 && kPer * (kGenThreads / kUG) == kUKT / 8, "generator threads must tile the chunk");
+    const int r = tid & (kUG - 1);
+    uint64_t state[kPer];
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const uint64_t q = (uint64_t)((tid >> 7) + e * (kGenThreads / kUG));
+      state[e] = s0 + (((uint64_t)(i_begin >> 3) + q) * (uint64_t)d + (uint64_t)(r_base + r) + 1) * kGamma;
+    }
+    const uint64_t state_step = 8ull * (uint64_t)d * kGamma;
+    int since = 0;                                               // chunks in D since the last flush
+    RingPos<kUGStages> g, gp;                                    // chunk c and c - 1 in the G ring
+    RingPos<kUBStages> t;                                        // chunk c in the A ring
     for (int64_t c = 0; c < nchunks; ++c) {
-      const int sg = (int)(c % kUGStages), s = (int)(c % kUBStages);
-      const int64_t i0 = i_begin + c * kUKT;
-      // G stage sg is free once chunk c - kUGStages's MMAs are done; the b values come with the tile
-      const bool ok = (c < kUGStages || u_wait(&gfree[sg], (uint32_t)(((c - kUGStages) / kUGStages) & 1))) &&
-                      u_wait(&tile_ready[s], (uint32_t)((c / kUBStages) & 1));
+      const int sg = g.s, s = t.s;
+      // G stage sg is free once chunk c - kUGStages's MMAs are done (the phase before
+      // g.ph); the b values come with the tile
+      const bool ok = (c < kUGStages || u_wait(&gfree[sg], g.ph ^ 1u)) && u_wait(&tile_ready[s], t.ph);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) fail();
         break;
@@ -467,15 +515,13 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
       // masking: their products never reach SA (rows past d are not written out;
       // the converted A and b are zero there).
       {
-        const int r = tid & (kUG - 1);
-        const uint64_t kg = (uint64_t)(r_base + r);
         const float* bc = stb(s);
         float part = 0.f;
-        constexpr int kGenThreads = 32 * kUGenWarps;
 #pragma unroll
-        for (int e = 0; e < (kUKT / 8) / (kGenThreads / kUG); ++e) {
+        for (int e = 0; e < kPer; ++e) {
           const int q = (tid >> 7) + e * (kGenThreads / kUG);
-          const uint64_t key = splitmix_at(s0, ((uint64_t)(i0 >> 3) + (uint64_t)q) * (uint64_t)d + kg);
+          const uint64_t key = mix64(state[e]);
+          state[e] += state_step;
           const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
           float v[8];
 #pragma unroll
@@ -510,20 +556,23 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (c > c_acc0 && (c - c_acc0) % flush_every == 0) {
-        // chunks c_acc0 .. c - 1 are in D: wait for their MMAs, add D into S; the
-        // MMA warp restarts D with chunk c only after every warp has arrived
-        const int64_t cl = c - 1;
-        if (!__all_sync(0xffffffffu, u_wait(&gfree[cl % kUGStages], (uint32_t)((cl / kUGStages) & 1)))) {
+      if (since == flush_every) {
+        // chunks c - flush_every .. c - 1 are in D: wait for their MMAs, add D into
+        // S; the MMA warp restarts D with chunk c only after every warp has arrived
+        if (!__all_sync(0xffffffffu, u_wait(&gfree[gp.s], gp.ph))) {
           if (lane == 0) fail();
           break;
         }
         tmem_flush(false);
-        c_acc0 = c;
+        since = 0;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(u_smem(&g_ready[sg])) : "memory");
+      ++since;
+      gp = g;
+      g.next();
+      t.next();
     }
   }
   __syncthreads();
@@ -606,11 +655,12 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
     SNS_CUDA_TRY(cudaGetLastError());
     SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
     dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
+    const float scale = (float)(1.0 / std::sqrt((double)d));
     {
       SNS_PROF(K_GAUSS, st);
-      gauss_umma<<<grid, kUThreads, gauss_umma_smem(), st>>>(tiles, gg.ntiles, a.m, a.n, d, s0, dtab, gg.kchunk,
-                                                             (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs,
-                                                             err, kUFlush);
+      gauss_umma<<<grid, 32 * (kUGenWarps + 1), gauss_umma_smem(), st>>>(tiles, gg.ntiles, a.m, a.n, d, s0, dtab,
+                                                                         gg.kchunk, scale, SA, ldsa, Sb, sbs, err,
+                                                                         kUFlush);
     }
     SNS_CUDA_TRY(cudaGetLastError());
     return SNS_OK;
