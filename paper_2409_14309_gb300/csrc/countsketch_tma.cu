@@ -173,24 +173,28 @@ cs_build_list(uint32_t d, int64_t nblk, const uint32_t* __restrict__ sorted, con
 }
 
 // ---------------------------------------------------------------------------
-// Phases 1 + 1b in one cooperative launch (one CTA per 4096-row block, all
-// co-resident): the same hash, per-warp histograms and stable per-block order
+// Phases 1 + 1b in one cooperative launch (one CTA per block of rows_per_blk
+// = 4096 consecutive rows, all co-resident; measured: 16 warps and two CTAs
+// per SM ran faster than one 32-warp CTA per SM with equal blocks): the same hash, per-warp histograms and stable per-block order
 // as cs_sort_blocks, and the same bucket-major list, chunk tables and
 // empty-bucket zeroing as cs_build_list, without the intermediate per-block
 // sorted array.  Two grid barriers separate the phases:
 //   A  per block: hash every row once (bucket | sign kept in shared memory),
-//      per-warp bucket histograms, block totals -> seg[k * nblk + blk];
+//      per-warp bucket histograms and each row's stable rank among the rows
+//      of its bucket that its warp hashed before it, block totals ->
+//      seg[k * nblk + blk];
 //   B  per bucket (buckets spread over the CTAs): exclusive scan of its block
 //      totals in block order (the bucket's start in each block), total -> btot;
 //   C  per CTA: bucket bases and chunk bases by scanning btot (each CTA scans
-//      all d totals itself), chunk table and zeroed SA rows for its buckets,
-//      then its block's rows scattered to list[bbase + block start + warp
-//      offset + rank], rows of a bucket in ascending order.
+//      all d totals itself; btot and the block's starts are read in one
+//      round trip), chunk table and zeroed SA rows for its buckets, then its
+//      block's rows scattered to list[bbase + block start + warp offset +
+//      rank] (no second multisplit), rows of a bucket in ascending order.
 // The grid barriers are bounded: a CTA whose wait gives up sets the error word
 // and skips its remaining work but still arrives at later barriers; every CTA
 // reads the word before scattering, positions are checked against m, and the
 // gather returns at once when the word is set.
-constexpr int kPlanWarps = 8;
+constexpr int kPlanWarps = 16;
 SNS_D uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -274,23 +278,31 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
              uint32_t* __restrict__ ticket, int64_t nticket, uint32_t* __restrict__ btot, uint32_t* __restrict__ bbase,
              uint32_t* __restrict__ list, uint32_t* __restrict__ cbase, uint32_t* __restrict__ ctab,
              float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs, int64_t n,
-             uint32_t* __restrict__ bar, int* __restrict__ err, int nbits) {
+             uint32_t* __restrict__ bar, int* __restrict__ err, int nbits, int rows_per_blk) {
   extern __shared__ __align__(16) uint8_t psm[];
   uint16_t* cnt = reinterpret_cast<uint16_t*>(psm);                 // [W][d] per-warp counts, then offsets
   uint16_t* hb = cnt + (size_t)kPlanWarps * d;                       // [R] bucket | sign << 15
-  uint32_t* sb = reinterpret_cast<uint32_t*>(hb + kListRowsPerBlock);  // [d] bases, then [d] totals (phase C)
+  uint16_t* rk = hb + rows_per_blk;                                  // [R] rank within (warp, bucket)
+  uint32_t* sb = reinterpret_cast<uint32_t*>(rk + rows_per_blk);     // [d] bases; then [d] totals, [d] starts (C)
   __shared__ uint32_t wsum[kPlanWarps];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t blk = blockIdx.x;
-  const int64_t r0 = blk * kListRowsPerBlock;
+  const int64_t r0 = blk * rows_per_blk;
   const uint32_t G = gridDim.x;
-  constexpr int kRowsPerWarp = kListRowsPerBlock / kPlanWarps;
+  const int kRowsPerWarp = rows_per_blk / kPlanWarps;                // a multiple of 32
   constexpr uint32_t kNone = 0xFFFFu;
   const uint32_t kOut = (1u << nbits) - 1u;        // >= d: groups the rows past m in the masks
+  // a block with no row past m needs no bit for kOut
+  const int nb = (r0 + rows_per_blk <= m && nbits > 1 && ((d - 1) >> (nbits - 1)) == 0) ? nbits - 1 : nbits;
 
   // ---- A: hash, per-warp histograms, block totals
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < nticket; i += (int64_t)G * blockDim.x) ticket[i] = 0;
-  for (int i = tid; i < kPlanWarps * (int)d; i += blockDim.x) cnt[i] = 0;
+  if ((d & 7) == 0) {
+    uint4* c4 = reinterpret_cast<uint4*>(cnt);
+    for (int i = tid; i < kPlanWarps * (int)d / 8; i += blockDim.x) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    for (int i = tid; i < kPlanWarps * (int)d; i += blockDim.x) cnt[i] = 0;
+  }
   __syncthreads();
   for (int j = 0; j < kRowsPerWarp; j += 32) {
     const int loc = w * kRowsPerWarp + j + lane;
@@ -302,8 +314,11 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
       sgn = (uint32_t)(key >> 63);
     }
     hb[loc] = (uint16_t)(h == kNone ? kNone : (h | (sgn << 15)));
-    const unsigned peers = equal_lanes(h == kNone ? kOut : h, nbits);
-    if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
+    const unsigned peers = equal_lanes(h == kNone ? kOut : h, nb);
+    const uint32_t before = h != kNone ? cnt[w * d + h] : 0u;   // every peer reads it before the update
+    rk[loc] = (uint16_t)(before + __popc(peers & ((1u << lane) - 1u)));
+    __syncwarp();
+    if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] = (uint16_t)(before + __popc(peers));
     __syncwarp();
   }
   __syncthreads();
@@ -323,7 +338,7 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
   // (the block totals of 8 rounds of 32 blocks are loaded at once)
   if (ok1) {
     constexpr int kAhead = 8;
-    for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
+    for (int64_t k = (int64_t)w * G + blockIdx.x; k < d; k += (int64_t)G * kPlanWarps) {
       uint32_t* sk = seg + (size_t)k * nblk;
       uint32_t run = 0;
       for (int64_t b0 = 0; b0 < nblk; b0 += 32 * kAhead) {
@@ -353,14 +368,18 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
   if (!grid_barrier(bar, 2 * G, err)) return;           // CTA-uniform
 
   // ---- C: bases, chunk tables, empty buckets, scatter.  The bucket totals
-  // are read from L2 once, into shared memory beside the bases.
+  // and this block's starts are read from L2 together, into shared memory.
   uint32_t* stot = sb + d;
-  for (int k = tid; k < (int)d; k += blockDim.x) stot[k] = __ldcg(btot + k);
+  uint32_t* sst = sb + 2 * (size_t)d;
+  for (int k = tid; k < (int)d; k += blockDim.x) {
+    stot[k] = __ldcg(btot + k);
+    sst[k] = __ldcg(seg + (size_t)k * nblk + blk);
+  }
   __syncthreads();
   const uint32_t nchunks =
       block_scan_buckets(d, [&](int k) { return (stot[k] + kChunkRows - 1) / kChunkRows; }, sb, wsum);
   if (blockIdx.x == 0 && tid == 0) cbase[d] = nchunks;
-  for (int64_t k = (int64_t)blockIdx.x * kPlanWarps + w; k < d; k += (int64_t)G * kPlanWarps) {
+  for (int64_t k = (int64_t)w * G + blockIdx.x; k < d; k += (int64_t)G * kPlanWarps) {
     const uint32_t len = stot[k];
     const uint32_t nch = (len + kChunkRows - 1) / kChunkRows;
     for (uint32_t c = lane; c < nch; c += 32) ctab[sb[k] + c] = (uint32_t)k;
@@ -374,28 +393,24 @@ cs_plan_coop(int64_t m, uint32_t d, uint64_t s0, int64_t nblk, uint32_t* __restr
   block_scan_buckets(d, [&](int k) { return stot[k]; }, sb, wsum);
   for (int k = tid; k < (int)d; k += blockDim.x) {
     if (blockIdx.x == 0) bbase[k] = sb[k];
-    sb[k] += __ldcg(seg + (size_t)k * nblk + blk);            // this block's start in bucket k
+    sb[k] += sst[k];                                          // this block's start in bucket k
   }
+  // the gather may be scheduled now; it waits for this grid to complete
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
   for (int j = 0; j < kRowsPerWarp; j += 32) {
     const int loc = w * kRowsPerWarp + j + lane;
-    const int64_t row = r0 + loc;
     const uint32_t hw = hb[loc];
-    const uint32_t h = hw == kNone ? kNone : (hw & 0x7FFFu);
-    const unsigned peers = equal_lanes(h == kNone ? kOut : h, nbits);
-    if (h != kNone) {
-      const uint32_t pos = sb[h] + cnt[w * d + h] + __popc(peers & lt);
-      if (pos < (uint64_t)m) list[pos] = (uint32_t)row | ((hw >> 15) << 31);
+    if (hw != kNone) {
+      const uint32_t h = hw & 0x7FFFu;
+      const uint32_t pos = sb[h] + cnt[w * d + h] + rk[loc];
+      if (pos < (uint64_t)m) list[pos] = (uint32_t)(r0 + loc) | ((hw >> 15) << 31);
     }
-    __syncwarp();
-    if (h != kNone && lane == __ffs(peers) - 1) cnt[w * d + h] += (uint16_t)__popc(peers);
-    __syncwarp();
   }
 }
 
-size_t cs_plan_smem(int64_t d) {
-  return (size_t)kPlanWarps * d * 2 + (size_t)kListRowsPerBlock * 2 + (size_t)d * 8;
+size_t cs_plan_smem(int64_t d, int64_t rows_per_blk) {
+  return (size_t)kPlanWarps * d * 2 + (size_t)rows_per_blk * 4 + (size_t)d * 12;
 }
 
 // ---------------------------------------------------------------------------
@@ -636,6 +651,9 @@ cs_gather_warp(const float* __restrict__ A, int64_t lda, const float* __restrict
                const uint32_t* __restrict__ ctab, uint32_t d, uint32_t* __restrict__ ticket,
                uint32_t* __restrict__ next_item, float* __restrict__ part, float* __restrict__ SA, int64_t ldsa,
                float* __restrict__ Sb, int64_t sbs, const int* __restrict__ err) {
+  // launched as a programmatic dependent of the plan kernel: nothing the plan
+  // writes is read before the plan grid has completed (no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // a plan phase that gave up a bounded wait left its tables incomplete
   if (*err != 0) return;
   const int lane = threadIdx.x & 31;
@@ -825,35 +843,48 @@ static int warp_tile_choice() {
   return sel;
 }
 template <int VPL, int U>
+// With `dependent`, the gather is launched as a programmatic dependent of the
+// kernel before it on `st` (the plan): its launch and CTA placement overlap the
+// plan's tail, and it waits for the plan grid before reading its tables.
 static sns_status launch_warp_gather_t(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA,
-                                       int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st) {
+                                       int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st, bool dependent) {
   constexpr int CT = 128 * VPL;
   const int64_t ntile = (a.n + CT - 1) / CT;
   auto kern = cs_gather_warp<VPL, U>;
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
   const int64_t grid2 = (int64_t)num_sms() * std::max(occ, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid2);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
   {
     SNS_PROF(K_CS_GATHER, st);
-    kern<<<(unsigned)grid2, 256, 0, st>>>(
-        static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile,
+    SNS_CUDA_TRY(cudaLaunchKernelEx(
+        &cfg, kern, static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.n, ntile,
         reinterpret_cast<const uint32_t*>(ws + L.off_list), reinterpret_cast<const uint32_t*>(ws + L.off_btot),
         reinterpret_cast<const uint32_t*>(ws + L.off_bbase), reinterpret_cast<const uint32_t*>(ws + L.off_cbase),
         reinterpret_cast<const uint32_t*>(ws + L.off_ctab), (uint32_t)d, reinterpret_cast<uint32_t*>(ws + L.off_ticket),
         reinterpret_cast<uint32_t*>(ws + L.off_err) + 1, reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb,
-        sbs, reinterpret_cast<const int*>(ws + L.off_err));
+        sbs, reinterpret_cast<const int*>(ws + L.off_err)));
   }
   SNS_CUDA_TRY(cudaGetLastError());
   return SNS_OK;
 }
 static sns_status launch_warp_gather(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA,
-                                     int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st) {
+                                     int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st, bool dependent = false) {
   int choice = warp_tile_choice();
   if (choice == 0) choice = a.n > 128 ? 2 : 1;
   switch (choice) {
-    case 2: return launch_warp_gather_t<2, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
-    case 3: return launch_warp_gather_t<2, 4>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
-    default: return launch_warp_gather_t<1, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+    case 2: return launch_warp_gather_t<2, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st, dependent);
+    case 3: return launch_warp_gather_t<2, 4>(a, d, L, ws, SA, ldsa, Sb, sbs, st, dependent);
+    default: return launch_warp_gather_t<1, 8>(a, d, L, ws, SA, ldsa, Sb, sbs, st, dependent);
   }
 }
 
@@ -896,14 +927,23 @@ bool cs_bulk_gather_selected() {
 sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsLayout& L, uint8_t* ws, float* SA,
                          int64_t ldsa, float* Sb, int64_t sbs, cudaStream_t st, bool* used) {
   *used = false;
-  const size_t smem = cs_plan_smem(d);
+  // ranks and offsets within a block are 16-bit; a block of at least 4096
+  // rows keeps the block totals within the two-kernel plan's table
+  const int64_t rows_per_blk = kListRowsPerBlock;
+  const int64_t nblk_plan = (a.m + rows_per_blk - 1) / rows_per_blk;
+  const size_t smem = cs_plan_smem(d, rows_per_blk);
   SNS_CUDA_TRY(raise_smem_limit((const void*)cs_plan_coop));
+  int dev = 0, smem_max = 0;
+  SNS_CUDA_TRY(cudaGetDevice(&dev));
+  SNS_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem + 1024 > (size_t)smem_max) return SNS_OK;
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_plan_coop, kPlanWarps * 32, smem));
-  if ((int64_t)occ * num_sms() < L.nblk || L.nblk >= ((int64_t)1 << 31)) return SNS_OK;
+  if ((int64_t)occ * num_sms() < nblk_plan || nblk_plan > L.nblk) return SNS_OK;
   *used = true;
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));
-  int64_t m = a.m, nblk = L.nblk, nticket = L.nticket, n = a.n, ldsa_ = ldsa, sbs_ = sbs;
+  int64_t m = a.m, nblk = nblk_plan, nticket = L.nticket, n = a.n, ldsa_ = ldsa, sbs_ = sbs;
+  int rpb = (int)rows_per_blk;
   uint32_t dd = (uint32_t)d;
   uint64_t s0 = shift_state(stream_state(seed, kStreamCountSketch), a.row0);
   uint32_t* seg = reinterpret_cast<uint32_t*>(ws + L.off_seg);
@@ -918,13 +958,13 @@ sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsL
   int nbits = 1;                                   // bit length of d
   while (((int64_t)1 << nbits) <= d) ++nbits;
   void* args[] = {&m, &dd, &s0, &nblk, &seg, &ticket, &nticket, &btot, &bbase, &list, &cbase, &ctab,
-                  &SA, &ldsa_, &Sb, &sbs_, &n, &bar, &err, &nbits};
+                  &SA, &ldsa_, &Sb, &sbs_, &n, &bar, &err, &nbits, &rpb};
   {
     SNS_PROF(K_CS_SORT, st);
     SNS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cs_plan_coop, dim3((unsigned)nblk), dim3(kPlanWarps * 32),
                                              args, smem, st));
   }
-  return launch_warp_gather(a, d, L, ws, SA, ldsa, Sb, sbs, st);
+  return launch_warp_gather(a, d, L, ws, SA, ldsa, Sb, sbs, st, /*dependent=*/true);
 }
 
 }  // namespace sns
