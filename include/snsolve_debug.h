@@ -61,6 +61,27 @@ sns_status snsolve_debug_form_y(const sns_problem* prob, const double* Rinv, voi
  * meant for tests of the timeout path. */
 void snsolve_debug_set_qr_wait_limit(int64_t polls);
 
+/* ---- Host-side fault injection ----------------------------------------------
+ * Arms one failure that a host-side check reports; no GPU faults, traps or
+ * hangs.  spec = "<kind>[:<n>]": the n-th occurrence (n >= 1, default 1) of
+ * <kind> fails, once, and the fault disarms.  Kinds:
+ *   "alloc"   one of the library's own allocations (snsolve_create's pinned
+ *             buffer, a thread's pinned status buffer, the server arena, the
+ *             batched staging buffer) returns SNS_ENOMEM without allocating;
+ *   "launch"  the check after a kernel launch returns SNS_ECUDA (the kernel
+ *             was launched and completes; the call stops there);
+ *   "timeout" the host's read of a device error word (sketch waits, QR polls)
+ *             reports an expired wait: SNS_ETIMEOUT.
+ * NULL, "" or "none" disarms.  SNS_EINVAL for any other spec.  Process-wide;
+ * the environment variable SNSOLVE_FAULT holds the same spec, read at the
+ * first check unless this call came first.  snsolve_last_cuda_error() names
+ * an injected failure. */
+sns_status snsolve_debug_set_fault(const char* spec);
+
+/* Armed kind (0 none, 1 alloc, 2 launch, 3 timeout) and, in *left (may be
+ * NULL), the occurrences still to pass before it fires (counting this one). */
+int snsolve_debug_fault_armed(int64_t* left);
+
 /* ---- Measurement ----------------------------------------------------------
  * Number of kernel launches this library has issued in this process. */
 uint64_t snsolve_launch_count(void);

@@ -83,6 +83,8 @@ SIGNATURES = [
     ("snsolve_tune_reset", None, []),
     ("snsolve_debug_set_qr_wait_limit", None, [i64]),
     ("snsolve_debug_form_y", C.c_int, [P(sns_problem), vp, vp, i64, vp]),
+    ("snsolve_debug_set_fault", C.c_int, [C.c_char_p]),
+    ("snsolve_debug_fault_armed", C.c_int, [P(i64)]),
 ]
 
 _lib = None

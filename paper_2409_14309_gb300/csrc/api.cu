@@ -27,6 +27,10 @@ sns_status record_cuda_error(cudaError_t e) {
   snprintf(t_err, sizeof(t_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   return SNS_ECUDA;
 }
+sns_status record_injected(const char* what, sns_status s) {
+  snprintf(t_err, sizeof(t_err), "%s", what);
+  return s;
+}
 
 static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -99,6 +103,10 @@ static SideStream& thread_side_stream() {
 }
 static double* thread_pinned() {
   if (!t_pinned.p) {
+    if (fault_hit(kFaultAlloc)) {
+      record_injected("injected allocation failure", SNS_ENOMEM);
+      return nullptr;
+    }
     if (cudaHostAlloc(&t_pinned.p, 4096, cudaHostAllocDefault) != cudaSuccess) t_pinned.p = nullptr;
   }
   return t_pinned.p;
@@ -297,6 +305,7 @@ sns_status snsolve_create(sns_ctx** ctx, int device) {
   int cur = 0;
   SNS_CUDA_TRY(cudaGetDevice(&cur));
   if (cur != device) SNS_CUDA_TRY(cudaSetDevice(device));
+  if (fault_hit(kFaultAlloc)) return record_injected("injected allocation failure", SNS_ENOMEM);
   sns_ctx* c = new sns_ctx();
   c->device = device;
   e = cudaHostAlloc(&c->pinned, 4096, cudaHostAllocDefault);
@@ -398,6 +407,7 @@ sns_status snsolve_solve_sketched(sns_ctx* ctx, const void* SAaug, int64_t ld, i
   int32_t qs = 0, qerr = 0;
   memcpy(&qs, hp + 21, 4);
   if (coop) memcpy(&qerr, hp + 23, 4);
+  if (fault_hit(kFaultTimeout)) qerr = 1;
   const int status = qerr ? SNS_ETIMEOUT : qs;
   if (info) {
     memset(info, 0, sizeof(*info));
@@ -425,6 +435,7 @@ sns_status snsolve_sketch_status(const sns_problem* prob, const sns_sketch_desc*
   SNS_CUDA_TRY(cudaStreamSynchronize(st));
   int32_t e = 0;
   memcpy(&e, hp + 20, 4);
+  if (fault_hit(kFaultTimeout)) e = 1;
   return e ? SNS_ETIMEOUT : SNS_OK;
 }
 
@@ -499,6 +510,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     memcpy(&qs, hp + 16, 4);
     if (coop) memcpy(&qerr, hp + 18, 4);
     if (skerr) memcpy(&serr, hp + 19, 4);
+    if (fault_hit(kFaultTimeout)) serr = 1;
     sres = hp[17];
     if (qerr || serr) {
       info_fill(info, SNS_ETIMEOUT, 0, 0, 0.0, 0.0, 0.0);
@@ -645,6 +657,15 @@ sns_status snsolve_debug_srht_sample_ws(int64_t mp, int64_t d, size_t* bytes) {
   return SNS_OK;
 }
 void snsolve_debug_set_qr_wait_limit(int64_t polls) { set_qr_wait_limit((long long)polls); }
+
+sns_status snsolve_debug_set_fault(const char* spec) { return fault_arm(spec); }
+
+int snsolve_debug_fault_armed(int64_t* left) {
+  long long l = 0;
+  const int k = fault_armed(&l);
+  if (left) *left = (int64_t)l;
+  return k;
+}
 
 sns_status snsolve_debug_form_y(const sns_problem* prob, const double* Rinv, void* Y, int64_t ldy, void* stream) {
   sns_status s = validate_problem(prob);

@@ -195,7 +195,7 @@ static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_
     SNS_CUDA_TRY(cudaMemcpyAsync(w + L.off_tasks, host_tasks, task_bytes, cudaMemcpyHostToDevice, s));
     SNS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, s));
     batched_fused<<<grid, S.threads, smem, s>>>(tasks, order, nprob, counter, outs, S.ct);
-    SNS_CUDA_TRY(cudaGetLastError());
+    SNS_LAUNCH_CHECK();
     return SNS_OK;
   };
   SNS_PROF(K_BATCH, st);
@@ -254,6 +254,7 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
     if (g_stage) cudaFreeHost(g_stage);
     g_stage = nullptr;
     g_stage_bytes = 0;
+    if (fault_hit(kFaultAlloc)) return record_injected("injected allocation failure", SNS_ENOMEM);
     SNS_CUDA_TRY(cudaHostAlloc(&g_stage, stage_need, cudaHostAllocDefault));
     g_stage_bytes = stage_need;
   }

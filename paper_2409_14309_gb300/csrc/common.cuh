@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "snsolve.h"
+#include "fault.h"
 
 #define SNS_HD __host__ __device__ __forceinline__
 #define SNS_D __device__ __forceinline__
@@ -141,6 +142,15 @@ SNS_D void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" 
   do {                                                       \
     cudaError_t _e = (expr);                                 \
     if (_e != cudaSuccess) return sns::record_cuda_error(_e); \
+  } while (0)
+
+// After a kernel launch: the launch's own error, or a host-side injected
+// launch failure (fault.h).
+#define SNS_LAUNCH_CHECK()                                                        \
+  do {                                                                            \
+    if (::sns::fault_hit(::sns::kFaultLaunch))                                    \
+      return ::sns::record_injected("injected launch failure", SNS_ECUDA);       \
+    SNS_CUDA_TRY(cudaGetLastError());                                             \
   } while (0)
 
 namespace sns {

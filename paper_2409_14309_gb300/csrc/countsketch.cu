@@ -625,7 +625,7 @@ sns_status cs_phase1(int64_t m, int64_t d, uint64_t seed, int64_t row0, const Cs
       reinterpret_cast<uint32_t*>(ws + L.off_seg), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
       L.nticket, reinterpret_cast<uint32_t*>(ws + L.off_btot));
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -649,7 +649,7 @@ static sns_status launch_gather(const DenseArgs& a, int64_t d, const CsLayout& L
       reinterpret_cast<uint32_t*>(ws + L.off_ticket), reinterpret_cast<T*>(ws + L.off_part), static_cast<T*>(SA), ldsa,
       static_cast<T*>(Sb), sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -714,7 +714,7 @@ sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, v
                                              a.m, a.n, (uint32_t)d, s0, static_cast<float*>(SA), ldsa,
                                              static_cast<float*>(Sb), sbs);
     }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -739,7 +739,7 @@ sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, i
       reinterpret_cast<const uint32_t*>(w + L.off_sorted), reinterpret_cast<const uint32_t*>(w + L.off_seg),
       reinterpret_cast<uint32_t*>(w + L.off_ticket), reinterpret_cast<float*>(w + L.off_part), SA, ldsa, Sb, sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -834,7 +834,7 @@ sns_status cs_apply_csr_stream(const CsrArgs& a, int64_t d, uint64_t seed, float
                                        shift_state(stream_state(seed, kStreamCountSketch), a.row0), SA, ldsa,
                                        Sb, sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -868,7 +868,7 @@ sns_status cs_apply_sparse_sign(const DenseArgs& a, int64_t d, int zeta, uint64_
                                                     static_cast<const float*>(a.b), a.m, a.n, (uint32_t)d, zeta, s0,
                                                     s4, scale, SA, ldsa, Sb, sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -892,7 +892,7 @@ sns_status debug_countsketch_hash(int64_t m, int64_t d, uint64_t seed, uint32_t*
     SNS_PROF(K_MISC, st);
   cs_hash_dump<<<num_sms() * 4, 256, 0, st>>>(m, (uint32_t)d, stream_state(seed, kStreamCountSketch), h, s);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 sns_status debug_stream_keys(uint64_t seed, int stream, int64_t start, int64_t count, uint64_t* out, cudaStream_t st) {
@@ -900,7 +900,7 @@ sns_status debug_stream_keys(uint64_t seed, int stream, int64_t start, int64_t c
     SNS_PROF(K_MISC, st);
   stream_keys_dump<<<num_sms() * 4, 256, 0, st>>>(stream_state(seed, (uint64_t)stream), start, count, out);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 

@@ -824,7 +824,7 @@ static sns_status launch_tma(const DenseArgs& a, int64_t d, const CsLayout& L, u
         reinterpret_cast<const uint32_t*>(ws + L.off_bbase), reinterpret_cast<uint32_t*>(ws + L.off_ticket),
         reinterpret_cast<float*>(ws + L.off_part), SA, ldsa, Sb, sbs, reinterpret_cast<int*>(ws + L.off_err));
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -874,7 +874,7 @@ static sns_status launch_warp_gather_t(const DenseArgs& a, int64_t d, const CsLa
         reinterpret_cast<uint32_t*>(ws + L.off_err) + 1, reinterpret_cast<float*>(ws + L.off_wpart), SA, ldsa, Sb,
         sbs, reinterpret_cast<const int*>(ws + L.off_err)));
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 static sns_status launch_warp_gather(const DenseArgs& a, int64_t d, const CsLayout& L, uint8_t* ws, float* SA,
@@ -905,7 +905,7 @@ sns_status cs_tma_phase2(const DenseArgs& a, int64_t d, const CsLayout& L, uint8
                                            reinterpret_cast<uint32_t*>(ws + L.off_list), cbase, ctab,
                                            use_tma ? nullptr : SA, ldsa, Sb, sbs, a.n);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   if (use_tma)
     return a.n <= 128 ? launch_tma<128>(a, d, L, ws, SA, ldsa, Sb, sbs, st)
                       : launch_tma<256>(a, d, L, ws, SA, ldsa, Sb, sbs, st);

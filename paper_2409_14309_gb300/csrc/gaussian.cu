@@ -652,7 +652,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
                                                    static_cast<const float*>(a.b), a.m, a.n, gg.nchunks, gg.ntiles,
                                                    tiles);
     }
-    SNS_CUDA_TRY(cudaGetLastError());
+    SNS_LAUNCH_CHECK();
     SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
     dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
     const float scale = (float)(1.0 / std::sqrt((double)d));
@@ -662,7 +662,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
                                                                          gg.kchunk, scale, SA, ldsa, Sb, sbs, err,
                                                                          kUFlush);
     }
-    SNS_CUDA_TRY(cudaGetLastError());
+    SNS_LAUNCH_CHECK();
     return SNS_OK;
   }
   const int64_t q = a.n + 1;
@@ -678,7 +678,7 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
                                    s0, dtab, kchunk,
                                    (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 

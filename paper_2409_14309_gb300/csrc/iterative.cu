@@ -916,7 +916,7 @@ static sns_status launch_dense_f32(const DenseArgs& a, const IterWs& W, const do
                                   W.ticket, W.lvl2, pcg_vecs(W)));
     }
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -971,7 +971,7 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
       SNS_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kPassThreads), args, smem, st));
     }
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -998,7 +998,7 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
                                     ca->n, W.z32, W.part, W.ticket, W.lvl2, pcg_vecs(W)));
     }
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -1138,7 +1138,7 @@ sns_status pgram_build(const double* Rinv, int64_t n, double* P, cudaStream_t st
     SNS_PROF(K_RINV, st);
     pgram_kernel<<<(unsigned)(T * (T + 1) / 2), kPT * kPT, 0, st>>>(Rinv, n, P);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -1158,7 +1158,7 @@ sns_status pcg_start(const IterWs& W, int64_t n, double tol, cudaStream_t st, bo
       pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, W.g, pcg_vecs(W), W.ticket + kPcgTicket, tol,
                                                                nullptr, 0);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 sns_status pcg_start_rhs(const IterWs& W, int64_t n, double tol, const double* v, cudaStream_t st) {
@@ -1167,7 +1167,7 @@ sns_status pcg_start_rhs(const IterWs& W, int64_t n, double tol, const double* v
     pcg_matvec<true><<<pcg_grid(n), kSmallThreads, 0, st>>>(W.P, n, v, pcg_vecs(W), W.ticket + kPcgTicket, tol,
                                                              nullptr, 0);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st, bool factored) {
@@ -1185,7 +1185,7 @@ sns_status pcg_step(const IterWs& W, int64_t n, cudaStream_t st, bool factored) 
       SNS_CUDA_TRY(launch_dependent(pcg_matvec<false>, dim3(pcg_grid(n)), dim3(kSmallThreads), 0, st, W.P, n, W.rx,
                                     pcg_vecs(W), W.ticket + kPcgTicket, 0.0, (const double*)nullptr, 0));
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -1224,7 +1224,7 @@ sns_status diag_range(const double* W, int64_t ldw, int64_t n, double* out, cuda
     SNS_PROF(K_QR, st);
     diag_range_kernel<<<1, kSmallThreads, 0, st>>>(W, ldw, n, out);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st) {
@@ -1233,7 +1233,7 @@ sns_status pcg_apply(const IterWs& W, int64_t n, double* x, cudaStream_t st) {
     pcg_apply_kernel<<<(unsigned)std::max<int64_t>(1, (n + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0,
                        st>>>(W.dx, n, x);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -1268,7 +1268,7 @@ sns_status eta_eval(const IterWs& W, int64_t n, double* host_out, cudaStream_t s
     SNS_PROF(K_ETA, st);
   eta_kernel<<<1, kSmallThreads, 0, st>>>(W.g, n, W.scal);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   SNS_CUDA_TRY(cudaMemcpyAsync(host_out, W.scal + 8, kHostSlots * sizeof(double), cudaMemcpyDeviceToHost, st));
   return SNS_OK;
 }

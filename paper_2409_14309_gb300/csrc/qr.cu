@@ -44,7 +44,7 @@ sns_status qr_load_colmajor(const void* SAaug, int64_t ld, bool f64, int64_t d, 
       SNS_PROF(K_QR_LOAD, st);
     qr_load_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(SAaug), ld, d, q, W);
     }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -74,7 +74,7 @@ sns_status qr_solve_one(const QrOut& o, cudaStream_t st) {
     SNS_PROF(K_QR, st);
   qr_one_kernel<<<1, kQrThreads, smem, st>>>(o);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -88,7 +88,7 @@ sns_status qr_solve_tasks(const QrOut* tasks_dev, int ntasks, int64_t max_d, cud
     SNS_PROF(K_QR, st);
   qr_tasks_kernel<<<grid, kQrThreads, smem, st>>>(tasks_dev, ntasks);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -476,7 +476,7 @@ sns_status qr_solve_coop(const QrOut& o, void* ws, cudaStream_t st) {
     SNS_PROF(K_QR, st);
     qr_finish_kernel<<<1, kFinishThreads, zs, st>>>(o);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -527,7 +527,7 @@ sns_status rinv_build(const double* W, int64_t ldw, int64_t n, double* Rinv, dou
     SNS_PROF(K_RINV, st);
     rinv_kernel<<<grid, kRinvThreads, smem, st>>>(W, ldw, n, Rinv, RinvT, identity ? 1 : 0);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 

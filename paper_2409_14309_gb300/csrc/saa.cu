@@ -138,7 +138,7 @@ static sns_status launch_form_y(const T* A, int64_t lda, int64_t m, int64_t n, c
     SNS_PROF(K_SAA_Y, st);
     form_y_kernel<T><<<grid, kYWarps * 32, 0, st>>>(A, lda, m, n, Rinv, Y, ldy);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -158,7 +158,7 @@ sns_status saa_matvec(const double* M, int64_t n, const double* v, double* out, 
     if (accumulate) tri_matvec_kernel<true><<<grid, 128, 0, st>>>(M, n, v, out);
     else tri_matvec_kernel<false><<<grid, 128, 0, st>>>(M, n, v, out);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -168,7 +168,7 @@ sns_status ident_build(double* P, int64_t n, cudaStream_t st) {
     SNS_PROF(K_RINV, st);
     ident_fill_kernel<<<grid, 256, 0, st>>>(P, n);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 

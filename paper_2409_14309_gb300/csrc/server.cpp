@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "snsolve.h"
+#include "fault.h"
 
 namespace sns {
 sns_status record_cuda_error(cudaError_t e);
@@ -176,6 +177,10 @@ sns_status snsolve_server_create(sns_server** out, sns_ctx* ctx, size_t hbm_budg
   const size_t cap = (size_t)32 << 30;
   if (arena > cap) arena = cap;
   arena = (arena + 255) & ~(size_t)255;
+  if (sns::fault_hit(sns::kFaultAlloc)) {
+    delete S;
+    return sns::record_injected("injected allocation failure", SNS_ENOMEM);
+  }
   cudaError_t e = cudaMalloc(&S->arena_base, arena);
   if (e != cudaSuccess) {
     delete S;

@@ -241,7 +241,7 @@ static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sam
       srht_sample_bitmap<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, nlist,
                                                 m2);
     }
-    SNS_CUDA_TRY(cudaGetLastError());
+    SNS_LAUNCH_CHECK();
     return SNS_OK;
   }
   int cap = 1;
@@ -254,7 +254,7 @@ static sns_status srht_sample(int64_t mp, int64_t d, uint64_t seed, int32_t* sam
     SNS_PROF(K_SRHT_SAMPLE, st);
   srht_sample_kernel<<<1, 1024, smem, st>>>(mp, d, stream_state(seed, kStreamSrhtSample), sample, need, nlist, m2);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -555,13 +555,13 @@ static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, 
                                                                 s_sign, need, Y, L.ldy);
     }
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   {
     SNS_PROF(K_SRHT_PASS2, st);
     srht_pass2_split<T><<<(unsigned)d, 256, 0, st>>>(Y, L.ldy, L.q, L.m1, L.m2, sample,
                                                     (T)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
@@ -598,7 +598,7 @@ sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out,
     SNS_PROF(K_MISC, st);
   widen_i32<<<64, 256, 0, st>>>(sample, d, out);
   }
-  SNS_CUDA_TRY(cudaGetLastError());
+  SNS_LAUNCH_CHECK();
   return SNS_OK;
 }
 
