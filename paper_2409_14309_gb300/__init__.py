@@ -7,6 +7,7 @@ the C calls, and allocates the caller-side workspace with torch.
 """
 import ctypes as C
 
+import numpy as np
 import torch
 
 from . import abi
@@ -204,23 +205,44 @@ class Context:
     def lstsq_batched(self, As, bs, ds, seeds, ws=None, stream=None, check=True):
         """Sketch-and-solve of many dense FP32 problems in one persistent launch.
         As, bs: lists of CUDA tensors; ds, seeds: ints per problem.  Returns
-        (list of x tensors, list of sns_info)."""
+        (list of x tensors, list of sns_info).  The problem and option tables
+        are filled column-wise (numpy arrays laid out as the C structs) and the
+        x vectors are views of one allocation, so marshalling stays a small
+        fraction of a batch."""
         k = len(As)
-        probs = (abi.sns_problem * k)()
-        ops = (abi.sns_opts * k)()
-        xs = [torch.empty(A.shape[1], dtype=torch.float64, device=self.device) for A in As]
-        xp = (C.c_void_p * k)()
-        for i in range(k):
-            probs[i] = dense_problem(As[i], bs[i])
-            ops[i] = opts(ds[i], "countsketch", seeds[i])
-            xp[i] = xs[i].data_ptr()
+        for A, b in zip(As, bs):
+            if not (A.is_cuda and b.is_cuda and A.dtype == torch.float32 and b.dtype == torch.float32
+                    and A.dim() == 2 and A.stride(1) == 1 and b.dim() == 1 and b.is_contiguous()):
+                raise TypeError("lstsq_batched: every A must be a row-major float32 CUDA matrix, b float32")
+        ns = [A.shape[1] for A in As]
+        probs = np.zeros(k, dtype=np.dtype(abi.sns_problem))
+        probs["m"] = [A.shape[0] for A in As]
+        probs["n"] = ns
+        probs["fmt"] = SNS_DENSE_F32
+        probs["A"] = [A.data_ptr() for A in As]
+        probs["lda"] = [A.stride(0) for A in As]
+        probs["b"] = [b.data_ptr() for b in bs]
+        ops = np.zeros(k, dtype=np.dtype(abi.sns_opts))
+        ops["sk"]["kind"] = abi.SNS_COUNTSKETCH
+        ops["sk"]["d"] = ds
+        ops["sk"]["seed"] = [int(sd) & (2**64 - 1) for sd in seeds]
+        ops["precondition"] = 1
+        xflat = torch.empty(sum(ns), dtype=torch.float64, device=self.device)
+        xs = list(torch.split(xflat, ns))
+        xp = np.empty(k, dtype=np.uint64)
+        xp[0] = xflat.data_ptr()
+        if k > 1:
+            xp[1:] = xflat.data_ptr() + 8 * np.cumsum(np.asarray(ns[:-1], dtype=np.uint64))
+        pp = probs.ctypes.data_as(C.POINTER(abi.sns_problem))
+        op = ops.ctypes.data_as(C.POINTER(abi.sns_opts))
+        xpp = xp.ctypes.data_as(C.POINTER(C.c_void_p))
         n = C.c_size_t()
-        _check(self._L.snsolve_lstsq_batched_workspace_size(probs, ops, k, C.byref(n)),
+        _check(self._L.snsolve_lstsq_batched_workspace_size(pp, op, k, C.byref(n)),
                "snsolve_lstsq_batched_workspace_size")
         if ws is None or ws.numel() < n.value:
             ws = _workspace(n.value, self.device)
         infos = (abi.sns_info * k)()
-        code = self._L.snsolve_lstsq_batched(self.h, probs, ops, k, xp, infos, _ptr(ws), ws.numel(), _stream(stream))
+        code = self._L.snsolve_lstsq_batched(self.h, pp, op, k, xpp, infos, _ptr(ws), ws.numel(), _stream(stream))
         if check and code not in (abi.SNS_OK, abi.SNS_ERANK):
             raise SnsError(code, "snsolve_lstsq_batched")
         return xs, list(infos)

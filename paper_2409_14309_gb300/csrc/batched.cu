@@ -1,19 +1,26 @@
 // Batched sketch-and-solve: many independent dense FP32 problems of uneven
 // sizes in one persistent launch (Sec. 1.2 steps 1-3 applied per problem).
 //
-// Each CTA repeatedly takes the next problem from a queue ordered by
-// decreasing estimated cost (longest-processing-time-first), then
-//  1. sketches [A | b] with its CountSketch, one column tile of ct columns at a
-//     time (b rides along in tile 0), into a shared-memory tile of d x (ct+1)
-//     FP32 accumulators with shared atomics; the tile is widened to FP64 and
-//     stored column-major in the problem's slice of the workspace;
-//  2. runs the FP64 Householder QR of [SA | Sb] and the back substitution on
-//     that slice (the one-CTA kernels of qr.cu), writing x^, the rank status and
-//     the sketched residual.
-// The upload of the task table, the reset of the queue counter and the kernel
-// are captured once into a CUDA graph per (workspace, batch size, launch
-// shape) and replayed.  The launch shape (threads per CTA, tile width, CTAs
-// per SM) comes from the tuner in tune.cpp.
+// Two persistent kernels, each taking problems from its own queue ordered by
+// decreasing cost (longest-processing-time-first):
+//  1. batched_sketch (HBM bound; queue ordered by bytes of [A | b]): a CTA
+//     sketches [A | b] with the problem's CountSketch, one column tile of ct
+//     columns at a time (b rides along in tile 0), into a shared-memory tile of
+//     d x (ct+1) FP32 accumulators with shared atomics; the tile is widened to
+//     FP64 and stored column-major in the problem's slice of the workspace;
+//  2. batched_qr (FP64 bound; queue ordered by QR flops): a CTA runs the FP64
+//     Householder QR of [SA | Sb] and the back substitution on that slice (the
+//     one-CTA routines of qr_cta.cuh), writing x^, the rank status and the
+//     sketched residual.
+// Apart, each kernel runs at the occupancy its own bound wants (measured: a
+// fused sketch-then-QR CTA left HBM idle during the QRs and the FP64 pipe idle
+// during the sketches; splitting the batch into groups whose QRs overlap the
+// next group's sketch ran slower: a group holds too few of the long QRs to
+// keep every SM's FP64 pipe busy).  The upload of the task table, the reset of
+// the queue counters and both kernels are captured once into a CUDA graph per
+// (workspace, batch size, launch shape) and replayed.  The launch shape
+// (threads per sketch CTA, tile width, sketch and QR CTAs per SM) comes from
+// the tuner in tune.cpp.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -47,12 +54,70 @@ struct BatchOut {
 };
 
 
-__global__ void batched_fused(const BatchTask* __restrict__ tasks, const int32_t* __restrict__ order, int ntasks,
-                              int* __restrict__ counter, BatchOut* __restrict__ outs, int ct) {
-  extern __shared__ __align__(16) float tile[];   // d_max x (ct + 1) floats (also reused as FP64 scratch)
-  __shared__ double red[32];
+// Rows r0 .. r0 + kBR - 1 of columns c0 .. c0 + w - 1 (and b when with_b) into
+// the tile.  LPR lanes per row and SLOTS column slots per lane (w <= LPR *
+// SLOTS): a load instruction covers 32 / LPR rows, so narrow problems keep all
+// lanes busy.  Lane u < kBR hashes row r0 + u once; the bucket and sign reach
+// the other lanes by shuffle.  Each shared atomic instruction carries one row
+// (the rows of a load group add in turn): two rows of one instruction may share
+// a bucket, and the order in which such same-address adds apply is not the same
+// for every column, so identical columns of A would no longer give bitwise
+// identical columns of SA (and an exactly rank-deficient A would escape the
+// rank check).
+constexpr int kBR = 16;
+template <int LPR, int SLOTS>
+SNS_D void batched_rows(const BatchTask& T, int64_t r0, int64_t m, int64_t c0, int w, bool with_b, uint64_t s0,
+                        uint64_t d, float* tile, int ldt) {
+  constexpr int RPI = 32 / LPR;                    // rows per load instruction
+  const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
+  uint32_t hk = 0;
+  float sk = 0.f, bv = 0.f;
+  {
+    const int64_t r = r0 + lane;
+    if (lane < kBR && r < m) {
+      const uint64_t key = splitmix_at(s0, (uint64_t)r);
+      hk = bucket_of(key, d);
+      sk = (key >> 63) ? -1.f : 1.f;
+      if (with_b) bv = __ldg(T.b + r);
+    }
+  }
+  float v[kBR / RPI][SLOTS];
+#pragma unroll
+  for (int g = 0; g < kBR / RPI; ++g) {
+    const int64_t r = r0 + g * RPI + sub;
+    const float* row = T.A + (r < m ? r : 0) * T.lda + c0;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+      const int j = cl + LPR * t;
+      v[g][t] = (r < m && j < w) ? __ldg(row + j) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < kBR / RPI; ++g) {
+    const int u = g * RPI + sub;
+    const uint32_t h = __shfl_sync(0xffffffffu, hk, u);
+    const float sg = __shfl_sync(0xffffffffu, sk, u);
+    float* trow = tile + (int64_t)h * ldt;
+#pragma unroll
+    for (int s2 = 0; s2 < RPI; ++s2) {
+      if (sub == s2) {
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+          const int j = cl + LPR * t;
+          if (r0 + u < m && j < w) atomicAdd(trow + j, sg * v[g][t]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (with_b && lane < kBR && r0 + lane < m) atomicAdd(tile + (int64_t)hk * ldt + w, sk * bv);
+}
+
+__global__ void batched_sketch(const BatchTask* __restrict__ tasks, const int32_t* __restrict__ order, int ntasks,
+                               int* __restrict__ counter, int ct) {
+  extern __shared__ __align__(16) float tile[];   // d_max x (ct + 1) floats
   __shared__ int s_idx;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, wid = tid >> 5, nw = blockDim.x >> 5;
   for (;;) {
     if (tid == 0) s_idx = atomicAdd(counter, 1);
     __syncthreads();
@@ -61,46 +126,21 @@ __global__ void batched_fused(const BatchTask* __restrict__ tasks, const int32_t
     if (idx >= ntasks) break;
     const int ti = order[idx];
     const BatchTask T = tasks[ti];
-    const int64_t m = T.m, n = T.n, d = T.d, q = n + 1;
+    const int64_t m = T.m, n = T.n, d = T.d;
     const uint64_t s0 = stream_state(T.seed, kStreamCountSketch);
     const int ldt = ct + 1;
     for (int64_t c0 = 0; c0 < n; c0 += ct) {
       const int w = (int)min((int64_t)ct, n - c0);
       const bool with_b = (c0 == 0);
-      const int wt = w + (with_b ? 1 : 0);            // tile width incl. b
+      const int wt = w + (with_b ? 1 : 0);            // tile width incl. b (column w of tile 0)
       for (int64_t e = tid; e < d * ldt; e += blockDim.x) tile[e] = 0.f;
       __syncthreads();
-      // kRowsInFlight rows per warp iteration: all loads first, then the
-      // shared-memory atomics (tile widths are at most 3 x 32 + 1 columns)
-      constexpr int kR = 8;
-      for (int64_t r0 = (int64_t)wid * kR; r0 < m; r0 += (int64_t)nw * kR) {
-        float v[kR][3];
-        uint32_t hh[kR];
-        float sg[kR];
-#pragma unroll
-        for (int u = 0; u < kR; ++u) {
-          const int64_t r = r0 + u;
-          const bool ok = r < m;
-          const uint64_t key = splitmix_at(s0, (uint64_t)(ok ? r : 0));
-          hh[u] = bucket_of(key, (uint64_t)d);
-          sg[u] = (key >> 63) ? -1.f : 1.f;
-          const float* row = T.A + (ok ? r : 0) * T.lda + c0;
-#pragma unroll
-          for (int q2 = 0; q2 < 3; ++q2) {
-            const int j = lane + 32 * q2;
-            v[u][q2] = (ok && j < wt) ? ((j < w) ? __ldg(row + j) : __ldg(T.b + r)) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kR; ++u) {
-          if (r0 + u >= m) break;
-          float* trow = tile + (int64_t)hh[u] * ldt;
-#pragma unroll
-          for (int q2 = 0; q2 < 3; ++q2) {
-            const int j = lane + 32 * q2;
-            if (j < wt) atomicAdd(trow + j, sg[u] * v[u][q2]);
-          }
-        }
+      for (int64_t r0 = (int64_t)wid * kBR; r0 < m; r0 += (int64_t)nw * kBR) {
+        if (w <= 8) batched_rows<8, 1>(T, r0, m, c0, w, with_b, s0, (uint64_t)d, tile, ldt);
+        else if (w <= 16) batched_rows<16, 1>(T, r0, m, c0, w, with_b, s0, (uint64_t)d, tile, ldt);
+        else if (w <= 32) batched_rows<32, 1>(T, r0, m, c0, w, with_b, s0, (uint64_t)d, tile, ldt);
+        else if (w <= 64) batched_rows<32, 2>(T, r0, m, c0, w, with_b, s0, (uint64_t)d, tile, ldt);
+        else batched_rows<32, 3>(T, r0, m, c0, w, with_b, s0, (uint64_t)d, tile, ldt);
       }
       __syncthreads();
       // widen to FP64, column-major: columns c0..c0+w-1, and b to column n
@@ -111,9 +151,26 @@ __global__ void batched_fused(const BatchTask* __restrict__ tasks, const int32_t
       }
       __syncthreads();
     }
-    double* scratch = reinterpret_cast<double*>(tile);   // d doubles (v), then reused for z
-    qr_factor_cta(T.W, d, q, scratch, red);
-    qr_finish_cta(T.W, d, q, T.x, &outs[ti].status, &outs[ti].sres, scratch, red);
+  }
+}
+
+__global__ void batched_qr(const BatchTask* __restrict__ tasks, const int32_t* __restrict__ order, int ntasks,
+                           int* __restrict__ counter, BatchOut* __restrict__ outs) {
+  extern __shared__ __align__(16) double qscratch[];   // d_max doubles (v), then 2 q for the back substitution
+  __shared__ double red[32];
+  __shared__ int s_idx;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_idx = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= ntasks) break;
+    const int ti = order[idx];
+    const BatchTask T = tasks[ti];
+    const int64_t d = T.d, q = (int64_t)T.n + 1;
+    qr_factor_cta(T.W, d, q, qscratch, red);
+    qr_finish_cta(T.W, d, q, T.x, &outs[ti].status, &outs[ti].sres, qscratch, red);
     __syncthreads();
   }
 }
@@ -127,8 +184,8 @@ static BatchLayout batch_layout(const sns_problem* probs, const sns_opts* opts, 
   BatchLayout L{};
   size_t off = 0;
   L.off_tasks = off; off += al((size_t)nprob * sizeof(BatchTask));
-  L.off_order = off; off += al((size_t)nprob * 4);
-  L.off_counter = off; off += al(16);
+  L.off_order = off; off += al((size_t)nprob * 8);     // sketch order, then QR order
+  L.off_counter = off; off += al(16);                  // the two queue counters
   L.off_outs = off; off += al((size_t)nprob * sizeof(BatchOut));
   L.off_w = off;
   for (int i = 0; i < nprob; ++i) off += al((size_t)opts[i].sk.d * (probs[i].n + 1) * 8);
@@ -152,12 +209,18 @@ size_t batch_ws_bytes(const sns_problem* probs, const sns_opts* opts, int nprob)
   return batch_layout(probs, opts, nprob).bytes;
 }
 
-// Tuned launch shape.
+// Tuned launch shape: sketch CTA threads, sketch tile width, sketch CTAs per SM,
+// QR CTAs per SM (kQrBatchThreads threads each).
 struct BatchShape {
-  int threads, ct, ctas_per_sm;
+  int threads, ct, ctas_per_sm, qr_per_sm;
 };
+constexpr int kQrBatchThreads = 128;
 std::vector<BatchShape> batch_candidates() {
-  return {{256, 64, 1}, {256, 32, 2}, {512, 64, 1}, {128, 32, 3}, {256, 16, 2}, {256, 8, 2}};
+  std::vector<BatchShape> c;
+  for (const BatchShape& s : {BatchShape{256, 64, 2, 0}, BatchShape{256, 32, 3, 0}, BatchShape{512, 64, 1, 0},
+                              BatchShape{256, 32, 4, 0}, BatchShape{128, 32, 6, 0}})
+    for (int qp : {4, 8}) c.push_back({s.threads, s.ct, s.ctas_per_sm, qp});
+  return c;
 }
 // implemented in tune.cpp
 bool tune_lookup(const char* key, int* a, int* b, int* c);
@@ -166,11 +229,11 @@ void tune_store(const char* key, int a, int b, int c);
 struct GraphKey {
   void* ws;
   const void* stage;
-  int nprob, threads, ct, grid;
-  size_t smem;
+  int nprob, threads, ct, grid, qgrid;
+  size_t smem, qsmem;
   bool operator<(const GraphKey& o) const {
-    return std::tie(ws, stage, nprob, threads, ct, grid, smem) <
-           std::tie(o.ws, o.stage, o.nprob, o.threads, o.ct, o.grid, o.smem);
+    return std::tie(ws, stage, nprob, threads, ct, grid, qgrid, smem, qsmem) <
+           std::tie(o.ws, o.stage, o.nprob, o.threads, o.ct, o.grid, o.qgrid, o.smem, o.qsmem);
   }
 };
 static std::mutex g_graph_mu;
@@ -178,15 +241,18 @@ static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 
 static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_t* w, const BatchLayout& L,
                             const void* host_tasks, size_t task_bytes, cudaStream_t st, bool use_graph) {
-  // sketch tile; reused as QR scratch (d doubles) and back-substitution scratch (2 q <= 2 d + 2 doubles)
-  const size_t smem = std::max((size_t)dmax * (S.ct + 1) * 4, (size_t)(2 * dmax + 2) * 8);
+  // sketch tile; QR scratch: d doubles (reflector), then 2 q <= 2 d + 2 doubles (back substitution)
+  const size_t smem = (size_t)dmax * (S.ct + 1) * 4;
+  const size_t qsmem = (size_t)(2 * dmax + 2) * 8;
   if (smem > 227 * 1024 || S.ct > 95) return SNS_EINVAL;   // the row loop covers 3 x 32 tile columns
-  SNS_CUDA_TRY(raise_smem_limit((const void*)batched_fused));
-  int occ = 0;
-  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_fused, S.threads, smem));
-  if (occ < 1) return SNS_EINVAL;
-  const int per = std::min(occ, S.ctas_per_sm);
-  const int grid = std::min(nprob, num_sms() * per);
+  SNS_CUDA_TRY(raise_smem_limit((const void*)batched_sketch));
+  SNS_CUDA_TRY(raise_smem_limit((const void*)batched_qr));
+  int occ = 0, qocc = 0;
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_sketch, S.threads, smem));
+  SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qocc, batched_qr, kQrBatchThreads, qsmem));
+  if (occ < 1 || qocc < 1) return SNS_EINVAL;
+  const int grid = std::min(nprob, num_sms() * std::min(occ, S.ctas_per_sm));
+  const int qgrid = std::min(nprob, num_sms() * std::min(qocc, std::max(1, S.qr_per_sm)));
   const BatchTask* tasks = reinterpret_cast<const BatchTask*>(w + L.off_tasks);
   const int32_t* order = reinterpret_cast<const int32_t*>(w + L.off_order);
   int* counter = reinterpret_cast<int*>(w + L.off_counter);
@@ -194,13 +260,15 @@ static sns_status run_shape(const BatchShape& S, int64_t dmax, int nprob, uint8_
   auto enqueue = [&](cudaStream_t s) -> sns_status {
     SNS_CUDA_TRY(cudaMemcpyAsync(w + L.off_tasks, host_tasks, task_bytes, cudaMemcpyHostToDevice, s));
     SNS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, s));
-    batched_fused<<<grid, S.threads, smem, s>>>(tasks, order, nprob, counter, outs, S.ct);
+    batched_sketch<<<grid, S.threads, smem, s>>>(tasks, order, nprob, counter, S.ct);
+    SNS_LAUNCH_CHECK();
+    batched_qr<<<qgrid, kQrBatchThreads, qsmem, s>>>(tasks, order + nprob, nprob, counter + 1, outs);
     SNS_LAUNCH_CHECK();
     return SNS_OK;
   };
   SNS_PROF(K_BATCH, st);
   if (!use_graph) return enqueue(st);
-  GraphKey key{w, host_tasks, nprob, S.threads, S.ct, grid, smem};
+  GraphKey key{w, host_tasks, nprob, S.threads, S.ct, grid, qgrid, smem, qsmem};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -248,7 +316,7 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
   // task table + LPT order (host), staged in pinned memory
   const size_t task_bytes = (size_t)nprob * sizeof(BatchTask);
   const size_t order_off = al(task_bytes);
-  const size_t stage_need = order_off + (size_t)nprob * 4;
+  const size_t stage_need = order_off + (size_t)nprob * 8;
   std::lock_guard<std::mutex> lk(g_stage_mu);
   if (g_stage_bytes < stage_need) {
     if (g_stage) cudaFreeHost(g_stage);
@@ -263,7 +331,7 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
   int32_t* order = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(g_stage) + order_off);
   size_t woff = L.off_w;
   int64_t dmax = 1;
-  std::vector<std::pair<double, int>> cost(nprob);
+  std::vector<std::pair<double, int>> cost(nprob), qcost(nprob);
   for (int i = 0; i < nprob; ++i) {
     const sns_problem& p = probs[i];
     const int64_t d = opts[i].sk.d, q = p.n + 1;
@@ -279,14 +347,18 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
     T[i].seed = opts[i].sk.seed;
     woff += al((size_t)d * q * 8);
     dmax = std::max(dmax, d);
-    // FP64 QR flops at ~1 TFLOP/s vs bytes of [A | b] at ~6 TB/s
-    const double c = (2.0 * d * q * q) / 1.0e12 + (double)p.m * q * 4.0 / 6.0e12;
-    cost[i] = {-c, i};
+    // sketch queue: bytes of [A | b]; QR queue: FP64 flops (ties broken by index)
+    cost[i] = {-(double)p.m * q, i};
+    qcost[i] = {-(2.0 * d * q * q), i};
   }
   std::sort(cost.begin(), cost.end());
-  for (int i = 0; i < nprob; ++i) order[i] = cost[i].second;
-  // the order array travels with the task table in one copy
-  const size_t copy_bytes = order_off + (size_t)nprob * 4;
+  std::sort(qcost.begin(), qcost.end());
+  for (int i = 0; i < nprob; ++i) {
+    order[i] = cost[i].second;
+    order[nprob + i] = qcost[i].second;
+  }
+  // the order arrays travel with the task table in one copy
+  const size_t copy_bytes = order_off + (size_t)nprob * 8;
   if (L.off_order != L.off_tasks + order_off) {
     // layouts differ only if alignment rules change; keep both copies consistent
     return SNS_EINVAL;
@@ -299,13 +371,13 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
     const int64_t n = probs[i].n;
     nsum[n <= 16 ? 0 : n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 3 : 4]++;
   }
-  snprintf(key, sizeof(key), "batched:sm%d:n%d:dmax%lld:mix%lld-%lld-%lld-%lld-%lld", num_sms(), nprob,
+  snprintf(key, sizeof(key), "batched:v2:sm%d:n%d:dmax%lld:mix%lld-%lld-%lld-%lld-%lld", num_sms(), nprob,
            (long long)dmax, (long long)nsum[0], (long long)nsum[1], (long long)nsum[2], (long long)nsum[3],
            (long long)nsum[4]);
-  BatchShape best{256, 64, 1};
+  BatchShape best{256, 64, 2, 4};
   int ta, tb, tc;
   if (tune_lookup(key, &ta, &tb, &tc)) {
-    best = {ta, tb, tc};
+    best = {ta, tb, tc % 16, tc / 16};                     // sketch and QR CTAs per SM packed as c + 16 qr
   } else {
     // time every candidate once on this batch (results are overwritten by the final run)
     float best_ms = 1e30f;
@@ -327,7 +399,7 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    tune_store(key, best.threads, best.ct, best.ctas_per_sm);
+    tune_store(key, best.threads, best.ct, best.ctas_per_sm + 16 * best.qr_per_sm);
   }
   s = run_shape(best, dmax, nprob, w, L, g_stage, copy_bytes, st, true);
   if (s != SNS_OK) return s;
