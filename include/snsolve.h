@@ -249,10 +249,13 @@ sns_status snsolve_lstsq_batched(sns_ctx* ctx, const sns_problem* probs, const s
  * most 32 GiB, allocated here once; nothing is allocated while serving) and
  * max_slots worker threads, each with its own stream.  A request's footprint
  * is the bytes of its inputs (A and b, resident on the device and owned by the
- * caller) plus its solver workspace.  Requests are admitted in arrival order
- * while a slot is free, the admitted footprints sum to at most the budget and
- * the arena has room; admitted requests run concurrently (their kernels
- * overlap on the device) and each starts as soon as a slot and memory free up.
+ * caller) plus its solver workspace.  A free slot takes the oldest pending
+ * request that fits (the admitted footprints sum to at most the budget and
+ * the arena has room), so a request waiting for memory does not block smaller
+ * ones behind it; the oldest request is passed over at most 2 x max_slots
+ * times, then nothing overtakes it until it is admitted.  Admitted requests
+ * run concurrently (their kernels overlap on the device) and each starts as
+ * soon as a slot and memory free up.
  * Each request is solved exactly as snsolve_lstsq would solve it.  Problem
  * pointers given to submit must stay valid until the request is polled done. */
 typedef struct sns_server sns_server;

@@ -5,9 +5,12 @@
 // serving) and starts one worker thread per slot, each with its own CUDA stream.
 // snsolve_submit queues a request.  A request's footprint is the bytes of its
 // resident inputs (A and b, owned by the caller) plus its solver workspace.
-// Requests are admitted in arrival order while a slot is free, the sum of the
-// admitted footprints stays within the HBM budget and the arena has room; a
-// request whose footprint alone exceeds the budget is refused (SNS_EBUDGET).
+// A free slot takes the oldest pending request that fits (the sum of the
+// admitted footprints stays within the HBM budget and the arena has room), so a
+// large request that must wait for memory does not block smaller ones behind
+// it; the oldest request can be passed over at most 2 x slots times, after
+// which nothing overtakes it until it is admitted (no starvation).  A request
+// whose footprint alone exceeds the budget is refused (SNS_EBUDGET).
 // Admitted requests run concurrently on their slots' streams, so their kernels
 // overlap on the device, and a newly arrived request starts as soon as a slot
 // and memory free up, without waiting for the others (continuous batching).
@@ -86,6 +89,7 @@ struct Req {
   sns_opts opts;
   double* x;
   size_t ws_bytes, footprint;
+  int bypassed = 0;     // times a younger request was admitted ahead of this one
 };
 struct Result {
   bool done = false;
@@ -130,17 +134,22 @@ static void worker_loop(sns_server* S, int slot) {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
         if (S->stop) return;
-        if (!S->pending.empty()) {
-          Req& h = S->pending.front();
-          // strict arrival order: the oldest request is admitted first
-          if (S->used + h.footprint <= S->budget && S->arena.alloc(h.ws_bytes, &off)) {
-            r = h;
-            S->pending.pop_front();
+        // first fit in arrival order, the oldest request passed over a bounded number of times
+        bool took = false;
+        const int bypass_limit = 2 * S->max_slots;
+        for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+          if (it != S->pending.begin() && S->pending.front().bypassed >= bypass_limit) break;
+          if (S->used + it->footprint <= S->budget && S->arena.alloc(it->ws_bytes, &off)) {
+            r = *it;
+            if (it != S->pending.begin()) S->pending.front().bypassed++;
+            S->pending.erase(it);
             S->used += r.footprint;
             S->running++;
+            took = true;
             break;
           }
         }
+        if (took) break;
         S->cv_work.wait(lk);
       }
     }

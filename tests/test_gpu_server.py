@@ -131,3 +131,38 @@ def test_poll_timeout_and_eagain_and_unknown_id():
     code, _ = srv.poll(rid_small, timeout_us=0)
     assert code == 1            # collected already: unknown id
     srv.close()
+
+
+def test_small_request_overtakes_one_waiting_for_memory():
+    """Two slots, budget for one large request plus small ones: while the first
+    large request runs, the second must wait for memory, and a small request
+    submitted after it is admitted ahead of it and finishes first."""
+    import paper_2409_14309_gb300 as sns
+    c = ctx()
+    m, n = 1 << 21, 256
+    A1 = torch.randn(m, n, device="cuda")
+    b1 = torch.randn(m, device="cuda")
+    A2 = torch.randn(m, n, device="cuda")
+    b2 = torch.randn(m, device="cuda")
+    As = torch.randn(5000, 16, device="cuda")
+    bs = torch.randn(5000, device="cuda")
+    prob = sns.dense_problem(A1, b1)
+    op = sns.opts(1024, "countsketch", 1, tol=1e-12, max_iter=200)
+    foot = m * n * 4 + m * 4 + ((c.lstsq_workspace(prob, op) + 255) // 256) * 256
+    srv = sns.Server(c, hbm_budget_bytes=foot + foot // 4, max_slots=2)
+    rid1, _ = srv.submit(A1, b1, 1024, seed=1, tol=1e-12, max_iter=200)
+    rid2, _ = srv.submit(A2, b2, 1024, seed=2, tol=1e-12, max_iter=200)
+    rids, _ = srv.submit(As, bs, 64, seed=3)
+    code, info = srv.poll(rids, timeout_us=60_000_000)
+    assert code == 0 and info.status == 0
+    # the small request ran beside the first large one: that one has not finished
+    # yet (in strict arrival order the small one would have waited for the second
+    # large one's admission, which follows the first one's completion)
+    code1, _ = srv.poll(rid1, timeout_us=0)
+    assert code1 == 5               # SNS_EAGAIN
+    code2, _ = srv.poll(rid2, timeout_us=0)
+    assert code2 == 5
+    for rid in (rid1, rid2):
+        code, info = srv.poll(rid, timeout_us=120_000_000)
+        assert code == 0
+    srv.close()
