@@ -356,7 +356,7 @@ def main():
                     help="served workload: arrival rates as multiples of the one-slot capacity")
     ap.add_argument("--sweep-requests", type=int, default=4000,
                     help="served workload: requests at the rates below the highest one")
-    ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr"],
+    ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr", "batched"],
                     help="profile-case: which small case to run")
     ap.add_argument("--latency-solves", type=int, default=200,
                     help="solves of the separate latency pass (p50/p99)")
@@ -997,7 +997,9 @@ def run_profile_case(args):
     on the device.  solve: 2^18 x 256 FP32 (kappa 1e6, noise 1e-4), CountSketch
     d = 1024, two solves to eta <= 1e-6.  countsketch / srht / gaussian: three
     sketches of a 2^18 x 256 N(0,1) matrix (2^19 rows for countsketch), d = 1024.
-    csr: 2^19 x 512 at 1 % plus 64 dense rows x100, d = 2048, two solves to 1e-8."""
+    csr: 2^19 x 512 at 1 % plus 64 dense rows x100, d = 2048, two solves to 1e-8.
+    batched: 256 problems of the batched workload's shape mix (N(0,1) entries),
+    three batched calls (the first tunes the launch shape)."""
     import torch
     import paper_2409_14309_gb300 as sns
     dev = torch.device("cuda", 0)
@@ -1020,6 +1022,16 @@ def run_profile_case(args):
             x, info = ctx.lstsq(A, b, 1024, seed=1, tol=1e-6)
         torch.cuda.synchronize()
         print(json.dumps({"case": "solve", "status": info.status, "passes": info.iters, "eta": info.eta}))
+    elif args.case == "batched":
+        from synth import batched_shapes
+        shapes = batched_shapes(256, seed=1004)
+        As = [torch.randn(m, n, generator=gen, device=dev) for (m, n, _) in shapes]
+        bs = [torch.randn(m, generator=gen, device=dev) for (m, _, _) in shapes]
+        for _ in range(3):
+            xs, infos = ctx.lstsq_batched(As, bs, [d for (_, _, d) in shapes], list(range(len(shapes))))
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "batched", "problems": len(shapes), "ok": sum(i.status == 0 for i in infos),
+                          "input_bytes": sum(m * (n + 1) * 4 for (m, n, _) in shapes)}))
     elif args.case == "csr":
         rowptr, col, val, b, nnz = _csr_dense_rows(1 << 19, 512, 0.01, 64, gen, dev)
         for _ in range(2):

@@ -136,11 +136,12 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // per (64-row chunk, 256-column tile), in the canonical K-major layout without
 // swizzle (8 x 16-byte core matrices: element (column nn, row k) at
 // ((nn/8)*8 + k/8)*128 + (nn%8)*16 + (k%8)*2), beside each chunk's 64
-// BF16-rounded b values as FP32.  gauss_umma then never touches FP32 A: per
-// chunk it takes the tile with one bulk copy into a 3-stage shared-memory ring
-// (issued two chunks ahead), generates the chunk's 128 x 64 tile of G, and one
-// thread issues 4 MMAs of 128 x N x 16 (K = 16 steps).  Every A tile is read
-// by the d / 128 row-tile CTAs of its K range, mostly from L2.
+// BF16-rounded b values as FP32.  gauss_umma then never touches FP32 A.  It is
+// warp-specialised: 16 warps generate the chunk's 128 x 64 tile of G into a
+// 2-stage ring, and one warp takes each chunk's A tile with one bulk copy into
+// a 5-stage ring (issued four chunks ahead) and issues 4 MMAs of 128 x N x 16
+// (K = 16 steps) per chunk; the roles meet only at mbarriers.  Every A tile is
+// read by the d / 128 row-tile CTAs of its K range, mostly from L2.
 //
 // G: one hash per (row, 8 consecutive k) gives 8 lookups in a per-bank copy of
 // the FP32 table and one 16-byte store; the b column is accumulated on the CUDA
