@@ -149,6 +149,10 @@ typedef struct {
   double eta;              /* final eta(x) (tol > 0), else 0 */
   double resid_norm;       /* ||b - A x|| (tol > 0), else 0 */
   double sketch_resid;     /* ||SA x^ - Sb|| from the QR: |R_aug[n, n]| */
+  float ms_sketch;         /* snsolve_lstsq: device time of the sketch (CUDA events on the */
+  float ms_qr;             /*   call's stream), of the QR + back-solve, and of everything */
+  float ms_iter;           /*   after it (refinement); 0 where a phase did not run or in   */
+  int32_t reserved2;       /*   snsolve_lstsq_batched */
 } sns_info;
 
 typedef struct sns_ctx sns_ctx;

@@ -38,7 +38,8 @@ class sns_opts(C.Structure):
 
 class sns_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("outer", C.c_int32), ("reserved", C.c_int32),
-                ("eta", C.c_double), ("resid_norm", C.c_double), ("sketch_resid", C.c_double)]
+                ("eta", C.c_double), ("resid_norm", C.c_double), ("sketch_resid", C.c_double),
+                ("ms_sketch", C.c_float), ("ms_qr", C.c_float), ("ms_iter", C.c_float), ("reserved2", C.c_int32)]
 
 
 P = C.POINTER

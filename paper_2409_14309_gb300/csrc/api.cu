@@ -457,6 +457,43 @@ static void info_fill(sns_info* info, int status, int iters, int outer, double e
   info->eta = eta;
   info->resid_norm = rn;
   info->sketch_resid = sres;
+  info->ms_sketch = info->ms_qr = info->ms_iter = 0.f;
+  info->reserved2 = 0;
+}
+
+// Per-thread events bracketing a solve's phases on its stream: [0] start,
+// [1] sketch done, [2] QR + back-solve done, [3] end.
+struct PhaseEvents {
+  cudaEvent_t e[4] = {};
+  bool ok = false;
+  int device = -1;
+  ~PhaseEvents() {
+    for (cudaEvent_t v : e)
+      if (v) cudaEventDestroy(v);
+  }
+};
+static thread_local PhaseEvents t_phase;
+static PhaseEvents* phase_events() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (!t_phase.ok || t_phase.device != dev) {
+    t_phase.ok = true;
+    for (cudaEvent_t& v : t_phase.e)
+      if (cudaEventCreate(&v) != cudaSuccess) t_phase.ok = false;
+    t_phase.device = dev;
+  }
+  return t_phase.ok ? &t_phase : nullptr;
+}
+// Records the end event and fills the phase times of `info` (after info_fill).
+static void phase_times(PhaseEvents* pe, cudaStream_t st, sns_info* info) {
+  if (!pe || !info) return;
+  if (cudaEventRecord(pe->e[3], st) != cudaSuccess || cudaEventSynchronize(pe->e[3]) != cudaSuccess) return;
+  float t[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < 3; ++k)
+    if (cudaEventElapsedTime(&t[k], pe->e[k], pe->e[k + 1]) != cudaSuccess) t[k] = 0.f;
+  info->ms_sketch = t[0];
+  info->ms_qr = t[1];
+  info->ms_iter = t[2];
 }
 
 sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* opts, double* x, sns_info* info,
@@ -478,6 +515,8 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   double* hp = thread_pinned();
   if (!hp) return SNS_ENOMEM;
   const bool precond = opts->precondition != 0 || opts->tol <= 0;
+  PhaseEvents* pe = phase_events();
+  if (pe) SNS_CUDA_TRY(cudaEventRecord(pe->e[0], st));
 
   double sres = 0.0;
   if (precond) {
@@ -486,6 +525,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     void* Sb = w + L.off_saug + (size_t)n * (f64 ? 8 : 4);
     s = run_sketch(prob, &opts->sk, SA, q, Sb, q, w + L.off_sk, L.sk_bytes, st);
     if (s != SNS_OK) return s;
+    if (pe) SNS_CUDA_TRY(cudaEventRecord(pe->e[1], st));
     // step 3: FP64 Householder QR of [SA | Sb] and back substitution
     s = qr_load_colmajor(SA, q, f64, d, q, W, st);
     if (s != SNS_OK) return s;
@@ -493,6 +533,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     const bool coop = q >= 32;
     s = coop ? qr_solve_coop(o, w + L.off_qr, st) : qr_solve_one(o, st);
     if (s != SNS_OK) return s;
+    if (pe) SNS_CUDA_TRY(cudaEventRecord(pe->e[2], st));
     if (opts->tol > 0) {
       s = diag_range(W, d, n, reinterpret_cast<double*>(w + L.off_dev + 16), st);
       if (s != SNS_OK) return s;
@@ -514,17 +555,24 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     sres = hp[17];
     if (qerr || serr) {
       info_fill(info, SNS_ETIMEOUT, 0, 0, 0.0, 0.0, 0.0);
+      phase_times(pe, st, info);
       return SNS_ETIMEOUT;
     }
     if (qs != SNS_OK) {
       info_fill(info, qs, 0, 0, 0.0, 0.0, sres);
+      phase_times(pe, st, info);
       return (sns_status)qs;
     }
     if (opts->tol <= 0) {
       info_fill(info, SNS_OK, 0, 0, 0.0, 0.0, sres);
+      phase_times(pe, st, info);
       return SNS_OK;
     }
   } else {
+    if (pe) {
+      SNS_CUDA_TRY(cudaEventRecord(pe->e[1], st));
+      SNS_CUDA_TRY(cudaEventRecord(pe->e[2], st));
+    }
     SNS_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * 8, st));
   }
 
@@ -576,11 +624,13 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
       // residual was not positive): no further progress is possible
       if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
       info_fill(info, SNS_ENOTCONV, passes, outer, eta, rn, sres);
+      phase_times(pe, st, info);
       return SNS_ENOTCONV;
     }
     if (passes >= max_iter) {
       if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
       info_fill(info, SNS_ENOTCONV, passes, outer, eta, rn, sres);
+      phase_times(pe, st, info);
       return SNS_ENOTCONV;
     }
     // inner solver: preconditioned CG on A^T A dx = g (M^-1 = R^-1 R^-T); the
@@ -613,6 +663,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   }
   if (!rinv_joined) SNS_CUDA_TRY(cudaStreamWaitEvent(st, side.ev_out, 0));
   info_fill(info, SNS_OK, passes, outer, eta, rn, sres);
+  phase_times(pe, st, info);
   return SNS_OK;
 }
 

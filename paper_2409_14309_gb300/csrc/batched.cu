@@ -419,6 +419,8 @@ sns_status lstsq_batched(const sns_problem* probs, const sns_opts* opts, int npr
       infos[i].eta = 0.0;
       infos[i].resid_norm = 0.0;
       infos[i].sketch_resid = outs[i].sres;
+      infos[i].ms_sketch = infos[i].ms_qr = infos[i].ms_iter = 0.f;
+      infos[i].reserved2 = 0;
     }
   }
   return worst;

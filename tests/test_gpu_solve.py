@@ -171,3 +171,23 @@ def test_max_iter_reports_not_converged():
     A, b, _ = ill_conditioned_problem(20000, 32, seed=13, kappa=1e6, noise=1e-4)
     x, info = c.lstsq(dev(A), dev(b), 128, seed=1, tol=1e-14, max_iter=2, inner=1)
     assert info.status == 4   # SNS_ENOTCONV
+
+
+def test_phase_times_reported():
+    """sns_info carries the device time of the sketch, the QR + back-solve and the
+    refinement (CUDA events on the call's stream)."""
+    import time
+    c = ctx()
+    A, b, _ = ill_conditioned_problem(65536, 64, seed=77, kappa=1e4, noise=1e-3)
+    Ad, bd = dev(A).float(), dev(b).float()
+    x, info = c.lstsq(Ad, bd, 256, seed=3)
+    assert info.status == 0
+    assert info.ms_sketch > 0 and info.ms_qr > 0 and info.ms_iter >= 0
+    assert info.ms_iter < 0.5                       # sketch-and-solve: no refinement
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, info = c.lstsq(Ad, bd, 256, seed=3, tol=1e-10)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    assert info.status == 0 and info.iters > 0
+    assert info.ms_sketch > 0 and info.ms_qr > 0 and info.ms_iter > 0
+    assert info.ms_sketch + info.ms_qr + info.ms_iter <= wall_ms * 1.05 + 0.1
