@@ -200,7 +200,7 @@ def algorithmic(name, m, n, d):
         return "hbm", m * n * 4.0
     if name in ("resid_pass",):
         return "hbm", m * (n + 1) * 4.0
-    if name in ("cs_gather_dense", "cs_stream_dense", "cs_sort_blocks"):
+    if name in ("cs_gather_dense", "cs_stream_dense", "cs_sort_blocks", "cs_apply"):
         return "hbm", m * (n + 1) * 4.0
     if name in ("qr_house",):
         q = n + 1
@@ -500,9 +500,16 @@ def main():
                 "algorithmic_flops_per_launch": amount, "avg_launch_ms": avg_s * 1e3,
                 "launches_per_step": cnt / args.steps}
 
-    sk_names = [k for k in ("cs_sort_blocks", "cs_gather_dense", "cs_stream_dense") if k in prof]
-    sk_ms = sum(prof[k][0] for k in sk_names)
-    sk_n = max([prof[k][1] for k in ("cs_gather_dense", "cs_stream_dense") if k in prof] or [0])
+    # the single-launch plan and its dependent gather are timed as one span
+    # ("cs_apply": one event pair, so no event separates the pair); other
+    # variants as the sum of their kernels
+    if "cs_apply" in prof:
+        sk_names = ["cs_apply"]
+        sk_ms, sk_n = prof["cs_apply"]
+    else:
+        sk_names = [k for k in ("cs_sort_blocks", "cs_gather_dense", "cs_stream_dense") if k in prof]
+        sk_ms = sum(prof[k][0] for k in sk_names)
+        sk_n = max([prof[k][1] for k in ("cs_gather_dense", "cs_stream_dense") if k in prof] or [0])
     sketch = None
     if sk_n:
         gbs = M * (N + 1) * 4.0 / (sk_ms / sk_n / 1e3) / 1e9

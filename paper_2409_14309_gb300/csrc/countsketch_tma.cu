@@ -942,6 +942,7 @@ sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsL
   if ((int64_t)occ * num_sms() < nblk_plan || nblk_plan > L.nblk) return SNS_OK;
   *used = true;
   SNS_CUDA_TRY(cudaMemsetAsync(ws + L.off_err, 0, 16, st));
+  ProfSpan span(K_CS_APPLY, st);                   // plan + gather, timed as one
   int64_t m = a.m, nblk = nblk_plan, nticket = L.nticket, n = a.n, ldsa_ = ldsa, sbs_ = sbs;
   int rpb = (int)rows_per_blk;
   uint32_t dd = (uint32_t)d;

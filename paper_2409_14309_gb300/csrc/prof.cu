@@ -15,7 +15,7 @@ static const char* kNames[K_COUNT] = {
     "cs_sort_blocks", "cs_gather_dense", "cs_stream_dense", "cs_gather_csr", "srht_sample", "srht_pass1",
     "srht_pass2",     "gauss_apply",     "qr_load",         "qr_house",      "rinv",        "resid_pass",
     "normal_pass",    "pcg_matvec",      "pcg_apply",       "eta",           "batched",     "misc",
-    "saa_form_y"};
+    "saa_form_y",     "cs_apply"};
 
 const char* kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
 
@@ -41,9 +41,11 @@ static cudaEvent_t get_event() {
   return e;
 }
 
+static thread_local int t_span_depth = 0;
+
 ProfScope::ProfScope(int id, cudaStream_t st) : id_(id), st_(st), slot_(-1) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (g_on.load(std::memory_order_relaxed)) {
+  if (g_on.load(std::memory_order_relaxed) && t_span_depth == 0) {
     std::lock_guard<std::mutex> lk(g_mu);
     Rec r{id, get_event(), get_event()};
     cudaEventRecord(r.a, st);
@@ -53,6 +55,25 @@ ProfScope::ProfScope(int id, cudaStream_t st) : id_(id), st_(st), slot_(-1) {
 }
 
 ProfScope::~ProfScope() {
+  if (slot_ >= 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (slot_ < (int)g_recs.size()) cudaEventRecord(g_recs[slot_].b, st_);
+  }
+}
+
+ProfSpan::ProfSpan(int id, cudaStream_t st) : st_(st), slot_(-1) {
+  if (g_on.load(std::memory_order_relaxed) && t_span_depth == 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Rec r{id, get_event(), get_event()};
+    cudaEventRecord(r.a, st);
+    g_recs.push_back(r);
+    slot_ = (int)g_recs.size() - 1;
+  }
+  ++t_span_depth;
+}
+
+ProfSpan::~ProfSpan() {
+  --t_span_depth;
   if (slot_ >= 0) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (slot_ < (int)g_recs.size()) cudaEventRecord(g_recs[slot_].b, st_);
