@@ -308,8 +308,8 @@ gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict_
 constexpr int kUGenWarps = 16;   // 32 would exceed 1024 threads with the MMA warp
 __global__ void __launch_bounds__(32 * (kUGenWarps + 1), 1)
 gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t n, int64_t d, uint64_t s0,
-           const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ SA, int64_t ldsa,
-           float* __restrict__ Sb, int64_t sbs, int* __restrict__ err, int flush_every) {
+           const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ part,
+           float* __restrict__ partb, int* __restrict__ err, int flush_every) {
   extern __shared__ __align__(1024) uint8_t usm[];
   // G stages (kUStageA each), then A stages (A tile kUStageB, b values kUStageBb)
   auto stA = [&](int s) { return usm + (size_t)s * kUStageA; };
@@ -367,16 +367,19 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   // D (columns 0..255) -> S (columns kUSum..), by the generator warps: warp w
   // reads TMEM lanes of quadrant w mod 4 (the hardware rule) and the 16-column
   // blocks w / 4, w / 4 + 4, ...; the final pass adds D and S, scales and
-  // reduces into SA.  nflush counts the flushes done (uniform over the warps).
+  // stores the CTA's partial tile into its K split's slice of `part` (row
+  // stride n), and each generator thread its b-column partial into `partb`
+  // (slice (K split, thread group)); gauss_reduce adds the slices in a fixed
+  // order.  nflush counts the flushes done (uniform over the warps).
   int nflush = 0;
   float sb_hi = 0.f, sb_lo = 0.f;                              // b column (generator threads)
   auto tmem_flush = [&](bool final_pass) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int quarter = warp & 3, part = warp >> 2;
+    const int quarter = warp & 3, cblk = warp >> 2;
     const int rloc = quarter * 32 + lane;
     const int64_t row = r_base + rloc;
     const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
-    for (int c0 = part * 16; c0 < npad; c0 += 16 * (kUGenWarps / 4)) {
+    for (int c0 = cblk * 16; c0 < npad; c0 += 16 * (kUGenWarps / 4)) {
       float v[16];
       tmem_ld16(taddr + lanes + (uint32_t)c0, v);
       if (nflush > 0) {
@@ -390,23 +393,23 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
         continue;
       }
       if (row < d) {
-        float* dst = SA + row * ldsa + col0 + c0;
+        float* dst = part + ((int64_t)blockIdx.y * d + row) * n + col0 + c0;
         if (c0 + 16 <= ncols && ((uintptr_t)dst & 15) == 0) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j), "f"(v[j] * scale),
-                         "f"(v[j + 1] * scale), "f"(v[j + 2] * scale), "f"(v[j + 3] * scale)
-                         : "memory");
+            *reinterpret_cast<float4*>(dst + j) =
+                make_float4(v[j] * scale, v[j + 1] * scale, v[j + 2] * scale, v[j + 3] * scale);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c0 + j < ncols) atomicAdd(dst + j, v[j] * scale);
+            if (c0 + j < ncols) dst[j] = v[j] * scale;
         }
       }
     }
     if (final_pass) {
+      constexpr int kGroups = 32 * kUGenWarps / kUG;             // generator threads per row of G
       if (with_b && r_base + (tid & (kUG - 1)) < d)
-        atomicAdd(Sb + (r_base + (tid & (kUG - 1))) * sbs, (sb_hi + sb_lo) * scale);
+        partb[((int64_t)blockIdx.y * kGroups + (tid >> 7)) * d + r_base + (tid & (kUG - 1))] = (sb_hi + sb_lo) * scale;
     } else {
       ++nflush;
     }
@@ -517,7 +520,7 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
       // the converted A and b are zero there).
       {
         const float* bc = stb(s);
-        float part = 0.f;
+        float bpart = 0.f;
 #pragma unroll
         for (int e = 0; e < kPer; ++e) {
           const int q = (tid >> 7) + e * (kGenThreads / kUG);
@@ -539,20 +542,20 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
           if (with_b) {
             const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * q);
             const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * q + 4);
-            part = fmaf(v[0], b0.x, part);
-            part = fmaf(v[1], b0.y, part);
-            part = fmaf(v[2], b0.z, part);
-            part = fmaf(v[3], b0.w, part);
-            part = fmaf(v[4], b1.x, part);
-            part = fmaf(v[5], b1.y, part);
-            part = fmaf(v[6], b1.z, part);
-            part = fmaf(v[7], b1.w, part);
+            bpart = fmaf(v[0], b0.x, bpart);
+            bpart = fmaf(v[1], b0.y, bpart);
+            bpart = fmaf(v[2], b0.z, bpart);
+            bpart = fmaf(v[3], b0.w, bpart);
+            bpart = fmaf(v[4], b1.x, bpart);
+            bpart = fmaf(v[5], b1.y, bpart);
+            bpart = fmaf(v[6], b1.z, bpart);
+            bpart = fmaf(v[7], b1.w, bpart);
           }
         }
         if (with_b) {
-          const float t = sb_hi + part;                            // TwoSum (Knuth)
+          const float t = sb_hi + bpart;                            // TwoSum (Knuth)
           const float bb = t - sb_hi;
-          sb_lo += (sb_hi - (t - bb)) + (part - bb);
+          sb_lo += (sb_hi - (t - bb)) + (bpart - bb);
           sb_hi = t;
         }
       }
@@ -614,10 +617,43 @@ static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
   return g;
 }
 constexpr size_t kGaussTilesOffset = 8192 + 256;
-size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t) {
-  // the BF16 table (uploaded per call), the error word, the converted [A | b] tiles
+constexpr int kGaussGroups = 32 * kUGenWarps / kUG;     // b-column partials per (K split, row)
+// Workspace: the BF16 table (uploaded per call), the error word, the converted
+// [A | b] tiles, then the per-K-split partial tiles of SA (d x n each) and of
+// Sb (kGaussGroups x d each), sized for at most kSizingSms K splits per tile.
+constexpr int64_t kSizingSms = 256;
+static int64_t gauss_ksplit_bound(int64_t m, int64_t n, int64_t d) {
+  const int64_t tiles = ((d + kUG - 1) / kUG) * ((n + kUN - 1) / kUN);
+  return std::max<int64_t>(1, std::min<int64_t>(kSizingSms / std::max<int64_t>(1, tiles), (m + kUKT - 1) / kUKT));
+}
+static size_t gauss_part_offset(int64_t m, int64_t n) {
   const int64_t nchunks = (m + kUKT - 1) / kUKT, ntiles = (n + kUN - 1) / kUN;
   return kGaussTilesOffset + (size_t)nchunks * ntiles * kUTileBytes;
+}
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
+  const size_t ks = (size_t)gauss_ksplit_bound(m, n, d);
+  return gauss_part_offset(m, n) + ks * (size_t)d * n * 4 + ks * kGaussGroups * (size_t)d * 4;
+}
+
+// SA and Sb as the sums of the K splits' partials, in split order (the result
+// does not depend on the order in which the CTAs finished).
+__global__ void __launch_bounds__(256)
+gauss_reduce(const float* __restrict__ part, const float* __restrict__ partb, int64_t ksplit, int64_t d, int64_t n,
+             float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
+  const int64_t total = d * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total + d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < total) {
+      float acc = 0.f;
+      for (int64_t y = 0; y < ksplit; ++y) acc += __ldg(part + y * total + e);
+      SA[(e / n) * ldsa + e % n] = acc;
+    } else {
+      const int64_t row = e - total;
+      float acc = 0.f;
+      for (int64_t y = 0; y < ksplit * kGaussGroups; ++y) acc += __ldg(partb + y * d + row);
+      Sb[row * sbs] = acc;
+    }
+  }
 }
 
 sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
@@ -625,21 +661,23 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   if (!ws || ws_bytes < gauss_ws_bytes(a.m, a.n, d)) return SNS_ENOMEM;
   uint16_t* dtab = static_cast<uint16_t*>(ws);
   SNS_CUDA_TRY(cudaMemcpyAsync(dtab, table_host(), kGaussLevels * 2, cudaMemcpyHostToDevice, st));
-  if (ldsa == a.n) {
-    SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
-  } else {
-    SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
-  }
-  if (sbs == 1) {
-    SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
-  } else {
-    SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
-  }
   // SNSOLVE_GAUSS=simt selects the CUDA-core kernel
   static int use_simt = -1;
   if (use_simt < 0) {
     const char* e = getenv("SNSOLVE_GAUSS");
     use_simt = (e && e[0] == 's') ? 1 : 0;
+  }
+  if (use_simt) {                                      // it adds into SA and Sb
+    if (ldsa == a.n) {
+      SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
+    } else {
+      SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
+    }
+    if (sbs == 1) {
+      SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
+    } else {
+      SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
+    }
   }
   int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + gauss_err_offset());
   SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
@@ -655,13 +693,21 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
     }
     SNS_LAUNCH_CHECK();
     SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
+    if (gg.ksplit > gauss_ksplit_bound(a.m, a.n, d)) return SNS_EINVAL;   // more SMs than the sizing bound
     dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
     const float scale = (float)(1.0 / std::sqrt((double)d));
+    float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + gauss_part_offset(a.m, a.n));
+    float* partb = part + (size_t)gg.ksplit * d * a.n;
     {
       SNS_PROF(K_GAUSS, st);
       gauss_umma<<<grid, 32 * (kUGenWarps + 1), gauss_umma_smem(), st>>>(tiles, gg.ntiles, a.m, a.n, d, s0, dtab,
-                                                                         gg.kchunk, scale, SA, ldsa, Sb, sbs, err,
+                                                                         gg.kchunk, scale, part, partb, err,
                                                                          kUFlush);
+    }
+    SNS_LAUNCH_CHECK();
+    {
+      SNS_PROF(K_GAUSS, st);
+      gauss_reduce<<<num_sms() * 4, 256, 0, st>>>(part, partb, gg.ksplit, d, a.n, SA, ldsa, Sb, sbs);
     }
     SNS_LAUNCH_CHECK();
     return SNS_OK;

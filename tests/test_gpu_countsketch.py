@@ -230,6 +230,25 @@ def test_gaussian_sketch_tensor_core(m, n, d):
     assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-6
 
 
+def test_gaussian_sketch_bitwise_reproducible():
+    """The tensor-core Gaussian sketch adds its K splits' partial tiles in a
+    fixed order: repeated sketches, including ones that overlap on two streams
+    (so the CTAs finish in a different order), are equal bit for bit."""
+    c = ctx()
+    rng = np.random.default_rng(91)
+    A = dev(rng.standard_normal((120000, 160)).astype(np.float32))
+    b = dev(rng.standard_normal(120000).astype(np.float32))
+    SA1, Sb1 = c.sketch(A, b, 640, kind="gaussian", seed=5)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for s in (s1, s2):
+        with torch.cuda.stream(s):
+            outs.append(c.sketch(A, b, 640, kind="gaussian", seed=5, stream=s))
+    torch.cuda.synchronize()
+    for SA, Sb in outs:
+        assert torch.equal(SA, SA1) and torch.equal(Sb, Sb1)
+
+
 def test_gaussian_simt_variant_in_subprocess():
     """The CUDA-core Gaussian kernel (SNSOLVE_GAUSS=simt) follows the same
     definition of G as the tensor-core kernel."""
