@@ -912,7 +912,10 @@ def run_served(args):
 # ------------------------------------------------------------------ sketch kinds
 def run_sketches(args):
     """snsolve_sketch alone on the 1048576 x 256 workload for every sketch kind:
-    HBM GB/s (A and b read once) and, for the Gaussian GEMM, tensor TFLOP/s."""
+    HBM GB/s (A and b read once) and, for the Gaussian GEMM, tensor TFLOP/s.
+    Outside the timed loops, the quality of each sketch as a preconditioner:
+    kappa(A R^-1) with R from a QR of the sketch (FP64, from the eigenvalues of
+    R^-T (A^T A) R^-1; torch's linear algebra as a measuring tool)."""
     import torch
     import paper_2409_14309_gb300 as sns
     from paper_2409_14309_gb300 import abi
@@ -923,6 +926,19 @@ def run_sketches(args):
     A = torch.from_numpy(A_h).to(dev)
     b = torch.from_numpy(b_h).to(dev)
     hbm_peak, bf16_peak, kind_peak = peaks()
+    A64 = A.double()
+    gram = A64.T @ A64                                   # A^T A in FP64 (n x n)
+    del A64
+    ev = torch.linalg.eigvalsh(gram)
+    kappa_A = float(torch.sqrt(ev[-1] / ev[0]))
+
+    def kappa_precond(SA):
+        R = torch.linalg.qr(SA.double(), mode="r")[1]
+        t1 = torch.linalg.solve_triangular(R.T, gram, upper=False)          # R^-T G
+        Mx = torch.linalg.solve_triangular(R.T, t1.T.contiguous(), upper=False)   # R^-T G R^-1
+        e = torch.linalg.eigvalsh(0.5 * (Mx + Mx.T))
+        return float(torch.sqrt(e[-1] / e[0]))
+
     out = {}
     for name, kind, variant in [("countsketch_sorted", "countsketch", "sorted"),
                                 ("countsketch_stream", "countsketch", "stream"),
@@ -952,8 +968,11 @@ def run_sketches(args):
             fl = 2.0 * D * M * (N + 1)
             r["TFLOPs"] = fl / (ms / 1e3) / 1e12
             r["frac_bf16"] = r["TFLOPs"] / bf16_peak
+        SA_k, _ = ctx.sketch_problem(prob, sk, torch.float32, ws=ws)
+        r["kappa_A_Rinv"] = kappa_precond(SA_k)
         out[name] = r
     print(json.dumps({"metric": METRIC, "workload": "sketches", "config": {"m": M, "n": N, "d": D},
+                      "kappa_A": kappa_A,
                       "peaks": {"hbm_GBps": hbm_peak, "bf16_TFLOPs": bf16_peak, "kind": kind_peak},
                       "sketches": out}))
 
@@ -1082,7 +1101,8 @@ def _csr_dense_rows(m, n, dens, n_dense, gen, dev):
 def run_csr(args):
     """CSR 2^21 x 512, density 1 % plus 64 dense rows x100, CountSketch d = 2048:
     preconditioned against unpreconditioned iteration to eta <= 1e-8 (solves/s
-    and passes over A), and the CSR sketch's rate (8 B per nonzero + 8 B per row)."""
+    and passes over A), the bitwise reproducible form of the preconditioned solve
+    (variant "sorted"), and the CSR sketch's rate (8 B per nonzero + 8 B per row)."""
     import torch
     import paper_2409_14309_gb300 as sns
     from paper_2409_14309_gb300 import abi
@@ -1095,10 +1115,11 @@ def run_csr(args):
     rowptr, col, val, b, nnz = _csr_dense_rows(m, n, 0.01, 64, gen, dev)
     hbm_peak, _, peak_kind = peaks()
     out = {}
-    for name, pre in (("preconditioned", True), ("unpreconditioned", False)):
-        x = torch.empty(n, dtype=torch.float64, device=dev)
+    for name, pre, var in (("preconditioned", True, "auto"), ("unpreconditioned", False, "auto"),
+                           ("preconditioned_reproducible", True, "sorted")):
         for _ in range(max(1, args.warmup // 3)):
-            ctx.lstsq_csr(rowptr, col, val, b, n, d, seed=SKETCH_SEED, tol=tol, max_iter=4000, precondition=pre)
+            ctx.lstsq_csr(rowptr, col, val, b, n, d, seed=SKETCH_SEED, tol=tol, max_iter=4000, precondition=pre,
+                          variant=var)
         torch.cuda.synchronize()
         L.snsolve_profile(1)
         kernel_profile(L)
@@ -1106,7 +1127,7 @@ def run_csr(args):
         t0 = time.perf_counter()
         for _ in range(steps):
             _, info = ctx.lstsq_csr(rowptr, col, val, b, n, d, seed=SKETCH_SEED, tol=tol, max_iter=4000,
-                                    precondition=pre)
+                                    precondition=pre, variant=var)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / steps
         prof = kernel_profile(L)

@@ -72,9 +72,10 @@ typedef enum {
 typedef enum {
   SNS_CS_AUTO = 0,          /* library picks: FP32 dense -> SORTED while d <= 8192, else STREAM;
                                FP64 dense -> SORTED; CSR -> STREAM */
-  SNS_CS_SORTED = 1,        /* bucket-sorted segmented sum: bitwise reproducible on dense input;
-                               on CSR (d <= 8192) each bucket's rows are added with shared-memory
-                               atomics, so the order varies there too */
+  SNS_CS_SORTED = 1,        /* bucket-sorted segmented sum: bitwise reproducible (dense; CSR with
+                               d <= 8192 and n <= 6399, SNS_EINVAL beyond).  On CSR it also makes
+                               snsolve_lstsq's iterative passes reproducible (n <= 1422; about
+                               2.5x slower per pass than the default) */
   SNS_CS_STREAM = 2         /* one streaming pass with float reductions into SA (FP32 dense, CSR;
                                order of additions varies run to run) */
 } sns_cs_variant;

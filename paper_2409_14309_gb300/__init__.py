@@ -196,9 +196,11 @@ class Context:
                                   stream=stream)
 
     def lstsq_csr(self, rowptr, col, val, b, n, d, seed=0, tol=0.0, max_iter=0, inner=0, precondition=True,
-                  ws=None, stream=None):
+                  variant="auto", ws=None, stream=None):
+        """variant="sorted" makes the whole CSR solve bitwise reproducible
+        (n <= 1422), at about 2.5x the time of the default."""
         return self.lstsq_problem(csr_problem(rowptr, col, val, b, n),
-                                  opts(d, "countsketch", seed, "auto", tol, max_iter, inner, precondition),
+                                  opts(d, "countsketch", seed, variant, tol, max_iter, inner, precondition),
                                   ws=ws, stream=stream)
 
     # -------------------------------------------------------------- batched
@@ -296,10 +298,10 @@ class Server:
         return self.submit_problem(dense_problem(A, b), opts(d, kind, seed, "auto", tol, max_iter, inner), x,
                                    keep=(A, b)), x
 
-    def submit_csr(self, rowptr, col, val, b, n, d, seed=0, tol=0.0, max_iter=0):
+    def submit_csr(self, rowptr, col, val, b, n, d, seed=0, tol=0.0, max_iter=0, variant="auto"):
         x = torch.empty(n, dtype=torch.float64, device=self.ctx.device)
         return self.submit_problem(csr_problem(rowptr, col, val, b, n),
-                                   opts(d, "countsketch", seed, "auto", tol, max_iter), x,
+                                   opts(d, "countsketch", seed, variant, tol, max_iter), x,
                                    keep=(rowptr, col, val, b)), x
 
     def poll(self, rid, timeout_us=0):

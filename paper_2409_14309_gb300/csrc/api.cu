@@ -143,6 +143,7 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
       if (sk->variant == SNS_CS_SORTED && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
       if (sk->variant == SNS_CS_STREAM && p->fmt == SNS_DENSE_F64) return SNS_EINVAL;
       if (p->fmt == SNS_CSR_F32 && sk->variant == SNS_CS_SORTED && sk->d > cs_sorted_max_d()) return SNS_EINVAL;
+      if (p->fmt == SNS_CSR_F32 && sk->variant == SNS_CS_SORTED && p->n > cs_csr_sorted_max_n()) return SNS_EINVAL;
       if (p->fmt == SNS_CSR_F32 && p->n > 50000) return SNS_EINVAL;
       return SNS_OK;
     case SNS_GAUSSIAN:
@@ -162,9 +163,9 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
 }
 
 // CountSketch variant: FP64 dense is always sorted; CSR is sorted only when
-// asked for (the CSR iterative passes add in a varying order anyway, and the
-// streaming pass reads the CSR arrays once, in order); FP32 dense is sorted
-// unless asked otherwise or d is above the sorted variant's limit.
+// asked for (the sorted CSR sketch and the deterministic CSR passes it selects
+// cost ~2.5x the streaming ones, measured); FP32 dense is sorted unless asked
+// otherwise or d is above the sorted variant's limit.
 static bool cs_use_sorted(const sns_problem* p, const sns_sketch_desc* sk) {
   if (p->fmt == SNS_DENSE_F64) return true;
   if (sk->variant == SNS_CS_STREAM) return false;
@@ -255,6 +256,9 @@ static sns_status validate_opts(const sns_problem* p, const sns_opts* o) {
   sns_status s = validate_sketch(p, &o->sk);
   if (s != SNS_OK) return s;
   if (o->max_iter < 0 || o->inner < 0) return SNS_EINVAL;
+  if (p->fmt == SNS_CSR_F32 && o->sk.kind == SNS_COUNTSKETCH && o->sk.variant == SNS_CS_SORTED &&
+      p->n > csr_det_max_n())
+    return SNS_EINVAL;   // reproducible passes keep per-warp rows of n doubles in shared memory
   if (o->sk.d > 16384) return SNS_EINVAL;   // the QR keeps one column of SA in shared memory
   if (o->tol > 0 && p->fmt != SNS_CSR_F32 && p->n > 1024) return SNS_EINVAL;
   if (!(o->tol == o->tol)) return SNS_EINVAL;  // NaN
@@ -596,6 +600,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
   bool rinv_joined = false;
   DenseArgs da{prob->A, prob->lda, prob->b, prob->m, n, f64};
   CsrArgs ca{prob->rowptr, prob->col, prob->val, static_cast<const float*>(prob->b), prob->m, n, prob->nnz};
+  ca.det = opts->sk.kind == SNS_COUNTSKETCH && opts->sk.variant == SNS_CS_SORTED;   // reproducible CSR solve
   const DenseArgs* dap = prob->fmt == SNS_CSR_F32 ? nullptr : &da;
   const CsrArgs* cap = prob->fmt == SNS_CSR_F32 ? &ca : nullptr;
   // SAA: the explicit Y = A R^-1, formed before the first inner cycle

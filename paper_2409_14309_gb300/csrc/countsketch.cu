@@ -11,7 +11,8 @@
 //  * stream: one pass over A in row order; each warp adds its signed rows into
 //    SA with vector reductions (red.global.add.v4.f32) that land in L2.
 //  * CSR: phase 1 as above; phase 2 accumulates the sparse rows of a bucket
-//    slice into a shared-memory row with shared atomics, then combines as above.
+//    slice into per-warp shared-memory rows (equal columns of one step added
+//    in lane order), then combines as above: bitwise reproducible too.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -387,60 +388,82 @@ cs_gather_dense(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, i
   }
 }
 
-// Phase 2 (CSR): a lane takes a whole sparse row and adds it into the CTA's
-// shared row accumulator (n floats + 1 for b) with shared atomics.
-__global__ void __launch_bounds__(kGatherWarps * 32, 4)
+// Phase 2 (CSR): a lane takes a whole sparse row and adds it into its warp's
+// shared row accumulator (n floats + 1 for b); lanes that hit the same column
+// in one step add in lane order, the warps' rows are added in warp order and
+// the parts in part order, so the result is bitwise reproducible.
+__global__ void __launch_bounds__(kGatherWarps * 32)
 cs_gather_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
               const float* __restrict__ b, int64_t n, uint32_t d, int64_t nblk, int64_t spi, int64_t parts,
               const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ seg,
               uint32_t* __restrict__ ticket, float* __restrict__ part_buf,
               float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
   extern __shared__ __align__(16) uint8_t smraw[];
-  float* acc = reinterpret_cast<float*>(smraw);   // [n + 1]
+  float* accs = reinterpret_cast<float*>(smraw);   // [kGatherWarps][n + 1]: one row per warp
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  float* acc = accs + (size_t)w * (n + 1);
   const int64_t nitems = (int64_t)d * parts;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int64_t p = item % parts, k = item / parts;
     const int64_t sb0 = p * spi, sb1 = min(nblk, sb0 + spi);
-    for (int64_t c = threadIdx.x; c <= n; c += blockDim.x) acc[c] = 0.f;
+    for (int64_t c = threadIdx.x; c < (int64_t)kGatherWarps * (n + 1); c += blockDim.x) accs[c] = 0.f;
     __syncthreads();
     for (int64_t sbase = sb0 + w; sbase < sb1; sbase += (int64_t)kGatherWarps * 32) {
       const int64_t blk_l = sbase + (int64_t)lane * kGatherWarps;
       const SegSet S = load_segs(seg, k, nblk, blk_l, blk_l < sb1);
       for (uint32_t j0 = 0; j0 < S.total; j0 += 32) {
         const uint32_t rid = seg_row(S, sorted, j0 + lane);
-        if (rid != 0xFFFFFFFFu) {
-          const int64_t row = rid & 0x7FFFFFFFu;
-          const float sg = (rid >> 31) ? -1.f : 1.f;
-          const int64_t e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
-          const float bv = __ldg(b + row);
-          // the row's entries 8 at a time, all loads issued before the adds:
-          // rows are visited in bucket order, so every row is a random access
-          for (int64_t e = e0; e < e1; e += 8) {
-            int32_t cc[8];
-            float vv[8];
+        const bool okr = rid != 0xFFFFFFFFu;
+        const int64_t row = okr ? (int64_t)(rid & 0x7FFFFFFFu) : 0;
+        const float sg = (rid >> 31) ? -1.f : 1.f;
+        int64_t e = okr ? __ldg(rowptr + row) : 0;
+        const int64_t e1 = okr ? __ldg(rowptr + row + 1) : 0;
+        const float bv = okr ? sg * __ldg(b + row) : 0.f;
+        // the lanes' rows 8 entries at a time, warp-uniform; lanes that hit the
+        // same column add in lane order (one shared store per round), so every
+        // address sees its additions in a fixed order
+        while (__any_sync(0xffffffffu, e < e1)) {
+          int32_t cc[8];
+          float vv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const bool ok = e + u < e1;
-              cc[u] = ok ? __ldg(col + e + u) : -1;
-              vv[u] = ok ? __ldg(val + e + u) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (cc[u] >= 0) atomicAdd(acc + cc[u], sg * vv[u]);
+          for (int u = 0; u < 8; ++u) {
+            const bool ok = e + u < e1;
+            cc[u] = ok ? __ldg(col + e + u) : -1;
+            vv[u] = ok ? __ldg(val + e + u) : 0.f;
           }
-          atomicAdd(acc + n, sg * bv);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const unsigned peers = __match_any_sync(0xffffffffu, cc[u]);
+            const int rank = cc[u] >= 0 ? __popc(peers & lt) : 0;
+            const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)rank) + 1;
+            for (int rr = 0; rr < rounds; ++rr) {
+              if (cc[u] >= 0 && rank == rr) acc[cc[u]] += sg * vv[u];
+              __syncwarp();
+            }
+          }
+          e += 8;
         }
+        const float bs = warp_sum(bv);                    // fixed reduction tree
+        if (lane == 0) acc[n] += bs;
+        __syncwarp();
       }
     }
     __syncthreads();
+    // the warps' rows in warp order
+    auto total = [&](int64_t c) {
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < kGatherWarps; ++ww) t += accs[(size_t)ww * (n + 1) + c];
+      return t;
+    };
     if (parts == 1) {
-      for (int64_t c = threadIdx.x; c < n; c += blockDim.x) SA[k * ldsa + c] = acc[c];
-      if (threadIdx.x == 0) Sb[k * sbs] = acc[n];
+      for (int64_t c = threadIdx.x; c < n; c += blockDim.x) SA[k * ldsa + c] = total(c);
+      if (threadIdx.x == 0) Sb[k * sbs] = total(n);
     } else {
       float* pb = part_buf + ((size_t)k * parts + p) * (n + 1);
-      for (int64_t c = threadIdx.x; c <= n; c += blockDim.x) pb[c] = acc[c];
+      for (int64_t c = threadIdx.x; c <= n; c += blockDim.x) pb[c] = total(c);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) s_last = (atomicAdd(ticket + k, 1u) == (uint32_t)(parts - 1));
@@ -718,14 +741,21 @@ sns_status cs_apply_dense_stream(const DenseArgs& a, int64_t d, uint64_t seed, v
   return SNS_OK;
 }
 
+int64_t cs_csr_sorted_max_n() { return (int64_t)(200 * 1024) / (4 * kGatherWarps) - 1; }
+
 sns_status cs_apply_csr(const CsrArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb, int64_t sbs,
                         void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (a.n > cs_csr_sorted_max_n()) return SNS_EINVAL;
   const CsLayout L = cs_layout(a.m, a.n, d, false, true);
   if (ws_bytes < L.bytes) return SNS_ENOMEM;
   uint8_t* w = static_cast<uint8_t*>(ws);
   sns_status s = cs_phase1(a.m, d, seed, a.row0, L, w, st);
   if (s != SNS_OK) return s;
-  const size_t smem = (size_t)(a.n + 1) * 4;
+  const size_t smem = (size_t)kGatherWarps * (a.n + 1) * 4;     // one accumulator row per warp
+  int dev = 0, smem_max = 0;
+  SNS_CUDA_TRY(cudaGetDevice(&dev));
+  SNS_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)smem_max) return SNS_EINVAL;
   SNS_CUDA_TRY(raise_smem_limit((const void*)cs_gather_csr));
   int occ = 0;
   SNS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs_gather_csr, kGatherWarps * 32, smem));

@@ -585,20 +585,26 @@ normal_pass_f64(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
 // Rows are walked in chunks of 32 per warp (chunks go round the CTAs first, so
 // neighbouring chunks land on different SMs).  A row with at most kLongRow
 // nonzeros belongs to one lane, which loads its entries kRowBatch at a time.
-// Longer rows (dense rows) go to a per-CTA queue in shared memory that all
-// warps of the CTA drain after the main loop, each long row by a whole warp
-// with coalesced loads (inline when the queue is full).  Products are
-// scattered with shared-memory atomics into a per-warp accumulator row
-// (PERWARP; else one per CTA when n is too large), so only lanes of one warp
-// meet on an address; accumulator rows are added in a fixed order and reduced
-// across CTAs with tree_reduce.  The sum is deterministic up to the order in
-// which one atomic instruction applies equal-address lanes, and the order in
-// which warps drain the long-row queue.
+// Longer rows (dense rows) are taken by whole warps with coalesced loads: from
+// a per-CTA queue drained after the main loop (default), or right after the
+// chunk's short rows (DET).  Products are scattered into a per-warp
+// accumulator row (PERWARP; else one per CTA when n is too large) with shared
+// atomics (default).  With DET (asked for, and PERWARP) the
+// passes are bitwise reproducible: the walk is warp-uniform and static (every
+// row is taken by the same warp every run), lanes of one scatter step that hit
+// the same column add in lane order (rank rounds, plain shared stores),
+// accumulator rows are added in warp order and reduced across CTAs with
+// tree_reduce.  The rank rounds cost ~3.8x per pass (measured), hence opt-in.
 constexpr int kLongRow = 32;
 constexpr int kRowBatch = 8;             // entries loaded at once per lane (short rows)
 constexpr int kLongBatch = 16;           // per lane for long rows: 512-entry rows in one round trip
 // Shared memory up to which the CSR passes keep one accumulator row per warp.
 constexpr size_t kCsrSmemPerWarpMax = 100 * 1024;
+
+// The widest per-warp layout is the exact residual pass: x (double) plus one
+// double row per warp.
+int64_t csr_det_max_n() { return (int64_t)(kCsrSmemPerWarpMax / (8 + (size_t)kPassWarps * 8)); }
+
 
 constexpr int kLongQueue = 256;          // long rows queued per CTA (more are done in place)
 struct LongQueue {
@@ -606,12 +612,14 @@ struct LongQueue {
   int count, next;
 };
 
-// Walks this warp's chunks; short rows go to short_row(row, e0, e1) on their
-// lane; long rows are queued for the CTA (or passed to long_row(row, e0, e1)
-// by the whole warp when the queue is full), and all warps of the CTA drain
-// the queue after the main loop, one long row per warp at a time.
+// Walks this warp's chunks (default passes); short rows go to
+// short_row(row, e0, e1) on their lane; long rows are queued for the CTA (or
+// passed to long_row(row, e0, e1) by the whole warp when the queue is full),
+// and all warps of the CTA drain the queue after the main loop, one long row
+// per warp at a time (balances the dense rows across the CTA's warps).
 template <typename Short, typename Long>
-SNS_D void csr_walk(const int64_t* __restrict__ rowptr, int64_t m, LongQueue& Q, Short&& short_row, Long&& long_row) {
+SNS_D void csr_walk_queued(const int64_t* __restrict__ rowptr, int64_t m, LongQueue& Q, Short&& short_row,
+                           Long&& long_row) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)w * gridDim.x + blockIdx.x;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -654,13 +662,63 @@ SNS_D void csr_walk(const int64_t* __restrict__ rowptr, int64_t m, LongQueue& Q,
   }
 }
 
-template <bool PERWARP>
+// Walks this warp's chunks (reproducible passes); short rows go to
+// short_row(row, e0, e1, active), called by the whole warp with `active` set on
+// the lanes that own a short row; the chunk's long rows then go to
+// long_row(row, e0, e1), each taken by the whole warp, in lane order (no queue
+// shared by the CTA's warps, whose slot order would vary from run to run).
+template <typename Short, typename Long>
+SNS_D void csr_walk_static(const int64_t* __restrict__ rowptr, int64_t m, Short&& short_row, Long&& long_row) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)w * gridDim.x + blockIdx.x;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = gw * 32; r0 < m; r0 += nw * 32) {
+    const int64_t r = r0 + lane;
+    int64_t e0 = 0, e1 = 0;
+    if (r < m) {
+      e0 = __ldg(rowptr + r);
+      e1 = __ldg(rowptr + r + 1);
+    }
+    const bool lng = (e1 - e0) > kLongRow;
+    short_row(r < m ? r : 0, e0, e1, !lng && r < m);
+    unsigned lm = __ballot_sync(0xffffffffu, lng);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      long_row(r0 + src, __shfl_sync(0xffffffffu, e0, src), __shfl_sync(0xffffffffu, e1, src));
+    }
+  }
+}
+
+// One scatter step of a warp into its accumulator row acc: lane l adds v at
+// column c (c outside [0, n) adds nothing).  DET (a per-warp accumulator):
+// lanes with equal c add in lane order, one plain shared read-modify-write per
+// round; otherwise shared atomics (equal-address lanes apply in an order that
+// may vary, and the accumulator may be shared by the CTA's warps).
+template <bool DET, typename T>
+SNS_D void warp_scatter(T* acc, int64_t n, int32_t c, T v) {
+  const bool ok = (uint32_t)c < (uint64_t)n;
+  if constexpr (DET) {
+    const int lane = threadIdx.x & 31;
+    const int32_t key = ok ? c : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const unsigned rank = ok ? (unsigned)__popc(peers & ((1u << lane) - 1u)) : 0u;
+    const unsigned rounds = __reduce_max_sync(0xffffffffu, rank) + 1u;
+    for (unsigned rr = 0; rr < rounds; ++rr) {
+      if (ok && rank == rr) acc[c] += v;
+      __syncwarp();
+    }
+  } else {
+    if (ok) atomicAdd(acc + c, v);
+  }
+}
+
+template <bool PERWARP, bool DET>
 __global__ void __launch_bounds__(kPassThreads, 3)
 normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                 int64_t m, int64_t n, const float* __restrict__ z32, float* __restrict__ part,
                 uint32_t* __restrict__ ticket, double* __restrict__ lvl2, PcgVecs V) {
   extern __shared__ __align__(16) float fsm[];       // z[n], accumulators [PERWARP ? warps : 1][n]
-  __shared__ LongQueue Q;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int nacc = PERWARP ? kPassWarps : 1;
   grid_dep_wait();
@@ -671,36 +729,67 @@ normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ 
   for (int64_t c = threadIdx.x; c < nacc * n; c += blockDim.x) acc[c] = 0.f;
   __syncthreads();
   float* wl = acc + (PERWARP ? (size_t)w * n : 0);
+  // default: one lane per short row, shared atomics
   auto short_row = [&](int64_t, int64_t e0, int64_t e1) {
-    for (int64_t eb = e0; eb < e1; eb += kRowBatch) {
-      int32_t cc[kRowBatch];
-      float vv[kRowBatch];
+    int32_t cc[kRowBatch];
+    float vv[kRowBatch];
 #pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        const bool ok = eb + u < e1;
-        cc[u] = ok ? __ldg(col + eb + u) : -1;
-        vv[u] = ok ? __ldg(val + eb + u) : 0.f;
-      }
-      float t = 0.f;
+    for (int u = 0; u < kRowBatch; ++u) {
+      const bool ok = e0 + u < e1;
+      cc[u] = ok ? __ldg(col + e0 + u) : -1;
+      vv[u] = ok ? __ldg(val + e0 + u) : 0.f;
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u)
+      if ((uint32_t)cc[u] < (uint64_t)n) t = fmaf(vv[u], zs[cc[u]], t);
+    if (e0 + kRowBatch >= e1) {                        // the usual case: one batch holds the row
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u)
-        if ((uint32_t)cc[u] < (uint64_t)n) t = fmaf(vv[u], zs[cc[u]], t);
-      if (eb + kRowBatch >= e1 && eb == e0) {           // the usual case: one batch holds the row
+        if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(wl + cc[u], vv[u] * t);
+      return;
+    }
+    // rows of 9..32 entries: finish the dot, then scatter from the top
+    for (int64_t e = e0 + kRowBatch; e < e1; ++e) {
+      const uint32_t c = (uint32_t)__ldg(col + e);
+      if (c < (uint64_t)n) t = fmaf(__ldg(val + e), zs[c], t);
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+      const uint32_t c = (uint32_t)__ldg(col + e);
+      if (c < (uint64_t)n) atomicAdd(wl + c, __ldg(val + e) * t);
+    }
+  };
+  // DET: the whole warp steps through its short rows together (rank rounds)
+  auto short_row_det = [&](int64_t, int64_t e0, int64_t e1, bool active) {
+    // first batch of the row (all a row has in the usual case)
+    int32_t cc[kRowBatch];
+    float vv[kRowBatch];
 #pragma unroll
-        for (int u = 0; u < kRowBatch; ++u)
-          if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(wl + cc[u], vv[u] * t);
-        return;
-      }
-      // rows of 9..32 entries: finish the dot, then scatter from the top
-      for (int64_t e = eb + kRowBatch; e < e1; ++e) {
+    for (int u = 0; u < kRowBatch; ++u) {
+      const bool ok = active && e0 + u < e1;
+      cc[u] = ok ? __ldg(col + e0 + u) : -1;
+      vv[u] = ok ? __ldg(val + e0 + u) : 0.f;
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u)
+      if ((uint32_t)cc[u] < (uint64_t)n) t = fmaf(vv[u], zs[cc[u]], t);
+    if (active)                                         // rows of 9..32 entries: finish the dot
+      for (int64_t e = e0 + kRowBatch; e < e1; ++e) {
         const uint32_t c = (uint32_t)__ldg(col + e);
         if (c < (uint64_t)n) t = fmaf(__ldg(val + e), zs[c], t);
       }
-      for (int64_t e = e0; e < e1; ++e) {
-        const uint32_t c = (uint32_t)__ldg(col + e);
-        if (c < (uint64_t)n) atomicAdd(wl + c, __ldg(val + e) * t);
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u) warp_scatter<PERWARP && DET>(wl, n, cc[u], vv[u] * t);
+    for (int64_t eb = e0 + kRowBatch; __any_sync(0xffffffffu, active && eb < e1); eb += kRowBatch) {
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        const bool ok = active && eb + u < e1;
+        cc[u] = ok ? __ldg(col + eb + u) : -1;
+        vv[u] = ok ? __ldg(val + eb + u) : 0.f;
       }
-      return;
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) warp_scatter<PERWARP && DET>(wl, n, cc[u], vv[u] * t);
     }
   };
   auto long_row = [&](int64_t, int64_t a0, int64_t a1) {
@@ -729,11 +818,15 @@ normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ 
         vv[u] = e < a1 ? __ldg(val + e) : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < kLongBatch; ++u)
-        if ((uint32_t)cc[u] < (uint64_t)n) atomicAdd(wl + cc[u], vv[u] * t);
+      for (int u = 0; u < kLongBatch; ++u) warp_scatter<PERWARP && DET>(wl, n, cc[u], vv[u] * t);
     }
   };
-  csr_walk(rowptr, m, Q, short_row, long_row);
+  if constexpr (DET) {
+    csr_walk_static(rowptr, m, short_row_det, long_row);
+  } else {
+    __shared__ LongQueue Q;
+    csr_walk_queued(rowptr, m, Q, short_row, long_row);
+  }
   grid_dep_trigger();
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * n;
@@ -749,7 +842,7 @@ normal_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ 
 // Residual pass on CSR: r_i = b_i - a_i . x with exact products and
 // compensated sums (x = x_hi + x_lo in FP32), one FP64 value per row; g = A^T r
 // with FP64 shared atomics of a * r (EXACT) or FP32 atomics of a * r_hi.
-template <bool EXACT, bool ANORM, bool PERWARP>
+template <bool EXACT, bool ANORM, bool PERWARP, bool DET>
 __global__ void __launch_bounds__(kPassThreads, 2)
 resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
                const float* __restrict__ b, int64_t m, int64_t n, const double* __restrict__ x,
@@ -758,7 +851,6 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
   using AccT = typename std::conditional<EXACT, double, float>::type;
   extern __shared__ __align__(16) double dsm[];      // x_hi[n], x_lo[n] (FP32), accumulators
   __shared__ double sred[kPassWarps][2];
-  __shared__ LongQueue Q;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int nacc = PERWARP ? kPassWarps : 1;
   float* xh = reinterpret_cast<float*>(dsm);
@@ -788,12 +880,12 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
     rh = rc.hi + rc.lo;
     rl = rc.lo - (rh - rc.hi);
   };
+  // one scatter step of the warp: lane adds a * r at column c (c < 0: nothing)
   auto scatter = [&](int32_t c, float a, float rh, double rd) {
-    if ((uint32_t)c < (uint64_t)n) {
-      if constexpr (EXACT) atomicAdd(gl + c, (double)a * rd);
-      else atomicAdd(gl + c, a * rh);
-    }
+    if constexpr (EXACT) warp_scatter<PERWARP && DET, double>(gl, n, c, (double)a * rd);
+    else warp_scatter<PERWARP && DET, float>(gl, n, c, a * rh);
   };
+  // default: one lane per short row, shared atomics
   auto short_row = [&](int64_t r, int64_t e0, int64_t e1) {
     const float bv = __ldg(b + r);
     int32_t cc[kRowBatch];
@@ -818,6 +910,43 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
     for (int u = 0; u < kRowBatch; ++u)
       if (cc[u] >= 0) scatter(cc[u], vv[u], rh, rd);
     for (int64_t e = e0 + kRowBatch; e < e1; ++e) scatter(__ldg(col + e), __ldg(val + e), rh, rd);
+  };
+  // DET: the whole warp steps through its short rows together (rank rounds)
+  auto short_row_det = [&](int64_t r, int64_t e0, int64_t e1, bool active) {
+    const float bv = active ? __ldg(b + r) : 0.f;
+    int32_t cc[kRowBatch];
+    float vv[kRowBatch];
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u) {
+      const bool ok = active && e0 + u < e1;
+      cc[u] = ok ? __ldg(col + e0 + u) : -1;
+      vv[u] = ok ? __ldg(val + e0 + u) : 0.f;
+    }
+    Comp sdot = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u)
+      if (cc[u] >= 0) add_entry(sdot, cc[u], vv[u]);
+    if (active)
+      for (int64_t e = e0 + kRowBatch; e < e1; ++e) add_entry(sdot, __ldg(col + e), __ldg(val + e));
+    float rh = 0.f, rl = 0.f;
+    if (active) {
+      resid_of(bv, sdot, rh, rl);
+      comp_fma(rrc, rh, rh);
+      rrc.lo = fmaf(2.f * rh, rl, rrc.lo);
+    }
+    const double rd = EXACT ? (double)rh + (double)rl : 0.0;
+#pragma unroll
+    for (int u = 0; u < kRowBatch; ++u) scatter(cc[u], vv[u], rh, rd);
+    for (int64_t eb = e0 + kRowBatch; __any_sync(0xffffffffu, active && eb < e1); eb += kRowBatch) {
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        const bool ok = active && eb + u < e1;
+        cc[u] = ok ? __ldg(col + eb + u) : -1;
+        vv[u] = ok ? __ldg(val + eb + u) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) scatter(cc[u], vv[u], rh, rd);
+    }
   };
   auto long_row = [&](int64_t r, int64_t a0, int64_t a1) {
     Comp sdot = {0.f, 0.f};
@@ -853,11 +982,15 @@ resid_pass_csr(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ c
         vv[u] = e < a1 ? __ldg(val + e) : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < kLongBatch; ++u)
-        if (cc[u] >= 0) scatter(cc[u], vv[u], rh, rd);
+      for (int u = 0; u < kLongBatch; ++u) scatter(cc[u], vv[u], rh, rd);
     }
   };
-  csr_walk(rowptr, m, Q, short_row, long_row);
+  if constexpr (DET) {
+    csr_walk_static(rowptr, m, short_row_det, long_row);
+  } else {
+    __shared__ LongQueue Q;
+    csr_walk_queued(rowptr, m, Q, short_row, long_row);
+  }
   const double rrw = warp_sum((double)rrc.hi + (double)rrc.lo);
   const double anw = ANORM ? warp_sum((double)an) : 0.0;
   if (lane == 0) {
@@ -955,11 +1088,13 @@ sns_status resid_pass(const DenseArgs* da, const CsrArgs* ca, const double* x, c
     const size_t esz = exact_g ? 8 : 4;
     const bool perwarp = (size_t)n * 8 + (size_t)kPassWarps * n * esz <= kCsrSmemPerWarpMax;
     const size_t smem = (size_t)n * 8 + (perwarp ? (size_t)kPassWarps : 1) * n * esz;
-    const void* fns[2][2][2] = {{{(const void*)resid_pass_csr<false, false, false>, (const void*)resid_pass_csr<false, false, true>},
-                                 {(const void*)resid_pass_csr<false, true, false>, (const void*)resid_pass_csr<false, true, true>}},
-                                {{(const void*)resid_pass_csr<true, false, false>, (const void*)resid_pass_csr<true, false, true>},
-                                 {(const void*)resid_pass_csr<true, true, false>, (const void*)resid_pass_csr<true, true, true>}}};
-    const void* fn = fns[exact_g][want_anorm][perwarp];
+#define SNS_RCSR(E, A, P) (const void*)resid_pass_csr<E, A, P, false>, (const void*)resid_pass_csr<E, A, P, true>
+    const void* fns[2][2][2][2] = {{{{SNS_RCSR(false, false, false)}, {SNS_RCSR(false, false, true)}},
+                                    {{SNS_RCSR(false, true, false)}, {SNS_RCSR(false, true, true)}}},
+                                   {{{SNS_RCSR(true, false, false)}, {SNS_RCSR(true, false, true)}},
+                                    {{SNS_RCSR(true, true, false)}, {SNS_RCSR(true, true, true)}}}};
+#undef SNS_RCSR
+    const void* fn = fns[exact_g][want_anorm][perwarp][perwarp && ca->det];
     SNS_CUDA_TRY(raise_smem_limit(fn));
     const int grid = pass_grid(fn, smem, W.grid);
     const float* bb = ca->b;
@@ -989,7 +1124,8 @@ sns_status normal_pass(const DenseArgs* da, const CsrArgs* ca, const IterWs& W, 
     const int64_t n = ca->n;
     const bool perwarp = (size_t)(1 + kPassWarps) * n * 4 <= kCsrSmemPerWarpMax;
     const size_t smem = (size_t)(1 + (perwarp ? kPassWarps : 1)) * n * 4;
-    auto k = perwarp ? normal_pass_csr<true> : normal_pass_csr<false>;
+    auto k = perwarp ? (ca->det ? normal_pass_csr<true, true> : normal_pass_csr<true, false>)
+                     : normal_pass_csr<false, false>;
     SNS_CUDA_TRY(raise_smem_limit((const void*)k));
     const int grid = pass_grid((const void*)k, smem, W.grid);
     {

@@ -26,6 +26,7 @@ struct CsrArgs {
   const float* b;
   int64_t m, n, nnz;
   int64_t row0 = 0;
+  bool det = false;        // iterative passes: bitwise reproducible scatters (slower)
 };
 
 // CountSketch workspace layout.
@@ -50,6 +51,11 @@ sns_status cs_coop_apply(const DenseArgs& a, int64_t d, uint64_t seed, const CsL
 bool cs_bulk_gather_selected();
 CsLayout cs_layout(int64_t m, int64_t n, int64_t d, bool f64, bool csr);
 int64_t cs_sorted_max_d();
+// Largest n for which the sorted CSR gather's per-warp accumulator rows fit.
+int64_t cs_csr_sorted_max_n();
+// Largest n whose CSR iterative passes can run bitwise reproducibly (per-warp
+// accumulator rows for every pass variant).
+int64_t csr_det_max_n();
 int num_sms();
 
 sns_status cs_apply_dense_sorted(const DenseArgs& a, int64_t d, uint64_t seed, void* SA, int64_t ldsa, void* Sb,

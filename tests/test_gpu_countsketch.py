@@ -129,6 +129,22 @@ def test_countsketch_csr(m, n, d, dens, variant):
     assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 4), scale) <= TOL32
 
 
+def test_csr_sorted_bitwise_reproducible():
+    """The sorted CSR sketch adds every bucket's rows in a fixed order:
+    repeated and concurrent sketches are equal bit for bit."""
+    c = ctx()
+    A, b, _ = csr_problem(150000, 256, seed=8, density=0.03, n_dense=16)
+    args = (dev(A.rowptr), dev(A.col), dev(A.val), dev(b), 256, 1024)
+    SA1, Sb1 = c.sketch_csr(*args, seed=6, variant="sorted")
+    outs = []
+    for s in (torch.cuda.Stream(), torch.cuda.Stream()):
+        with torch.cuda.stream(s):
+            outs.append(c.sketch_csr(*args, seed=6, variant="sorted", stream=s))
+    torch.cuda.synchronize()
+    for SA, Sb in outs:
+        assert torch.equal(SA, SA1) and torch.equal(Sb, Sb1)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("variant", ["sorted", "stream"])
 def test_full_size_ill_conditioned_sampled_rows(variant):

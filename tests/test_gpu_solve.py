@@ -166,6 +166,36 @@ def test_csr_preconditioned_vs_unpreconditioned():
     assert i1.iters < i2.iters
 
 
+def test_csr_solve_bitwise_reproducible():
+    """CSR sketch-and-precondition with variant "sorted" (the sorted sketch and
+    the deterministic per-warp passes): repeated solves give the same bits."""
+    c = ctx()
+    A, b, _ = csr_problem(120000, 96, seed=9, density=0.03, n_dense=12)
+    args = (dev(A.rowptr), dev(A.col), dev(A.val), dev(b), 96, 384)
+    x1, i1 = c.lstsq_csr(*args, seed=2, tol=1e-10, max_iter=2000, variant="sorted")
+    x2, i2 = c.lstsq_csr(*args, seed=2, tol=1e-10, max_iter=2000, variant="sorted")
+    assert i1.status == 0 and i2.status == 0
+    assert i1.iters == i2.iters
+    assert torch.equal(x1, x2)
+    # the default (streaming sketch, atomic passes) reaches the same accuracy
+    x3, i3 = c.lstsq_csr(*args, seed=2, tol=1e-10, max_iter=2000)
+    D, bd = A.to_dense(), b.astype(np.float64)
+    assert i3.status == 0
+    assert OL.eta(D, bd, x3.cpu().numpy()) <= 1.5e-10 and OL.eta(D, bd, x1.cpu().numpy()) <= 1.5e-10
+
+
+def test_csr_sorted_solve_limits():
+    """The reproducible CSR solve needs per-warp rows of n doubles: n above
+    the limit is refused, the default variant still solves it."""
+    c = ctx()
+    A, b, _ = csr_problem(3000, 1500, seed=10, density=0.01, n_dense=0)
+    args = (dev(A.rowptr), dev(A.col), dev(A.val), dev(b), 1500, 3000)
+    with pytest.raises(RuntimeError):
+        c.lstsq_csr(*args, seed=1, variant="sorted")
+    x, info = c.lstsq_csr(*args, seed=1)
+    assert info.status in (0, 1)
+
+
 def test_max_iter_reports_not_converged():
     c = ctx()
     A, b, _ = ill_conditioned_problem(20000, 32, seed=13, kappa=1e6, noise=1e-4)
