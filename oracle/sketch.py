@@ -12,7 +12,8 @@ Three families, as the paper lists them:
   SplitMix64 output of stream 3 serves eight consecutive columns of one row:
   entry (k, i) uses byte (i mod 8) of output (i div 8) * d + k.  The
   tensor-core path multiplies BF16 operands, so the oracle offers SA for both
-  the exact A and the BF16-rounded A.
+  the exact A and A as the sum of its first T BF16 terms (bf16_split: T = 1 is
+  A rounded to BF16; T = 3 is an FP32 A exactly).
 * Subsampled randomized Hadamard (Sec. 1.2.1): S = (1/sqrt(d)) P H D with
   m' = 2^ceil(log2 m) (rows m..m'-1 of [A | b] are zero), H the unnormalised
   Sylvester-Hadamard matrix H[p, i] = (-1)^popcount(p & i) applied by the fast
@@ -86,6 +87,28 @@ def round_to_bf16_via_f32(x):
     r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
+
+def bf16_split(x, terms):
+    """The first `terms` BF16 terms of FP32 values x (list of FP64 arrays):
+    term 1 is x rounded to BF16, term t + 1 is the rounding of the remainder
+    x - (term 1 + .. + term t), each remainder computed exactly in FP64."""
+    rem = np.asarray(x, dtype=np.float32).astype(np.float64)
+    out = []
+    for _ in range(terms):
+        t = round_to_bf16(rem)
+        out.append(t)
+        rem = rem - t
+    return out
+
+
+def bf16_terms(x, terms):
+    """x as the sum of its first `terms` BF16 terms (FP64)."""
+    parts = bf16_split(x, terms)
+    total = parts[0].copy()
+    for t in parts[1:]:
+        total += t
+    return total
+
 # ---------------------------------------------------------------- Gaussian
 
 GAUSS_TABLE_BITS = 8
@@ -113,11 +136,12 @@ def gaussian_matrix(m, d, seed):
     return gaussian_table()[gaussian_indices(m, d, seed)] / math.sqrt(d)
 
 
-def gaussian_apply(A, d, seed, bf16_operand=True):
-    """SA = (G / sqrt(d)) A.  With bf16_operand the matrix A is first rounded to
-    BF16 (the operand the tensor-core path multiplies); the product is FP64."""
+def gaussian_apply(A, d, seed, bf16_operand=True, terms=1):
+    """SA = (G / sqrt(d)) A.  With bf16_operand the matrix A is first replaced
+    by the sum of its first `terms` BF16 terms (the operand the tensor-core path
+    multiplies; terms = 1: A rounded to BF16); the product is FP64."""
     A = np.asarray(A)
-    Ause = round_to_bf16_via_f32(A) if bf16_operand else A.astype(np.float64)
+    Ause = bf16_terms(A, terms) if bf16_operand else A.astype(np.float64)
     S = gaussian_matrix(A.shape[0], d, seed)
     return S @ Ause
 
@@ -200,11 +224,11 @@ def srht_apply(A, d, seed):
 KINDS = ("countsketch", "gaussian", "srht")
 
 
-def sketch_apply(kind, A, d, seed, bf16_operand=True):
+def sketch_apply(kind, A, d, seed, bf16_operand=True, terms=1):
     if kind == "countsketch":
         return countsketch_apply(A, d, seed)
     if kind == "gaussian":
-        return gaussian_apply(A, d, seed, bf16_operand=bf16_operand)
+        return gaussian_apply(A, d, seed, bf16_operand=bf16_operand, terms=terms)
     if kind == "srht":
         return srht_apply(A, d, seed)
     raise ValueError(kind)
@@ -234,14 +258,14 @@ def countsketch_rows(A, d, seed, rows):
     return np.array(out)
 
 
-def gaussian_rows(A, d, seed, rows, bf16_operand=True):
+def gaussian_rows(A, d, seed, rows, bf16_operand=True, terms=1):
     """Selected output rows k of (G / sqrt(d)) A (Sec. 1.2.1), each from its own
     row of G: G[k, i] = T[index(k, i)] for all i, then one dot product per
     column; FP64.  Same layout as gaussian_indices, one row at a time, for
     checking full-size results."""
     A = np.asarray(A)
     m = A.shape[0]
-    Ause = round_to_bf16_via_f32(A) if bf16_operand else A.astype(np.float64)
+    Ause = bf16_terms(A, terms) if bf16_operand else A.astype(np.float64)
     T = gaussian_table()
     i = np.arange(m, dtype=np.uint64)
     state = H.stream_state(seed, H.STREAM_GAUSSIAN)

@@ -102,6 +102,39 @@ def test_gaussian_sketch_and_solve_expected_residual():
     assert abs(np.mean(ratios) - expect) < 3.5 * se
 
 
+def test_bf16_split_terms():
+    """Three BF16 terms (8 significant bits each) hold an FP32 value exactly;
+    two leave at most 2^-16 of it; each term is itself a BF16 number (torch's
+    rounding leaves it unchanged), and every term after the first is at most
+    2^-8 of the previous remainder's size."""
+    rng = np.random.default_rng(12)
+    x = (rng.standard_normal(200000) * np.exp(rng.uniform(-40, 40, 200000))).astype(np.float32)
+    x64 = x.astype(np.float64)
+    parts = S.bf16_split(x, 3)
+    for t in parts:
+        assert np.array_equal(torch.from_numpy(t).to(torch.bfloat16).to(torch.float64).numpy(), t)
+    assert np.array_equal(parts[0] + parts[1] + parts[2], x64)
+    assert np.array_equal(S.bf16_terms(x, 3), x64)
+    assert np.array_equal(S.bf16_terms(x, 1), torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy())
+    assert np.all(np.abs(x64 - S.bf16_terms(x, 2)) <= np.ldexp(np.abs(x64), -16))
+    assert np.all(np.abs(parts[1]) <= np.ldexp(np.abs(x64), -8))
+    assert np.all(np.abs(parts[2]) <= np.ldexp(np.abs(x64 - parts[0]), -8))
+    # one term is strictly coarser than two: most values are not BF16 numbers
+    assert np.mean(S.bf16_terms(x, 1) != S.bf16_terms(x, 2)) > 0.9
+
+
+def test_gaussian_apply_three_terms_is_exact_fp32():
+    rng = np.random.default_rng(13)
+    A = (rng.standard_normal((300, 6)) * np.exp(rng.uniform(-5, 5, (300, 6)))).astype(np.float32)
+    Gm = S.gaussian_matrix(300, 16, 2)
+    exact = Gm @ A.astype(np.float64)
+    assert np.allclose(S.gaussian_apply(A, 16, 2, terms=3), exact, rtol=1e-13, atol=1e-13)
+    assert np.allclose(S.gaussian_apply(A, 16, 2, bf16_operand=False), exact, rtol=1e-13, atol=1e-13)
+    two = S.gaussian_apply(A, 16, 2, terms=2)
+    assert np.abs(two - exact).max() <= 2.0 ** -16 * (np.abs(Gm) @ np.abs(A.astype(np.float64))).max()
+    assert not np.allclose(S.gaussian_apply(A, 16, 2, terms=1), exact, rtol=1e-5, atol=0)
+
+
 def test_gaussian_apply_bf16_operand():
     rng = np.random.default_rng(4)
     A = rng.standard_normal((100, 5)).astype(np.float32)
