@@ -356,6 +356,8 @@ def main():
                     help="served workload: arrival rates as multiples of the one-slot capacity")
     ap.add_argument("--sweep-requests", type=int, default=4000,
                     help="served workload: requests at the rates below the highest one")
+    ap.add_argument("--gauss-terms", default="auto", choices=["auto", "1", "2", "3"],
+                    help="profile-case gaussian: BF16 terms of [A | b]")
     ap.add_argument("--case", default="solve", choices=["solve", "countsketch", "srht", "gaussian", "csr", "batched"],
                     help="profile-case: which small case to run")
     ap.add_argument("--latency-solves", type=int, default=200,
@@ -943,7 +945,9 @@ def run_sketches(args):
     for name, kind, variant in [("countsketch_sorted", "countsketch", "sorted"),
                                 ("countsketch_stream", "countsketch", "stream"),
                                 ("sparse_sign_zeta4", "sparse_sign", 4),
-                                ("gaussian_tcgen05", "gaussian", "auto"), ("srht", "srht", "auto")]:
+                                ("gaussian_tcgen05", "gaussian", "auto"),
+                                ("gaussian_tcgen05_2terms", "gaussian", 2),
+                                ("gaussian_tcgen05_3terms", "gaussian", 3), ("srht", "srht", "auto")]:
         prob = sns.dense_problem(A, b)
         sk = sns.sketch_desc(D, kind, SKETCH_SEED, variant)
         ws = torch.empty(max(ctx.sketch_workspace(prob, sk), 256), dtype=torch.uint8, device=dev)
@@ -965,9 +969,13 @@ def run_sketches(args):
         r = {"ms": ms, "GBps": byts / (ms / 1e3) / 1e9, "frac_hbm": byts / (ms / 1e3) / 1e9 / hbm_peak,
              "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()}}
         if kind == "gaussian":
+            # algorithmic flops of G [A | b]; the tensor cores run one product per BF16 term
+            terms = 1 if variant == "auto" else int(variant)
             fl = 2.0 * D * M * (N + 1)
+            r["terms"] = terms
             r["TFLOPs"] = fl / (ms / 1e3) / 1e12
-            r["frac_bf16"] = r["TFLOPs"] / bf16_peak
+            r["tensor_TFLOPs"] = terms * r["TFLOPs"]
+            r["frac_bf16"] = r["tensor_TFLOPs"] / bf16_peak
         SA_k, _ = ctx.sketch_problem(prob, sk, torch.float32, ws=ws)
         r["kappa_A_Rinv"] = kappa_precond(SA_k)
         out[name] = r
@@ -1068,10 +1076,11 @@ def run_profile_case(args):
         m = (1 << 19) if args.case == "countsketch" else (1 << 18)
         A = torch.randn(m, 256, generator=gen, device=dev)
         b = torch.randn(m, generator=gen, device=dev)
+        variant = args.gauss_terms if args.case == "gaussian" else "auto"
         for _ in range(3):
-            SA, Sb = ctx.sketch(A, b, 1024, kind=args.case, seed=1)
+            SA, Sb = ctx.sketch(A, b, 1024, kind=args.case, seed=1, variant=variant)
         torch.cuda.synchronize()
-        print(json.dumps({"case": args.case, "m": m, "norm_SA": float(SA.norm())}))
+        print(json.dumps({"case": args.case, "m": m, "variant": variant, "norm_SA": float(SA.norm())}))
 
 
 def _csr_dense_rows(m, n, dens, n_dense, gen, dev):

@@ -93,7 +93,11 @@ typedef enum {
  * draw of the column took u; the sign of draw z is bit 63 of its key. */
 typedef struct {
   int32_t kind;        /* sns_sketch_kind */
-  int32_t variant;     /* sns_cs_variant for CountSketch; zeta for SNS_SPARSE_SIGN; ignored otherwise */
+  int32_t variant;     /* sns_cs_variant for CountSketch; zeta for SNS_SPARSE_SIGN; for SNS_GAUSSIAN
+                          the BF16 terms [A | b] is split into for the tensor cores: 1 = rounded to
+                          BF16 (fastest), 2 = 16 significant bits, 3 = the FP32 values exactly;
+                          0 = auto: 1 in snsolve_sketch*, 3 in snsolve_lstsq and the server (a
+                          one-term R preconditions ill-conditioned A poorly); ignored otherwise */
   int64_t d;           /* sketch rows, n <= d; SRHT also d <= m' */
   uint64_t seed;
 } sns_sketch_desc;
@@ -177,8 +181,8 @@ sns_status snsolve_sketch_workspace_size(const sns_problem* prob, const sns_sket
 
 /* SA = S A (d x n, row-major, leading dimension ldsa >= n) and Sb = S b
  * (d entries).  SA and Sb are float for F32/CSR input and double for F64 input.
- * Gaussian sketches multiply BF16-rounded A in the tensor cores with FP32
- * accumulation (F32 input only).  Asynchronous on `stream`.
+ * Gaussian sketches multiply [A | b] as 1-3 BF16 terms (sk->variant) in the
+ * tensor cores with FP32 accumulation (F32 input only).  Asynchronous on `stream`.
  * Two sketch kernels wait on the device (the tensor-core Gaussian sketch and
  * the bulk-copy CountSketch gather, selected by SNSOLVE_CS_GATHER=t); their
  * waits are bounded, and one that gives up leaves SA/Sb incomplete and an

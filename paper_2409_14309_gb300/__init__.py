@@ -64,9 +64,13 @@ def csr_problem(rowptr, col, val, b, n):
 def sketch_desc(d, kind="countsketch", seed=0, variant="auto"):
     """Sketch descriptor.  For CountSketch `variant` is "auto", "sorted" or
     "stream"; for the sparse sign embedding it is zeta, the nonzeros per column
-    (an int 1..8; "auto" means 4)."""
+    (an int 1..8; "auto" means 4); for the Gaussian sketch it is the number of
+    BF16 terms of [A | b] in the tensor-core product (1, 2 or 3; "auto": 1 for
+    a sketch, 3 inside a solve)."""
     if kind == "sparse_sign":
         v = 4 if variant == "auto" else int(variant)
+    elif kind == "gaussian":
+        v = 0 if variant == "auto" else int(variant)
     else:
         v = VARIANT[variant]
     return abi.sns_sketch_desc(kind=KIND[kind], variant=v, d=int(d), seed=int(seed) & (2**64 - 1))

@@ -148,6 +148,7 @@ static sns_status validate_sketch(const sns_problem* p, const sns_sketch_desc* s
       return SNS_OK;
     case SNS_GAUSSIAN:
       if (p->fmt != SNS_DENSE_F32) return SNS_EINVAL;
+      if (sk->variant < 0 || sk->variant > 3) return SNS_EINVAL;   // BF16 terms of A (0: auto)
       return SNS_OK;
     case SNS_SRHT:
       if (p->fmt == SNS_CSR_F32) return SNS_EINVAL;
@@ -174,13 +175,26 @@ static bool cs_use_sorted(const sns_problem* p, const sns_sketch_desc* sk) {
   return sk->d <= cs_sorted_max_d();
 }
 
+// BF16 terms of A in the tensor-core Gaussian product; AUTO is one term for a
+// sketch returned to the caller (solve paths resolve it first: solve_sketch).
+static int gauss_terms(const sns_sketch_desc* sk) { return sk->variant == 0 ? 1 : sk->variant; }
+
+// The sketch a solve applies: AUTO Gaussian becomes three BF16 terms (FP32 A
+// exactly), since R of a one-term sketch preconditions an ill-conditioned A
+// poorly (kappa(A R^-1) grows with kappa(A) * 2^-9).
+static sns_sketch_desc solve_sketch(const sns_opts* o) {
+  sns_sketch_desc sk = o->sk;
+  if (sk.kind == SNS_GAUSSIAN && sk.variant == 0) sk.variant = 3;
+  return sk;
+}
+
 static size_t sketch_ws(const sns_problem* p, const sns_sketch_desc* sk) {
   switch (sk->kind) {
     case SNS_COUNTSKETCH:
       if (!cs_use_sorted(p, sk)) return 0;
       return cs_layout(p->m, p->n, sk->d, is_f64(p), p->fmt == SNS_CSR_F32).bytes;
     case SNS_GAUSSIAN:
-      return gauss_ws_bytes(p->m, p->n, sk->d);
+      return gauss_ws_bytes(p->m, p->n, sk->d, gauss_terms(sk));
     case SNS_SRHT:
       return srht_ws_bytes(p->m, p->n, sk->d, is_f64(p));
     case SNS_SPARSE_SIGN:
@@ -214,7 +228,8 @@ static sns_status run_sketch(const sns_problem* p, const sns_sketch_desc* sk, vo
       if (cs_use_sorted(p, sk)) return cs_apply_dense_sorted(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, ws, ws_bytes, st);
       return cs_apply_dense_stream(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, st);
     case SNS_GAUSSIAN:
-      return gauss_apply_dense(da, sk->d, sk->seed, static_cast<float*>(SA), ldsa, static_cast<float*>(Sb), sbs, ws,
+      return gauss_apply_dense(da, sk->d, sk->seed, gauss_terms(sk), static_cast<float*>(SA), ldsa,
+                               static_cast<float*>(Sb), sbs, ws,
                                ws_bytes, st);
     case SNS_SRHT:
       return srht_apply_dense(da, sk->d, sk->seed, SA, ldsa, Sb, sbs, ws, ws_bytes, st);
@@ -237,7 +252,8 @@ static LsLayout ls_layout(const sns_problem* p, const sns_opts* o) {
   const size_t esz = is_f64(p) ? 8 : 4;
   size_t off = 0;
   L.off_saug = off; off += al((size_t)d * q * esz);
-  L.sk_bytes = sketch_ws(p, &o->sk);
+  const sns_sketch_desc sk = solve_sketch(o);
+  L.sk_bytes = sketch_ws(p, &sk);
   L.off_sk = off; off += al(L.sk_bytes);
   L.off_w = off; off += al((size_t)d * q * 8);
   L.off_dev = off; off += al(64);
@@ -527,7 +543,8 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
     // steps 1-2: S [A | b] into the augmented buffer (ld = n + 1)
     void* SA = w + L.off_saug;
     void* Sb = w + L.off_saug + (size_t)n * (f64 ? 8 : 4);
-    s = run_sketch(prob, &opts->sk, SA, q, Sb, q, w + L.off_sk, L.sk_bytes, st);
+    const sns_sketch_desc sk = solve_sketch(opts);
+    s = run_sketch(prob, &sk, SA, q, Sb, q, w + L.off_sk, L.sk_bytes, st);
     if (s != SNS_OK) return s;
     if (pe) SNS_CUDA_TRY(cudaEventRecord(pe->e[1], st));
     // step 3: FP64 Householder QR of [SA | Sb] and back substitution
@@ -548,7 +565,7 @@ sns_status snsolve_lstsq(sns_ctx* ctx, const sns_problem* prob, const sns_opts* 
       const size_t eoff = L.off_qr + qr_coop_err_offset(d, q);
       SNS_CUDA_TRY(cudaMemcpyAsync(hp + 18, w + eoff, 4, cudaMemcpyDeviceToHost, st));
     }
-    const void* skerr = sketch_err_word(prob, &opts->sk, w + L.off_sk);
+    const void* skerr = sketch_err_word(prob, &sk, w + L.off_sk);
     if (skerr) SNS_CUDA_TRY(cudaMemcpyAsync(hp + 19, skerr, 4, cudaMemcpyDeviceToHost, st));
     SNS_CUDA_TRY(cudaStreamSynchronize(st));
     int32_t qs, qerr = 0, serr = 0;

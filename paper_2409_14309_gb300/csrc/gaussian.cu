@@ -4,10 +4,12 @@
 // stream 3 (one output serves the eight columns 8t .. 8t + 7 of row k), and
 // T[j] = BF16(Phi^-1((j + 1/2)/256)).
 // G is never stored: tiles are generated where they are consumed.  The operand
-// [A | b] is rounded to BF16 (round to nearest even) and products accumulate in
-// FP32, the precision of a BF16 tensor-core contraction.
+// [A | b] enters the BF16 tensor cores as T BF16 terms (T = 1: rounded to BF16,
+// round to nearest even; T = 3: the FP32 values exactly) and products
+// accumulate in FP32.
 //
-// This file holds the host-side table and the SIMT reference-speed path.
+// This file holds the host-side table, the SIMT path (one term) and the
+// tensor-core path.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -131,55 +133,70 @@ gauss_simt(const float* __restrict__ A, int64_t lda, const float* __restrict__ b
 // ---------------------------------------------------------------------------
 // Tensor-core path (tcgen05, BF16 operands, FP32 accumulation in TMEM).
 //
-// Two kernels.  gauss_convert streams [A | b] once: it rounds A to BF16
-// (round to nearest even) and writes it as ready-made MMA operand tiles, one
-// per (64-row chunk, 256-column tile), in the canonical K-major layout without
-// swizzle (8 x 16-byte core matrices: element (column nn, row k) at
-// ((nn/8)*8 + k/8)*128 + (nn%8)*16 + (k%8)*2), beside each chunk's 64
-// BF16-rounded b values as FP32.  gauss_umma then never touches FP32 A.  It is
-// warp-specialised: 16 warps generate the chunk's 128 x 64 tile of G into a
-// 2-stage ring, and one warp takes each chunk's A tile with one bulk copy into
-// a 5-stage ring (issued four chunks ahead) and issues 4 MMAs of 128 x N x 16
-// (K = 16 steps) per chunk; the roles meet only at mbarriers.  Every A tile is
-// read by the d / 128 row-tile CTAs of its K range, mostly from L2.
+// Two kernels.  gauss_convert streams [A | b] once and writes ready-made MMA
+// operand tiles, one per (chunk of KT rows, 256-column tile), in the canonical
+// K-major layout without swizzle (8 x 16-byte core matrices: element (column
+// nn, row k) at ((nn/8)*(KT/8) + k/8)*128 + (nn%8)*16 + (k%8)*2), beside the
+// chunk's KT b values as FP32.  A is written as T BF16 terms, T = 1, 2 or 3:
+// term 1 is A rounded to BF16 (round to nearest even), term t + 1 is the
+// rounding of what terms 1..t leave over; each remainder is exact in FP32
+// (Sterbenz), and three terms hold an FP32 value exactly (8 + 8 + 8
+// significant bits), so T = 3 multiplies the FP32 A itself.  gauss_umma then
+// never touches FP32 A.  It is warp-specialised: 16 warps generate the chunk's
+// 128 x KT tile of G into a 2-stage ring, and one warp takes each chunk's
+// tile with bulk copies into a ring of A stages (issued stages - 1 chunks
+// ahead) and issues T MMAs of 128 x N x 16 per K = 16 step, all T with the
+// same G operand; the roles meet only at mbarriers.  Every A tile is read by
+// the d / 128 row-tile CTAs of its K range, mostly from L2.  One term uses
+// chunks of KT = 64 rows; split A uses KT = 32 so that T-fold tiles still
+// leave room for a ring of A stages in shared memory.
 //
 // G: one hash per (row, 8 consecutive k) gives 8 lookups in a per-bank copy of
 // the FP32 table and one 16-byte store; the b column is accumulated on the CUDA
 // cores from the same looked-up values.
 //
 // Accumulation.  The tensor cores add into the TMEM accumulator in FP32
-// without round-to-nearest (measured: relative error ~2^-24 per accumulated K
-// = 16 step, growing linearly with the steps of one accumulation run).  So the
-// accumulator D (TMEM columns 0..255) only ever holds kUFlush chunks (16 MMA
-// steps): then the CTA's warps add D into a running FP32 sum S held in TMEM
-// columns 256..511 (tcgen05.ld of both, round-to-nearest adds in registers,
-// tcgen05.st of S) and the next chunk restarts D.  The epilogue adds D and S,
-// scales by 1/sqrt(d) and adds into SA / Sb with FP32 reductions (the K range
-// is split over CTAs).
+// without round-to-nearest (measured: relative error ~2^-24 per accumulated
+// MMA, growing linearly with the MMAs of one accumulation run).  So the
+// accumulator D (TMEM columns 0..255) only ever holds about 16 MMAs: then the
+// CTA's warps add D into a running FP32 sum S held in TMEM columns 256..511
+// (tcgen05.ld of both, round-to-nearest adds in registers, tcgen05.st of S)
+// and the next chunk restarts D.  The epilogue adds D and S, scales by
+// 1/sqrt(d) and stores the CTA's partial into its K split's slice of the
+// workspace; gauss_reduce adds the slices in split order.
 // Waits are bounded; on expiry the CTA records an error, lets its issued
 // copies and MMAs land (bounded), frees its TMEM and returns.
 constexpr int kUG = 128;          // G rows per CTA (one M = 128 tile)
-constexpr int kUKT = 64;          // K rows per chunk
 constexpr int kUN = 256;          // max columns per CTA
-constexpr int kUKC = kUKT / 8;    // core matrices along K
-constexpr int kUGStages = 2;      // G tile ring: chunk c + 1 is generated while chunk c's MMAs run
-constexpr int kUBStages = 5;      // A tile ring: copies run four chunks ahead
-constexpr uint32_t kUStageA = kUG * kUKT * 2;   // 16 KB: G tile
-constexpr uint32_t kUStageB = kUN * kUKT * 2;   // 32 KB: A tile (BF16)
-constexpr uint32_t kUStageBb = kUKT * 4;        // 256 B: b values of the chunk
-constexpr uint32_t kUBStage = kUStageB + kUStageBb;             // one A tile stage (16-byte multiple)
-constexpr size_t kUTileBytes = (size_t)kUStageB + kUStageBb;   // one converted (chunk, tile) in the workspace
-constexpr uint32_t kUSum = 256;                 // TMEM column of the running sum S
+constexpr uint32_t kUSum = 256;   // TMEM column of the running sum S
 constexpr long long kUWait = 1LL << 24;
-constexpr int kUFlush = 4;                      // chunks per accumulation run (16 MMA steps)
+constexpr int kUFlushMmas = 16;   // MMAs per accumulation run in D
+
+// Shape of the variant with T BF16 terms of A, G ring depth GS and A ring depth BS.
+template <int T, int GS = 2, int BS = (T == 3 ? 3 : 5)>
+struct GShape {
+  static constexpr int KT = T == 1 ? 64 : 32;             // K rows per chunk
+  static constexpr int KC = KT / 8;                       // core matrices along K
+  static constexpr int GStages = GS;                      // G ring: chunks generated ahead of their MMAs
+  static constexpr int BStages = BS;                      // A ring
+  static constexpr uint32_t StageA = kUG * KT * 2;        // G tile (BF16)
+  static constexpr uint32_t Term = kUN * KT * 2;          // one BF16 term of the A tile
+  static constexpr uint32_t StageBb = KT * 4;             // b values of the chunk (FP32)
+  static constexpr uint32_t BStage = T * Term + StageBb;  // one A stage = one converted tile (16-byte multiple)
+  static constexpr int Flush = kUFlushMmas / (T * KT / 16) > 0 ? kUFlushMmas / (T * KT / 16) : 1;  // chunks per run
+  static constexpr size_t Smem = (size_t)GStages * StageA + (size_t)BStages * BStage + (size_t)kGaussLevels * 32 * 4;
+  static_assert(BStage % 16 == 0 && Smem <= 227 * 1024, "A stages must fit in shared memory");
+};
 
 SNS_D uint32_t u_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-SNS_D uint32_t kmaj_off(int r, int k) { return (uint32_t)(((r >> 3) * kUKC + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2); }
+template <int KC>
+SNS_D uint32_t kmaj_off(int r, int k) { return (uint32_t)(((r >> 3) * KC + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2); }
+template <int KC>
 SNS_D uint64_t u_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;              // LBO: next core matrix along K
-  d |= (uint64_t)(((kUKC * 128u) >> 4) & 0x3FFF) << 32;     // SBO: next 8-row group
+  d |= (uint64_t)(((KC * 128u) >> 4) & 0x3FFF) << 32;       // SBO: next 8-row group
   d |= (uint64_t)1 << 46;                                   // descriptor version
   return d;                                                 // no swizzle
 }
@@ -246,23 +263,40 @@ struct RingPos {
   }
 };
 
+// The T BF16 terms of an FP32 value: x[0] = RN(v), x[t] = RN(v - x[0] - ..
+// - x[t-1]) (every remainder exact in FP32).  Returns x[0] + .. + x[T-1] as
+// FP32 (exact: v itself for T = 3 in the normal range).
+template <int T>
+SNS_D float bf16_terms(float v, float (&x)[T]) {
+  float rem = v, sum = 0.f;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    x[t] = __bfloat162float(__float2bfloat16_rn(rem));
+    rem -= x[t];
+    sum += x[t];
+  }
+  return sum;
+}
+
 // [A | b] -> BF16 operand tiles.  Tile (chunk c, column tile z) lives at
-// tiles + (c * ntiles + z) * kUTileBytes: the K-major BF16 block of rows
-// 64c .. 64c + 63 and columns 256z .. 256z + npad_z - 1 (zero past m and n),
-// then (z = 0 only meaningful) the chunk's 64 b values rounded to BF16, as FP32.
-// A block converts whole tiles; a thread takes 8 rows x 4 columns (16-byte
-// loads that consecutive threads make for consecutive column quads) and writes
-// the 4 columns' 8-row runs as four 16-byte stores.
+// tiles + (c * ntiles + z) * BStage: T K-major BF16 blocks (one per term) of
+// rows KT c .. KT c + KT - 1 and columns 256z .. 256z + 255 (zero past m and
+// n), then (z = 0 only meaningful) the chunk's KT b values as the sum of their
+// T terms, in FP32.  A block converts whole tiles; a thread takes 8 rows x 4
+// columns (16-byte loads that consecutive threads make for consecutive column
+// quads) and writes each term's 4 columns' 8-row runs as 16-byte stores.
+template <int T>
 __global__ void __launch_bounds__(256)
 gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
               int64_t nchunks, int64_t ntiles, uint8_t* __restrict__ tiles) {
+  using S = GShape<T>;
   const bool vec = (lda & 3) == 0 && ((uintptr_t)A & 15) == 0;
   const int64_t units = nchunks * ntiles;
   for (int64_t ct = blockIdx.x; ct < units; ct += gridDim.x) {
     const int64_t c = ct / ntiles, z = ct - c * ntiles;
-    uint8_t* tile = tiles + (size_t)ct * kUTileBytes;
-    const int64_t r0 = c * kUKT;
-    for (int t = threadIdx.x; t < kUKC * (kUN / 4); t += blockDim.x) {
+    uint8_t* tile = tiles + (size_t)ct * S::BStage;
+    const int64_t r0 = c * S::KT;
+    for (int t = threadIdx.x; t < S::KC * (kUN / 4); t += blockDim.x) {
       const int nn = 4 * (t % (kUN / 4)), k8 = t / (kUN / 4);
       const int64_t col = z * kUN + nn;
       float f[8][4];
@@ -282,18 +316,25 @@ gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict_
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        uint4 w;
-        w.x = pack_bf16(f[0][q], f[1][q]);
-        w.y = pack_bf16(f[2][q], f[3][q]);
-        w.z = pack_bf16(f[4][q], f[5][q]);
-        w.w = pack_bf16(f[6][q], f[7][q]);
-        *reinterpret_cast<uint4*>(tile + kmaj_off(nn + q, 8 * k8)) = w;
+        float x[8][T];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bf16_terms<T>(f[j][q], x[j]);
+#pragma unroll
+        for (int p = 0; p < T; ++p) {
+          uint4 w;
+          w.x = pack_bf16(x[0][p], x[1][p]);
+          w.y = pack_bf16(x[2][p], x[3][p]);
+          w.z = pack_bf16(x[4][p], x[5][p]);
+          w.w = pack_bf16(x[6][p], x[7][p]);
+          *reinterpret_cast<uint4*>(tile + (size_t)p * S::Term + kmaj_off<S::KC>(nn + q, 8 * k8)) = w;
+        }
       }
     }
-    if (threadIdx.x < kUKT) {
+    if (threadIdx.x < S::KT) {
       const int64_t row = r0 + threadIdx.x;
-      reinterpret_cast<float*>(tile + kUStageB)[threadIdx.x] =
-          (row < m && z == 0) ? __bfloat162float(__float2bfloat16_rn(__ldg(b + row))) : 0.f;
+      float x[T];
+      reinterpret_cast<float*>(tile + (size_t)T * S::Term)[threadIdx.x] =
+          (row < m && z == 0) ? bf16_terms<T>(__ldg(b + row), x) : 0.f;
     }
   }
 }
@@ -306,22 +347,25 @@ gauss_convert(const float* __restrict__ A, int64_t lda, const float* __restrict_
 // stage may be refilled; two commits after each chunk).  Phases never alias:
 // a barrier's next phase cannot complete before its current one was waited for.
 constexpr int kUGenWarps = 16;   // 32 would exceed 1024 threads with the MMA warp
+template <int T, int GS, int BS>
 __global__ void __launch_bounds__(32 * (kUGenWarps + 1), 1)
 gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t n, int64_t d, uint64_t s0,
            const uint16_t* __restrict__ table, int64_t kchunk, float scale, float* __restrict__ part,
            float* __restrict__ partb, int* __restrict__ err, int flush_every) {
+  using S = GShape<T, GS, BS>;
+  constexpr int KT = S::KT, GST = S::GStages, BST = S::BStages;
   extern __shared__ __align__(1024) uint8_t usm[];
-  // G stages (kUStageA each), then A stages (A tile kUStageB, b values kUStageBb)
-  auto stA = [&](int s) { return usm + (size_t)s * kUStageA; };
-  auto stB = [&](int s) { return usm + (size_t)kUGStages * kUStageA + (size_t)s * kUBStage; };
-  auto stb = [&](int s) { return reinterpret_cast<const float*>(stB(s) + kUStageB); };
+  // G stages (StageA each), then A stages (T terms, then the b values)
+  auto stA = [&](int s) { return usm + (size_t)s * S::StageA; };
+  auto stB = [&](int s) { return usm + (size_t)GST * S::StageA + (size_t)s * S::BStage; };
+  auto stb = [&](int s) { return reinterpret_cast<const float*>(stB(s) + (size_t)T * S::Term); };
   // the table as FP32, replicated once per bank: entry j of lane l at sT[j * 32 + l],
   // so a warp's 32 random lookups never conflict
-  float* sT = reinterpret_cast<float*>(usm + (size_t)kUGStages * kUStageA + (size_t)kUBStages * kUBStage);
-  __shared__ __align__(8) uint64_t tile_ready[kUBStages];     // copy of chunk c landed (stage c mod kUBStages)
-  __shared__ __align__(8) uint64_t bfree[kUBStages];          // MMAs of chunk c done (A stage reusable)
-  __shared__ __align__(8) uint64_t g_ready[kUGStages];        // G tile of chunk c written (stage c mod kUGStages)
-  __shared__ __align__(8) uint64_t gfree[kUGStages];          // MMAs of chunk c done (G stage reusable)
+  float* sT = reinterpret_cast<float*>(usm + (size_t)GST * S::StageA + (size_t)BST * S::BStage);
+  __shared__ __align__(8) uint64_t tile_ready[BST];     // copy of chunk c landed (stage c mod BST)
+  __shared__ __align__(8) uint64_t bfree[BST];          // MMAs of chunk c done (A stage reusable)
+  __shared__ __align__(8) uint64_t g_ready[GST];        // G tile of chunk c written (stage c mod GST)
+  __shared__ __align__(8) uint64_t gfree[GST];          // MMAs of chunk c done (G stage reusable)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -332,18 +376,19 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   const int ncols = (int)min((int64_t)kUN, n - col0);
   const int npad = ((ncols + 15) / 16) * 16;                   // MMA N (multiple of 16)
   const bool with_b = (z == 0);
-  const int64_t i_begin = (int64_t)blockIdx.y * kchunk;        // a multiple of kUKT
+  const int64_t i_begin = (int64_t)blockIdx.y * kchunk;        // a multiple of KT
   const int64_t i_end = min(m, i_begin + kchunk);
-  const int64_t nchunks = (i_end - i_begin + kUKT - 1) / kUKT;
-  const int64_t c_base = i_begin / kUKT;                       // global chunk index of chunk 0
-  const uint32_t copy_bytes = (uint32_t)npad * 128u + (with_b ? kUStageBb : 0u);
+  const int64_t nchunks = (i_end - i_begin + KT - 1) / KT;
+  const int64_t c_base = i_begin / KT;                         // global chunk index of chunk 0
+  const uint32_t term_bytes = (uint32_t)npad * KT * 2u;        // the used prefix of one term block
+  const uint32_t copy_bytes = T * term_bytes + (with_b ? S::StageBb : 0u);
   for (int j = tid; j < kGaussLevels * 32; j += blockDim.x) sT[j] = __uint_as_float((uint32_t)table[j >> 5] << 16);
   if (tid == 0) {
-    for (int s = 0; s < kUBStages; ++s) {
+    for (int s = 0; s < BST; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&tile_ready[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&bfree[s])) : "memory");
     }
-    for (int s = 0; s < kUGStages; ++s) {
+    for (int s = 0; s < GST; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(u_smem(&g_ready[s])), "r"(kUGenWarps) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(u_smem(&gfree[s])) : "memory");
     }
@@ -418,23 +463,24 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   __shared__ long long s_issued;                               // chunks whose MMAs the MMA warp issued
   if (mma_warp) {
     if (lane == 0) {
-      // chunk c's tile (and b values) into A stage c mod kUBStages
+      // chunk c's tile (T terms and the b values) into A stage c mod BST
       int64_t copied = 0;
-      RingPos<kUBStages> cpos;                                   // chunk `copied` in the A ring
+      RingPos<BST> cpos;                                         // chunk `copied` in the A ring
       auto issue_copy = [&](int64_t c) {
         const int s = cpos.s;
         cpos.next();
-        const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * kUTileBytes;
+        const uint8_t* src = tiles + (size_t)((c_base + c) * ntiles + z) * S::BStage;
         u_expect(&tile_ready[s], copy_bytes);
-        u_copy(stB(s), src, (uint32_t)npad * 128u, &tile_ready[s]);
-        if (with_b) u_copy(stB(s) + kUStageB, src + kUStageB, kUStageBb, &tile_ready[s]);
+#pragma unroll
+        for (int p = 0; p < T; ++p) u_copy(stB(s) + (size_t)p * S::Term, src + (size_t)p * S::Term, term_bytes, &tile_ready[s]);
+        if (with_b) u_copy(stB(s) + (size_t)T * S::Term, src + (size_t)T * S::Term, S::StageBb, &tile_ready[s]);
         copied = c + 1;
       };
-      for (int64_t c = 0; c < kUBStages - 1 && c < nchunks; ++c) issue_copy(c);
+      for (int64_t c = 0; c < BST - 1 && c < nchunks; ++c) issue_copy(c);
       int64_t issued = 0;
       int since = 0;                                             // chunks in D since the last flush
-      RingPos<kUGStages> g;                                      // chunk c in the G ring
-      RingPos<kUBStages> t, tp;                                  // chunk c and c - 1 in the A ring
+      RingPos<GST> g;                                            // chunk c in the G ring
+      RingPos<BST> t, tp;                                        // chunk c and c - 1 in the A ring
       for (int64_t c = 0; c < nchunks; ++c) {
         const int sg = g.s, s = t.s;
         if (!u_wait(&g_ready[sg], g.ph)) { fail(); break; }
@@ -442,15 +488,18 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
         if (since == flush_every) since = 0;                     // D was moved into S
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int ks = 0; ks < kUKT / 16; ++ks) {
-          const uint64_t ad = u_desc(u_smem(stA(sg)) + (uint32_t)ks * 256u);
-          const uint64_t bd = u_desc(u_smem(stB(s)) + (uint32_t)ks * 256u);
-          const uint32_t acc = (since > 0 || ks > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+        for (int ks = 0; ks < KT / 16; ++ks) {
+          const uint64_t ad = u_desc<S::KC>(u_smem(stA(sg)) + (uint32_t)ks * 256u);
+#pragma unroll
+          for (int p = 0; p < T; ++p) {
+            const uint64_t bd = u_desc<S::KC>(u_smem(stB(s)) + (uint32_t)p * S::Term + (uint32_t)ks * 256u);
+            const uint32_t acc = (since > 0 || ks > 0 || p > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          u_smem(&gfree[sg]))
@@ -460,8 +509,8 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
                      : "memory");
         issued = c + 1;
         ++since;
-        // the copy kUBStages - 1 chunks ahead goes into the A stage chunk c - 1 used
-        const int64_t cn = c + kUBStages - 1;
+        // the copy BST - 1 chunks ahead goes into the A stage chunk c - 1 used
+        const int64_t cn = c + BST - 1;
         if (cn < nchunks) {
           if (c >= 1 && !u_wait(&bfree[tp.s], tp.ph)) {
             fail();
@@ -475,21 +524,21 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
       }
       s_issued = issued;
       // the last issued chunk's commit tracks all earlier MMAs; TMEM stays allocated until then
-      if (issued > 0 && !u_wait(&bfree[(issued - 1) % kUBStages], (uint32_t)(((issued - 1) / kUBStages) & 1)))
+      if (issued > 0 && !u_wait(&bfree[(issued - 1) % BST], (uint32_t)(((issued - 1) / BST) & 1)))
         fail();
       // copies issued but never consumed (failure path) land before the CTA exits: a
       // stage's copies complete in order, so its last one covers the earlier ones
-      for (int64_t c = max((int64_t)0, copied - kUBStages); c < copied; ++c)
-        if (!u_wait(&tile_ready[c % kUBStages], (uint32_t)((c / kUBStages) & 1))) fail();
+      for (int64_t c = max((int64_t)0, copied - BST); c < copied; ++c)
+        if (!u_wait(&tile_ready[c % BST], (uint32_t)((c / BST) & 1))) fail();
     }
     __syncwarp();
   } else {
-    // generator warps.  Thread (r, q) hashes outputs (i_begin / 8 + 8 c + q) d + r_base + r
+    // generator warps.  Thread (r, q) hashes outputs (i_begin / 8 + (KT / 8) c + q) d + r_base + r
     // of the stream, q = tid / 128 + e * (threads / 128): the counter state advances by
-    // 8 d gamma per chunk
+    // (KT / 8) d gamma per chunk
     constexpr int kGenThreads = 32 * kUGenWarps;
-    constexpr int kPer = (kUKT / 8) / (kGenThreads / kUG);       // hashes per thread and chunk
-    static_assert(kPer >= 1 && kPer * (kGenThreads / kUG) == kUKT / 8, "generator threads must tile the chunk");
+    constexpr int kPer = (KT / 8) / (kGenThreads / kUG);         // hashes per thread and chunk
+    static_assert(kPer >= 1 && kPer * (kGenThreads / kUG) == KT / 8, "generator threads must tile the chunk");
     const int r = tid & (kUG - 1);
     uint64_t state[kPer];
 #pragma unroll
@@ -497,22 +546,22 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
       const uint64_t q = (uint64_t)((tid >> 7) + e * (kGenThreads / kUG));
       state[e] = s0 + (((uint64_t)(i_begin >> 3) + q) * (uint64_t)d + (uint64_t)(r_base + r) + 1) * kGamma;
     }
-    const uint64_t state_step = 8ull * (uint64_t)d * kGamma;
+    const uint64_t state_step = (uint64_t)(KT / 8) * (uint64_t)d * kGamma;
     int since = 0;                                               // chunks in D since the last flush
-    RingPos<kUGStages> g, gp;                                    // chunk c and c - 1 in the G ring
-    RingPos<kUBStages> t;                                        // chunk c in the A ring
+    RingPos<GST> g, gp;                                          // chunk c and c - 1 in the G ring
+    RingPos<BST> t;                                              // chunk c in the A ring
     for (int64_t c = 0; c < nchunks; ++c) {
       const int sg = g.s, s = t.s;
-      // G stage sg is free once chunk c - kUGStages's MMAs are done (the phase before
+      // G stage sg is free once chunk c - GST's MMAs are done (the phase before
       // g.ph); the b values come with the tile
-      const bool ok = (c < kUGStages || u_wait(&gfree[sg], g.ph ^ 1u)) && u_wait(&tile_ready[s], t.ph);
+      const bool ok = (c < GST || u_wait(&gfree[sg], g.ph ^ 1u)) && u_wait(&tile_ready[s], t.ph);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) fail();
         break;
       }
       uint8_t* sA = stA(sg);
-      // G tile and b column: task (row r, group q of 8 consecutive k), two per
-      // thread (q and q + 4): one hash gives the row's 8 entries (byte t of output
+      // G tile and b column: task (row r, group q of 8 consecutive k), kPer per
+      // thread: one hash gives the row's 8 entries (byte t of output
       // (i div 8) d + k is entry i = 8 (i0 / 8 + q) + t), 8 conflict-free table
       // lookups, one 16-byte store into the K-major tile, and 8 FMAs of the b
       // column in the same registers.  Rows past d and columns past m need no
@@ -538,7 +587,7 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
           w.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
           w.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
           w.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
-          *reinterpret_cast<uint4*>(sA + kmaj_off(r, 8 * q)) = w;
+          *reinterpret_cast<uint4*>(sA + kmaj_off<S::KC>(r, 8 * q)) = w;
           if (with_b) {
             const float4 b0 = *reinterpret_cast<const float4*>(bc + 8 * q);
             const float4 b1 = *reinterpret_cast<const float4*>(bc + 8 * q + 4);
@@ -584,7 +633,7 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   if (!mma_warp && issued > 0 && !s_fail) {
     // the last issued chunk's commit tracks all earlier MMAs
     const int64_t cl = issued - 1;
-    if (__all_sync(0xffffffffu, u_wait(&gfree[cl % kUGStages], (uint32_t)((cl / kUGStages) & 1)))) {
+    if (__all_sync(0xffffffffu, u_wait(&gfree[cl % GST], (uint32_t)((cl / GST) & 1)))) {
       if (issued == nchunks) tmem_flush(true);
     } else if (lane == 0) {
       fail();
@@ -596,24 +645,25 @@ gauss_umma(const uint8_t* __restrict__ tiles, int64_t ntiles, int64_t m, int64_t
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
 }
 
-size_t gauss_umma_smem() {
-  return (size_t)kUGStages * kUStageA + (size_t)kUBStages * kUBStage + (size_t)kGaussLevels * 32 * 4;
+static int gauss_kt(int terms) { return terms == 3 ? GShape<3>::KT : terms == 2 ? GShape<2>::KT : GShape<1>::KT; }
+static size_t gauss_tile_bytes(int terms) {
+  return terms == 3 ? GShape<3>::BStage : terms == 2 ? GShape<2>::BStage : GShape<1>::BStage;
 }
 
 // Launch shape of gauss_umma: row tiles of G x K splits x column tiles, one
-// CTA per SM; K ranges in whole chunks.
+// CTA per SM; K ranges in whole chunks of kt rows.
 struct GaussGrid {
   int64_t mtiles, ntiles, ksplit, kchunk, nchunks;
 };
-static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d) {
+static GaussGrid gauss_grid(int64_t m, int64_t n, int64_t d, int64_t kt) {
   GaussGrid g;
   g.mtiles = (d + kUG - 1) / kUG;
   g.ntiles = (n + kUN - 1) / kUN;
   g.ksplit = std::max<int64_t>(1, (int64_t)num_sms() / std::max<int64_t>(1, g.mtiles * g.ntiles));
   g.kchunk = (m + g.ksplit - 1) / g.ksplit;
-  g.kchunk = ((g.kchunk + kUKT - 1) / kUKT) * kUKT;
+  g.kchunk = ((g.kchunk + kt - 1) / kt) * kt;
   g.ksplit = (m + g.kchunk - 1) / g.kchunk;
-  g.nchunks = (m + kUKT - 1) / kUKT;
+  g.nchunks = (m + kt - 1) / kt;
   return g;
 }
 constexpr size_t kGaussTilesOffset = 8192 + 256;
@@ -622,17 +672,18 @@ constexpr int kGaussGroups = 32 * kUGenWarps / kUG;     // b-column partials per
 // [A | b] tiles, then the per-K-split partial tiles of SA (d x n each) and of
 // Sb (kGaussGroups x d each), sized for at most kSizingSms K splits per tile.
 constexpr int64_t kSizingSms = 256;
-static int64_t gauss_ksplit_bound(int64_t m, int64_t n, int64_t d) {
+static int64_t gauss_ksplit_bound(int64_t m, int64_t n, int64_t d, int64_t kt) {
   const int64_t tiles = ((d + kUG - 1) / kUG) * ((n + kUN - 1) / kUN);
-  return std::max<int64_t>(1, std::min<int64_t>(kSizingSms / std::max<int64_t>(1, tiles), (m + kUKT - 1) / kUKT));
+  return std::max<int64_t>(1, std::min<int64_t>(kSizingSms / std::max<int64_t>(1, tiles), (m + kt - 1) / kt));
 }
-static size_t gauss_part_offset(int64_t m, int64_t n) {
-  const int64_t nchunks = (m + kUKT - 1) / kUKT, ntiles = (n + kUN - 1) / kUN;
-  return kGaussTilesOffset + (size_t)nchunks * ntiles * kUTileBytes;
+static size_t gauss_part_offset(int64_t m, int64_t n, int terms) {
+  const int64_t kt = gauss_kt(terms);
+  const int64_t nchunks = (m + kt - 1) / kt, ntiles = (n + kUN - 1) / kUN;
+  return kGaussTilesOffset + (size_t)nchunks * ntiles * gauss_tile_bytes(terms);
 }
-size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d) {
-  const size_t ks = (size_t)gauss_ksplit_bound(m, n, d);
-  return gauss_part_offset(m, n) + ks * (size_t)d * n * 4 + ks * kGaussGroups * (size_t)d * 4;
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d, int terms) {
+  const size_t ks = (size_t)gauss_ksplit_bound(m, n, d, gauss_kt(terms));
+  return gauss_part_offset(m, n, terms) + ks * (size_t)d * n * 4 + ks * kGaussGroups * (size_t)d * 4;
 }
 
 // SA and Sb as the sums of the K splits' partials, in split order (the result
@@ -656,61 +707,81 @@ gauss_reduce(const float* __restrict__ part, const float* __restrict__ partb, in
   }
 }
 
-sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
-                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (!ws || ws_bytes < gauss_ws_bytes(a.m, a.n, d)) return SNS_ENOMEM;
+template <int T, int GS, int BS>
+static sns_status gauss_launch(const uint8_t* tiles, const GaussGrid& gg, const DenseArgs& a, int64_t d, uint64_t s0,
+                               const uint16_t* dtab, float scale, float* part, float* partb, int* err,
+                               cudaStream_t st) {
+  using S = GShape<T, GS, BS>;
+  SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma<T, GS, BS>));
+  dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
+  {
+    SNS_PROF(K_GAUSS, st);
+    gauss_umma<T, GS, BS><<<grid, 32 * (kUGenWarps + 1), S::Smem, st>>>(
+        tiles, gg.ntiles, a.m, a.n, d, s0, dtab, gg.kchunk, scale, part, partb, err, S::Flush);
+  }
+  SNS_LAUNCH_CHECK();
+  return SNS_OK;
+}
+
+template <int T>
+static sns_status gauss_tensor(const DenseArgs& a, int64_t d, uint64_t s0, const uint16_t* dtab, float* SA,
+                               int64_t ldsa, float* Sb, int64_t sbs, void* ws, int* err, cudaStream_t st) {
+  using S = GShape<T>;
+  const GaussGrid gg = gauss_grid(a.m, a.n, d, S::KT);
+  uint8_t* tiles = static_cast<uint8_t*>(ws) + kGaussTilesOffset;
+  {
+    SNS_PROF(K_GAUSS, st);
+    gauss_convert<T><<<num_sms() * 8, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda,
+                                                    static_cast<const float*>(a.b), a.m, a.n, gg.nchunks, gg.ntiles,
+                                                    tiles);
+  }
+  SNS_LAUNCH_CHECK();
+  if (gg.ksplit > gauss_ksplit_bound(a.m, a.n, d, S::KT)) return SNS_EINVAL;   // more SMs than the sizing bound
+  const float scale = (float)(1.0 / std::sqrt((double)d));
+  float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + gauss_part_offset(a.m, a.n, T));
+  float* partb = part + (size_t)gg.ksplit * d * a.n;
+  const sns_status r = gauss_launch<T, S::GStages, S::BStages>(tiles, gg, a, d, s0, dtab, scale, part, partb, err, st);
+  if (r != SNS_OK) return r;
+  {
+    SNS_PROF(K_GAUSS, st);
+    gauss_reduce<<<num_sms() * 4, 256, 0, st>>>(part, partb, gg.ksplit, d, a.n, SA, ldsa, Sb, sbs);
+  }
+  SNS_LAUNCH_CHECK();
+  return SNS_OK;
+}
+
+sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, int terms, float* SA, int64_t ldsa,
+                             float* Sb, int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (terms < 1 || terms > 3) return SNS_EINVAL;
+  if (!ws || ws_bytes < gauss_ws_bytes(a.m, a.n, d, terms)) return SNS_ENOMEM;
   uint16_t* dtab = static_cast<uint16_t*>(ws);
   SNS_CUDA_TRY(cudaMemcpyAsync(dtab, table_host(), kGaussLevels * 2, cudaMemcpyHostToDevice, st));
-  // SNSOLVE_GAUSS=simt selects the CUDA-core kernel
+  // SNSOLVE_GAUSS=simt selects the CUDA-core kernel (one BF16 term only)
   static int use_simt = -1;
   if (use_simt < 0) {
     const char* e = getenv("SNSOLVE_GAUSS");
     use_simt = (e && e[0] == 's') ? 1 : 0;
   }
-  if (use_simt) {                                      // it adds into SA and Sb
-    if (ldsa == a.n) {
-      SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
-    } else {
-      SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
-    }
-    if (sbs == 1) {
-      SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
-    } else {
-      SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
-    }
-  }
   int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + gauss_err_offset());
   SNS_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
   const uint64_t s0 = shift_state(stream_state(seed, kStreamGaussian), (uint64_t)(a.row0 / 8) * (uint64_t)d);
-  if (!use_simt) {
-    const GaussGrid gg = gauss_grid(a.m, a.n, d);
-    uint8_t* tiles = static_cast<uint8_t*>(ws) + kGaussTilesOffset;
-    {
-      SNS_PROF(K_GAUSS, st);
-      gauss_convert<<<num_sms() * 8, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda,
-                                                   static_cast<const float*>(a.b), a.m, a.n, gg.nchunks, gg.ntiles,
-                                                   tiles);
+  if (!use_simt || terms > 1) {
+    switch (terms) {
+      case 1: return gauss_tensor<1>(a, d, s0, dtab, SA, ldsa, Sb, sbs, ws, err, st);
+      case 2: return gauss_tensor<2>(a, d, s0, dtab, SA, ldsa, Sb, sbs, ws, err, st);
+      default: return gauss_tensor<3>(a, d, s0, dtab, SA, ldsa, Sb, sbs, ws, err, st);
     }
-    SNS_LAUNCH_CHECK();
-    SNS_CUDA_TRY(raise_smem_limit((const void*)gauss_umma));
-    if (gg.ksplit > gauss_ksplit_bound(a.m, a.n, d)) return SNS_EINVAL;   // more SMs than the sizing bound
-    dim3 grid((unsigned)gg.mtiles, (unsigned)gg.ksplit, (unsigned)gg.ntiles);
-    const float scale = (float)(1.0 / std::sqrt((double)d));
-    float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + gauss_part_offset(a.m, a.n));
-    float* partb = part + (size_t)gg.ksplit * d * a.n;
-    {
-      SNS_PROF(K_GAUSS, st);
-      gauss_umma<<<grid, 32 * (kUGenWarps + 1), gauss_umma_smem(), st>>>(tiles, gg.ntiles, a.m, a.n, d, s0, dtab,
-                                                                         gg.kchunk, scale, part, partb, err,
-                                                                         kUFlush);
-    }
-    SNS_LAUNCH_CHECK();
-    {
-      SNS_PROF(K_GAUSS, st);
-      gauss_reduce<<<num_sms() * 4, 256, 0, st>>>(part, partb, gg.ksplit, d, a.n, SA, ldsa, Sb, sbs);
-    }
-    SNS_LAUNCH_CHECK();
-    return SNS_OK;
+  }
+  // the SIMT kernel adds into SA and Sb
+  if (ldsa == a.n) {
+    SNS_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)d * a.n * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * 4, 0, (size_t)a.n * 4, (size_t)d, st));
+  }
+  if (sbs == 1) {
+    SNS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)d * 4, st));
+  } else {
+    SNS_CUDA_TRY(cudaMemset2DAsync(Sb, (size_t)sbs * 4, 0, 4, (size_t)d, st));
   }
   const int64_t q = a.n + 1;
   const int64_t tiles = ((d + kGMt - 1) / kGMt) * ((q + kGNt - 1) / kGNt);
@@ -721,9 +792,8 @@ sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float
   dim3 grid((unsigned)tiles, (unsigned)ksplit);
   {
     SNS_PROF(K_GAUSS, st);
-  gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n, d,
-                                   s0, dtab, kchunk,
-                                   (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
+    gauss_simt<<<grid, 256, 0, st>>>(static_cast<const float*>(a.A), a.lda, static_cast<const float*>(a.b), a.m, a.n,
+                                     d, s0, dtab, kchunk, (float)(1.0 / std::sqrt((double)d)), SA, ldsa, Sb, sbs);
   }
   SNS_LAUNCH_CHECK();
   return SNS_OK;

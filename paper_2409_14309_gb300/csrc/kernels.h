@@ -81,13 +81,13 @@ sns_status srht_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, void* 
 sns_status debug_srht_sample(int64_t mp, int64_t d, uint64_t seed, int64_t* out, void* ws, size_t ws_bytes,
                              cudaStream_t st);
 
-// Gaussian.
-size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d);
+// Gaussian.  `terms` (1..3): BF16 terms of [A | b] in the tensor-core product.
+size_t gauss_ws_bytes(int64_t m, int64_t n, int64_t d, int terms);
 // Byte offset in the Gaussian workspace of the error word its bounded waits
 // set (0 after a sketch that completed).
 size_t gauss_err_offset();
-sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, float* SA, int64_t ldsa, float* Sb,
-                             int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
+sns_status gauss_apply_dense(const DenseArgs& a, int64_t d, uint64_t seed, int terms, float* SA, int64_t ldsa,
+                             float* Sb, int64_t sbs, void* ws, size_t ws_bytes, cudaStream_t st);
 // Levels of the BF16 normal-quantile table T of the Gaussian sketch.
 constexpr int kGaussLevels = 256;
 void gauss_table_host(uint16_t* out);

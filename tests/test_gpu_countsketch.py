@@ -228,22 +228,47 @@ def test_empty_buckets_are_written_as_zero(variant, m, n, d):
     assert rel_fro(Sb.cpu().numpy(), OS.countsketch_apply(b, d, 9), scale) <= TOL32
 
 
+@pytest.mark.parametrize("terms", [1, 2, 3])
 @pytest.mark.parametrize("m,n,d", [(777, 1, 5), (3000, 20, 80), (20000, 100, 333), (50000, 256, 1024),
-                                   (10000, 300, 1200)])
-def test_gaussian_sketch_tensor_core(m, n, d):
-    """Gaussian sketch on the tensor cores (BF16 G and BF16-rounded [A | b],
-    FP32 accumulation) against the oracle's FP64 product of the same BF16
-    operands."""
+                                   (10000, 300, 1200), (4133, 257, 300)])
+def test_gaussian_sketch_tensor_core(m, n, d, terms):
+    """Gaussian sketch on the tensor cores (BF16 G and [A | b] as `terms` BF16
+    terms, FP32 accumulation) against the oracle's FP64 product of the same
+    operands (terms = 3: the FP32 values themselves).  The values span
+    exponents so that the lower terms matter."""
     c = ctx()
     rng = np.random.default_rng(m + n)
-    A = rng.standard_normal((m, n)).astype(np.float32)
+    A = (rng.standard_normal((m, n)) * np.exp(rng.uniform(-3, 3, (m, n)))).astype(np.float32)
     b = rng.standard_normal(m).astype(np.float32)
-    SA, Sb = c.sketch(dev(A), dev(b), d, kind="gaussian", seed=13)
-    ref = OS.gaussian_apply(A, d, 13, bf16_operand=True)
-    refb = OS.gaussian_apply(b, d, 13, bf16_operand=True)
+    SA, Sb = c.sketch(dev(A), dev(b), d, kind="gaussian", seed=13, variant=str(terms))
+    ref = OS.gaussian_apply(A, d, 13, terms=terms)
+    refb = OS.gaussian_apply(b, d, 13, terms=terms)
     scale = np.sqrt(np.linalg.norm(ref) ** 2 + np.linalg.norm(refb) ** 2)
     assert rel_fro(SA.cpu().numpy(), ref, scale) <= 1e-6
     assert rel_fro(Sb.cpu().numpy(), refb, scale) <= 1e-6
+    if terms == 3:   # and it is a different product from the one-term sketch
+        one = OS.gaussian_apply(A, d, 13, terms=1)
+        assert rel_fro(one, ref, scale) > 1e-4
+
+
+def test_gaussian_three_terms_reproducible_and_auto_is_one_term():
+    c = ctx()
+    rng = np.random.default_rng(92)
+    A = dev(rng.standard_normal((70000, 96)).astype(np.float32))
+    b = dev(rng.standard_normal(70000).astype(np.float32))
+    SA1, Sb1 = c.sketch(A, b, 384, kind="gaussian", seed=5, variant="3")
+    outs = []
+    for s in (torch.cuda.Stream(), torch.cuda.Stream()):
+        with torch.cuda.stream(s):
+            outs.append(c.sketch(A, b, 384, kind="gaussian", seed=5, variant="3", stream=s))
+    torch.cuda.synchronize()
+    for SA, Sb in outs:
+        assert torch.equal(SA, SA1) and torch.equal(Sb, Sb1)
+    SAa, Sba = c.sketch(A, b, 384, kind="gaussian", seed=5)
+    SAo, Sbo = c.sketch(A, b, 384, kind="gaussian", seed=5, variant="1")
+    assert torch.equal(SAa, SAo) and torch.equal(Sba, Sbo)
+    with pytest.raises(RuntimeError):
+        c.sketch(A, b, 384, kind="gaussian", seed=5, variant="4")
 
 
 def test_gaussian_sketch_bitwise_reproducible():

@@ -83,13 +83,14 @@ def test_full_size_forward_error_follows_eta(problem, x_star):
         assert err <= bound + 100 * 1e6 * 2.0 ** -53, (err, bound)
 
 
-def test_full_size_gaussian_sampled_rows(problem):
+@pytest.mark.parametrize("terms", [1, 3])
+def test_full_size_gaussian_sampled_rows(problem, terms):
     A, b = problem
     c = ctx()
-    SA, Sb = c.sketch(dev(A), dev(b), D, kind="gaussian", seed=1)
+    SA, Sb = c.sketch(dev(A), dev(b), D, kind="gaussian", seed=1, variant=str(terms))
     rows = [0, 7, 8, 31, 32, 500, 1023]
-    ref = OS.gaussian_rows(A, D, 1, rows)
-    refb = OS.gaussian_rows(b, D, 1, rows)
+    ref = OS.gaussian_rows(A, D, 1, rows, terms=terms)
+    refb = OS.gaussian_rows(b, D, 1, rows, terms=terms)
     # FP32 accumulation of 2^20 BF16 products per entry
     assert rel_fro(SA.cpu().numpy()[rows], ref, np.linalg.norm(ref)) <= 1e-6
     assert rel_fro(Sb.cpu().numpy()[rows], refb, np.linalg.norm(refb)) <= 1e-6

@@ -38,8 +38,9 @@ def test_sketch_and_solve_f32_matches_oracle(kind, m, n, d):
     A, b, _ = ill_conditioned_problem(m, n, seed=m + n, kappa=1e3, noise=1e-3)
     x, info = c.lstsq(dev(A), dev(b), d, kind=kind, seed=7)
     assert info.status == 0
-    SA = OS.sketch_apply(kind, A, d, 7)
-    Sb = OS.sketch_apply(kind, b, d, 7)
+    # inside a solve the Gaussian sketch multiplies three BF16 terms of [A | b]
+    SA = OS.sketch_apply(kind, A, d, 7, terms=3)
+    Sb = OS.sketch_apply(kind, b, d, 7, terms=3)
     x_ref, _, _ = OL.sketch_and_solve(SA, Sb)
     err = np.linalg.norm(x.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
     assert err <= _xhat_tol(SA), err
@@ -69,13 +70,14 @@ def test_xhat_parity_at_kappa_1e6(kind):
     the oracle's SA; (3) x^ vs the oracle's x^ lies within the least-squares
     perturbation bound of that SA difference.  The measured error is printed.
     Check (1) needs the sketch inside the solve to be the one fetched here, so it
-    runs for the bitwise-reproducible kinds (sorted CountSketch, SRHT); the
-    Gaussian and sparse sign sketches add with float reductions in a varying
-    order, and at kappa(SA) ~ 1e6 two runs' x^ differ by a few percent."""
+    runs for the bitwise-reproducible kinds (sorted CountSketch, SRHT, the
+    Gaussian with three BF16 terms, as inside a solve); the sparse sign sketch
+    adds with float reductions in a varying order, and at kappa(SA) ~ 1e6 two
+    runs' x^ differ by a few percent."""
     c = ctx()
     m, n, d = 1 << 16, 256, 1024
     A, b, _ = ill_conditioned_problem(m, n, seed=1002, kappa=1e6, noise=1e-4)
-    variant = "4" if kind == "sparse_sign" else "auto"
+    variant = {"sparse_sign": "4", "gaussian": "3"}.get(kind, "auto")
     Ad, bd = dev(A), dev(b)
     SA_g, Sb_g = c.sketch(Ad, bd, d, kind=kind, seed=1, variant=variant)
     x, info = c.lstsq(Ad, bd, d, kind=kind, seed=1, variant=variant)
@@ -86,11 +88,11 @@ def test_xhat_parity_at_kappa_1e6(kind):
     # (1) solve of the GPU's own sketch in FP64 by the oracle
     x_own, _, _ = OL.sketch_and_solve(SA_g, Sb_g)
     e_solve = np.linalg.norm(xg - x_own) / np.linalg.norm(x_own)
-    # (2) the oracle's sketch (BF16-rounded operand for the Gaussian)
+    # (2) the oracle's sketch (three BF16 terms, i.e. the FP32 operand, for the Gaussian)
     if kind == "sparse_sign":
         SA_r, Sb_r = OS.sparse_sign_apply(A, d, 4, 1), OS.sparse_sign_apply(b, d, 4, 1)
     else:
-        SA_r, Sb_r = OS.sketch_apply(kind, A, d, 1), OS.sketch_apply(kind, b, d, 1)
+        SA_r, Sb_r = OS.sketch_apply(kind, A, d, 1, terms=3), OS.sketch_apply(kind, b, d, 1, terms=3)
     scale = np.sqrt(np.linalg.norm(SA_r) ** 2 + np.linalg.norm(Sb_r) ** 2)
     e_sa = np.sqrt(np.linalg.norm(SA_g - SA_r) ** 2 + np.linalg.norm(Sb_g - Sb_r) ** 2) / scale
     # (3) x^ against the oracle's x^
@@ -99,10 +101,41 @@ def test_xhat_parity_at_kappa_1e6(kind):
     bound, kappa = _ls_perturbation_bound(SA_r, Sb_r, SA_g - SA_r, Sb_g - Sb_r)
     print(f"{kind}: kappa(SA) {kappa:.3g}, |SA-SA_ref| {e_sa:.2e}, x^ vs own-SA solve {e_solve:.2e}, "
           f"x^ vs oracle {e_x:.3e} (first-order bound {bound:.3e})")
-    if kind in ("countsketch", "srht"):
+    if kind in ("countsketch", "srht", "gaussian"):
         assert e_solve <= 1e3 * kappa * 2.0 ** -53, e_solve
     assert e_sa <= 1e-6, e_sa
     assert e_x <= max(1e-4, 2.0 * bound), (e_x, bound)
+
+
+def _kappa_ARinv(A, SA):
+    R = np.linalg.qr(SA.astype(np.float64), mode="r")
+    s = np.linalg.svd(np.linalg.solve(R.T, A.astype(np.float64).T).T, compute_uv=False)
+    return s[0] / s[-1]
+
+
+def test_gaussian_split_operand_preconditions_ill_conditioned_A():
+    """At kappa(A) = 1e6 one BF16 term of A perturbs it by ~2^-9 ||A||, so R
+    of that sketch leaves kappa(A R^-1) in the hundreds; three terms (the FP32
+    A) bring it to the level of the other sketches (a few), and the solve,
+    whose auto Gaussian uses three terms, converges in as few passes."""
+    c = ctx()
+    m, n, d = 1 << 16, 128, 512
+    A, b, _ = ill_conditioned_problem(m, n, seed=1003, kappa=1e6, noise=1e-4)
+    Ad, bd = dev(A), dev(b)
+    kap = {}
+    for t in ("1", "2", "3"):
+        SA, _ = c.sketch(Ad, bd, d, kind="gaussian", seed=4, variant=t)
+        kap[t] = _kappa_ARinv(A, SA.cpu().numpy())
+    SAc, _ = c.sketch(Ad, bd, d, kind="countsketch", seed=4)
+    kap["cs"] = _kappa_ARinv(A, SAc.cpu().numpy())
+    print("kappa(A R^-1):", {k: round(v, 2) for k, v in kap.items()})
+    assert kap["1"] > 50
+    assert kap["3"] <= 2 * kap["cs"] + 1 and kap["2"] < kap["1"]
+    x3, i3 = c.lstsq(Ad, bd, d, kind="gaussian", seed=4, tol=1e-6, max_iter=400)
+    xc, ic = c.lstsq(Ad, bd, d, kind="countsketch", seed=4, tol=1e-6, max_iter=400)
+    assert i3.status == 0 and ic.status == 0
+    assert i3.iters <= 2 * ic.iters + 4, (i3.iters, ic.iters)
+    assert OL.eta(A.astype(np.float64), b.astype(np.float64), x3.cpu().numpy()) <= 1.5e-6
 
 
 def test_consistent_system_exact():
