@@ -6,7 +6,9 @@
 // stream 2 and sorted ascending.  Rows m..m'-1 of [A | b] are zero.
 //
 // H_{m'} = H_{m1} (x) H_{m2} with m2 = min(m', 1024) and the row index split as
-// i = i1 * m2 + i2.  Pass 1 transforms every 1024-row block over i2 (a warp
+// i = i1 * m2 + i2.  FP32 with m' >= 1024 and d <= 1024 runs as one pass
+// (srht_fused_f32: each block's transform stays in shared memory and the
+// sampled rows accumulate in registers); otherwise pass 1 transforms every 1024-row block over i2 (a warp
 // holds one column of the block: 5 butterfly stages across its 32 registers,
 // 5 across lanes by shuffles) and keeps only outputs p2 that some sampled row
 // needs.  Pass 2 forms each sampled row p = p1 * m2 + p2 as
@@ -33,9 +35,14 @@ static int64_t np2(int64_t m) {
   return p;
 }
 
+// The one-pass FP32 form (srht_fused_f32) takes m' >= 1024 and d <= 1024 and
+// needs no Y: one d x 16 partial per CTA, at most kFusedSlots CTAs.
+constexpr int64_t kFusedMaxD = 1024;
+constexpr int kFusedSlots = 256;
 struct SrhtLayout {
   int64_t mp, m1, m2, q, ldy;
-  size_t off_sample, off_need, off_nlist, off_y, bytes;
+  bool fused;
+  size_t off_sample, off_need, off_nlist, off_y, off_part, off_bits, bytes;
 };
 static SrhtLayout srht_layout(int64_t m, int64_t n, int64_t d, bool f64) {
   SrhtLayout L{};
@@ -44,12 +51,17 @@ static SrhtLayout srht_layout(int64_t m, int64_t n, int64_t d, bool f64) {
   L.m1 = L.mp / L.m2;
   L.q = n + 1;
   L.ldy = (L.q + 3) & ~(int64_t)3;                 // 16-byte rows for vector stores
+  L.fused = !f64 && L.m2 == kM2 && d <= kFusedMaxD;
   size_t off = 0;
   auto take = [&](size_t b) { size_t o = off; off += (b + 255) & ~(size_t)255; return o; };
   L.off_sample = take((size_t)d * 4);
   L.off_need = take((size_t)L.m2);
   L.off_nlist = take((size_t)(L.m2 + 1) * 4);
-  L.off_y = take((size_t)L.mp * L.ldy * (f64 ? 8 : 4));
+  if (L.fused) {
+    L.off_part = take((size_t)kFusedSlots * d * 16 * 4);
+    L.off_bits = take((size_t)L.mp / 8);
+  }
+  else L.off_y = take((size_t)L.mp * L.ldy * (f64 ? 8 : 4));
   L.bytes = off;
   return L;
 }
@@ -323,12 +335,11 @@ srht_pass1(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, int64_
             x[k + s] = a - bb;
           }
 #pragma unroll
-      for (int s = 1; s < 32; s <<= 1)          // strides 1..16 across lanes
+      for (int s = 1; s < 32; s <<= 1) {        // strides 1..16 across lanes: o - x or x + o
+        const T sg = (lane & s) ? T(-1) : T(1);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const T o = __shfl_xor_sync(0xffffffffu, x[k], s);
-          x[k] = (lane & s) ? (o - x[k]) : (x[k] + o);
-        }
+        for (int k = 0; k < 32; ++k) x[k] = fma(sg, x[k], __shfl_xor_sync(0xffffffffu, x[k], s));
+      }
 #pragma unroll
       for (int k = 0; k < 32; ++k) col[32 * k + lane] = x[k];
     }
@@ -354,6 +365,34 @@ srht_pass1(const T* __restrict__ A, int64_t lda, const T* __restrict__ b, int64_
     const int c = (int)(e % kSrhtCT);
     if (c < ncol && need[p2]) Y[(r0 + p2) * ldy + c0 + c] = tile[(int64_t)c * ldt + p2];
   }
+}
+
+// In-place unnormalised 1024-point Walsh-Hadamard transform of one column by
+// one warp: lane l holds x[k] = col[32 k + l]; 5 butterfly stages across the
+// registers (strides 32 s), 5 across lanes by shuffles (strides 1..16).  In a
+// lane stage the lane with the stride bit set keeps o - x, the other x + o:
+// one FMA with a per-lane sign of +-1 (exact multiply, the sum rounded once).
+SNS_D void fwht1024_warp(float* col, int lane) {
+  float x[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) x[k] = col[32 * k + lane];
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1)
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if ((k & sft) == 0) {
+        const float a = x[k], bb = x[k + sft];
+        x[k] = a + bb;
+        x[k + sft] = a - bb;
+      }
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const float sg = (lane & sft) ? -1.f : 1.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = fmaf(sg, x[k], __shfl_xor_sync(0xffffffffu, x[k], sft));
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) col[32 * k + lane] = x[k];
 }
 
 // Pass 1 for FP32 with 1024-row blocks: 16 columns per tile; each thread loads
@@ -410,30 +449,7 @@ srht_pass1_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
   }
   __syncthreads();
   const int lane = tid & 31, w = tid >> 5;
-  for (int c = w; c < ncol; c += blockDim.x / 32) {
-    float* col = tile + c * kLdt1;
-    float x[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) x[k] = col[32 * k + lane];
-#pragma unroll
-    for (int sft = 1; sft < 32; sft <<= 1)
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if ((k & sft) == 0) {
-          const float a = x[k], bb = x[k + sft];
-          x[k] = a + bb;
-          x[k + sft] = a - bb;
-        }
-#pragma unroll
-    for (int sft = 1; sft < 32; sft <<= 1)
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float o = __shfl_xor_sync(0xffffffffu, x[k], sft);
-        x[k] = (lane & sft) ? (o - x[k]) : (x[k] + o);
-      }
-#pragma unroll
-    for (int k = 0; k < 32; ++k) col[32 * k + lane] = x[k];
-  }
+  for (int c = w; c < ncol; c += blockDim.x / 32) fwht1024_warp(tile + c * kLdt1, lane);
   __syncthreads();
   const int nneed = nlist[kM2];
   if (vec) {
@@ -450,6 +466,139 @@ srht_pass1_f32(const float* __restrict__ A, int64_t lda, const float* __restrict
         Y[(r0 + p2) * ldy + c0 + c] = tile[c * kLdt1 + p2];
       }
     }
+  }
+}
+
+// One pass for FP32 with 1024-row blocks and d <= 32 * SPT: CTA per (column
+// tile of 16, range of blocks i1).  Per block: D [A | b] into shared memory
+// (the signs from the bit array srht_sign_bits wrote)
+// (rows as float4 when the tile lies in an aligned A), the 1024-point
+// transform of each column (warp per column), then every sampled row k adds
+// its term (-1)^popcount(p1_k & i1) Y[i1, p2_k, c] into the CTA's d x 16
+// partial in shared memory (thread: column c = tid mod 16, samples tid / 16 +
+// 32 j; each entry has one owner, so plain adds in block order).  The
+// next block's loads are issued before the transform, so they overlap it.
+// Y never leaves the SM; the CTA writes its d x 16 partial, and
+// srht_fused_reduce adds the CTAs of a column tile in CTA order.
+constexpr int kFT = 16;
+constexpr int kFThreads = 512;
+
+// The signs of D as bits: bit t of word w is set when row 32 w + t gets -1
+// (bit 63 of its stream-1 key).  Rows past m carry no data (their loads are
+// zero), so their bits do not matter.
+__global__ void __launch_bounds__(256)
+srht_sign_bits(int64_t nwords, uint64_t s_sign, uint32_t* __restrict__ bits) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = 0;
+#pragma unroll 4
+    for (int t = 0; t < 32; ++t) v |= (uint32_t)(splitmix_at(s_sign, (uint64_t)(32 * w + t)) >> 63) << t;
+    bits[w] = v;
+  }
+}
+struct SrhtFusedGrid {
+  int nfull, gf, gb, ctas;
+};
+template <int SPT>
+__global__ void __launch_bounds__(kFThreads, 1)
+srht_fused_f32(const float* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t m, int64_t n,
+               int64_t m1, SrhtFusedGrid fg, const uint32_t* __restrict__ sbits, const int32_t* __restrict__ sample,
+               int64_t d, float* __restrict__ part) {
+  extern __shared__ __align__(16) float fsm[];
+  float* tile = fsm;                                             // [kFT][kLdt1]
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(tile + kFT * kLdt1);   // [kM2 / 32] sign bits of the block
+  uint32_t* smp = sgn + kM2 / 32;                                // [d]: p1 * 1024 + p2 (p < 2^31)
+  float* sacc = reinterpret_cast<float*>(smp + d);               // [d][kFT] the CTA's partial
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int bid = blockIdx.x;
+  const bool full = bid < fg.nfull * fg.gf;
+  const int tix = full ? bid / fg.gf : fg.nfull;
+  const int g = full ? bid % fg.gf : bid - fg.nfull * fg.gf;
+  const int G = full ? fg.gf : fg.gb;
+  const int64_t q = n + 1;
+  const int64_t c0 = (int64_t)tix * kFT;
+  const int ncol = (int)min((int64_t)kFT, q - c0);
+  const int64_t ib = m1 * g / G, ie = m1 * (g + 1) / G;        // this CTA's blocks
+  for (int64_t k = tid; k < d; k += blockDim.x) smp[k] = (uint32_t)sample[k];
+  for (int64_t e = tid; e < d * kFT; e += blockDim.x) sacc[e] = 0.f;
+  const bool vec = c0 + kFT <= n && (lda & 3) == 0 && ((uintptr_t)A & 15) == 0;
+  const int rsub = tid >> 2, c4 = tid & 3;                      // rows rsub + 128 u, columns 4 c4 ..
+  float4 v[8];
+  auto load = [&](int64_t i1) {
+    const int64_t r0 = i1 * kM2;
+    if (vec) {
+      const float* p = A + (r0 + rsub) * lda + c0 + 4 * c4;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (r0 + rsub + 128 * u < m) ? __ldg(reinterpret_cast<const float4*>(p + (int64_t)u * 128 * lda))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t row = r0 + rsub + 128 * u;
+        float e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t col = c0 + 4 * c4 + t;
+          e[t] = (row < m && col < q) ? (col < n ? __ldg(A + row * lda + col) : __ldg(b + row)) : 0.f;
+        }
+        v[u] = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+  };
+  const int cc = tid & (kFT - 1), kk = tid >> 4;
+  if (ib < ie) load(ib);
+  for (int64_t i1 = ib; i1 < ie; ++i1) {
+    if (tid < kM2 / 32) sgn[tid] = __ldg(sbits + i1 * (kM2 / 32) + tid);
+    __syncthreads();                                             // also: the previous block's tile reads are done
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int rl = rsub + 128 * u;
+      const uint32_t neg = ((sgn[rl >> 5] >> (rl & 31)) & 1u) << 31;     // D: flip the sign bit
+      float* t = tile + (4 * c4) * kLdt1 + rl;
+      t[0] = __uint_as_float(__float_as_uint(v[u].x) ^ neg);
+      t[kLdt1] = __uint_as_float(__float_as_uint(v[u].y) ^ neg);
+      t[2 * kLdt1] = __uint_as_float(__float_as_uint(v[u].z) ^ neg);
+      t[3 * kLdt1] = __uint_as_float(__float_as_uint(v[u].w) ^ neg);
+    }
+    __syncthreads();
+    if (i1 + 1 < ie) load(i1 + 1);
+    if (w < ncol) fwht1024_warp(tile + w * kLdt1, lane);
+    __syncthreads();
+    if (cc < ncol) {
+      const float* col = tile + cc * kLdt1;
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        const int64_t k = kk + 32 * j;
+        if (k < d) {
+          const uint32_t p = smp[k];
+          // (-1)^popcount(p1 & i1) applied to the sign bit (p1 = p / 1024, i1 < 2^21)
+          const uint32_t neg = (uint32_t)__popc((p >> 10) & (uint32_t)i1) << 31;
+          sacc[k * kFT + cc] += __uint_as_float(__float_as_uint(col[p & (kM2 - 1)]) ^ neg);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* out = part + (size_t)bid * d * kFT;
+  for (int64_t e = tid; e < d * kFT; e += blockDim.x) out[e] = sacc[e];
+}
+
+// SA and Sb from the fused partials: entry (k, j) of column tile j / 16 is the
+// sum over that tile's CTAs, in CTA order, times 1/sqrt(d).
+__global__ void __launch_bounds__(256)
+srht_fused_reduce(const float* __restrict__ part, int64_t d, int64_t n, SrhtFusedGrid fg, float scale,
+                  float* __restrict__ SA, int64_t ldsa, float* __restrict__ Sb, int64_t sbs) {
+  const int64_t q = n + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d * q; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / q, j = e - k * q;
+    const int64_t tix = j / kFT;
+    const bool full = tix < fg.nfull;
+    const int64_t cta0 = full ? tix * fg.gf : (int64_t)fg.nfull * fg.gf;
+    const int G = full ? fg.gf : fg.gb;
+    float s = 0.f;
+    for (int g = 0; g < G; ++g) s += __ldg(part + ((size_t)(cta0 + g) * d + k) * kFT + (j - tix * kFT));
+    if (j < n) SA[k * ldsa + j] = s * scale;
+    else Sb[k * sbs] = s * scale;
   }
 }
 
@@ -522,6 +671,47 @@ srht_pass2_split(const T* __restrict__ Y, int64_t ldy, int64_t q, int64_t m1, in
   }
 }
 
+// Column tiles of 16 and their CTA groups for srht_fused_f32: the full tiles
+// get gf CTAs each and a last partial tile (holding b) the SMs left.  A block
+// of the partial tile costs about half a full one (measured: 2.9 vs 6.3 us),
+// so it counts as half a tile when the SMs are shared out.
+static SrhtFusedGrid srht_fused_grid(int64_t q, int64_t m1) {
+  SrhtFusedGrid fg{};
+  const int sms = std::min(num_sms(), kFusedSlots);
+  const int nfull = (int)(q / kFT);
+  const bool rem = q % kFT != 0;
+  fg.nfull = nfull;
+  if (nfull == 0) {
+    fg.gf = 1;
+    fg.gb = sms;
+  } else if (!rem) {
+    fg.gf = std::max(1, sms / nfull);
+  } else {
+    fg.gf = std::max(1, (2 * sms) / (2 * nfull + 1));
+    fg.gb = std::max(1, sms - nfull * fg.gf);
+  }
+  fg.gf = (int)std::min<int64_t>(fg.gf, m1);
+  fg.gb = (int)std::min<int64_t>(fg.gb, m1);
+  fg.ctas = nfull * fg.gf + (rem ? fg.gb : 0);
+  return fg;
+}
+
+template <int SPT>
+static sns_status srht_fused_launch(const DenseArgs& a, const SrhtLayout& L, const SrhtFusedGrid& fg,
+                                    const uint32_t* sbits, const int32_t* sample, int64_t d, float* part,
+                                    cudaStream_t st) {
+  const size_t smem = ((size_t)kFT * kLdt1 + kM2 / 32) * 4 + (size_t)d * 4 + (size_t)d * kFT * 4;
+  SNS_CUDA_TRY(raise_smem_limit((const void*)srht_fused_f32<SPT>));
+  {
+    SNS_PROF(K_SRHT_PASS1, st);
+    srht_fused_f32<SPT><<<(unsigned)fg.ctas, kFThreads, smem, st>>>(static_cast<const float*>(a.A), a.lda,
+                                                                     static_cast<const float*>(a.b), a.m, a.n, L.m1,
+                                                                     fg, sbits, sample, d, part);
+  }
+  SNS_LAUNCH_CHECK();
+  return SNS_OK;
+}
+
 template <typename T>
 static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, int64_t ldsa, T* Sb, int64_t sbs,
                            uint8_t* ws, const SrhtLayout& L, cudaStream_t st) {
@@ -532,6 +722,31 @@ static sns_status srht_run(const DenseArgs& a, int64_t d, uint64_t seed, T* SA, 
   sns_status s = srht_sample(L.mp, d, seed, sample, need, nlist, L.m2, st);
   if (s != SNS_OK) return s;
   const uint64_t s_sign = stream_state(seed, kStreamSrhtSign);
+  if constexpr (sizeof(T) == 4) {
+    if (L.fused) {
+      const SrhtFusedGrid fg = srht_fused_grid(L.q, L.m1);
+      if (fg.ctas > kFusedSlots) return SNS_EINVAL;
+      float* part = reinterpret_cast<float*>(ws + L.off_part);
+      uint32_t* sbits = reinterpret_cast<uint32_t*>(ws + L.off_bits);
+      {
+        SNS_PROF(K_SRHT_SAMPLE, st);
+        srht_sign_bits<<<(unsigned)std::min<int64_t>((L.mp / 32 + 255) / 256, num_sms() * 8), 256, 0, st>>>(
+            L.mp / 32, s_sign, sbits);
+      }
+      SNS_LAUNCH_CHECK();
+      s = d <= 256   ? srht_fused_launch<8>(a, L, fg, sbits, sample, d, part, st)
+          : d <= 512 ? srht_fused_launch<16>(a, L, fg, sbits, sample, d, part, st)
+                     : srht_fused_launch<32>(a, L, fg, sbits, sample, d, part, st);
+      if (s != SNS_OK) return s;
+      {
+        SNS_PROF(K_SRHT_PASS2, st);
+        srht_fused_reduce<<<num_sms() * 4, 256, 0, st>>>(part, d, a.n, fg, (float)(1.0 / std::sqrt((double)d)), SA,
+                                                         ldsa, Sb, sbs);
+      }
+      SNS_LAUNCH_CHECK();
+      return SNS_OK;
+    }
+  }
   const bool fast = sizeof(T) == 4 && L.m2 == kM2 && a.lda % 4 == 0 && (uintptr_t)a.A % 16 == 0;
   if (fast) {
     const int64_t ntile = (L.q + kT1 - 1) / kT1;
