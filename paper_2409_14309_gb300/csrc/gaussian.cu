@@ -200,13 +200,17 @@ SNS_D uint64_t u_desc(uint32_t addr) {
   d |= (uint64_t)1 << 46;                                   // descriptor version
   return d;                                                 // no swizzle
 }
+// Bounded wait on an mbarrier phase.  Each try suspends the thread until the
+// phase completes or kUSuspendNs pass (a waiting warp then takes no issue
+// slots from the working ones); kUWait tries bound the wait (~17 s).
+constexpr uint32_t kUSuspendNs = 1000;
 SNS_D bool u_wait(uint64_t* bar, uint32_t parity) {
   for (long long it = 0; it < kUWait; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0,1,0,p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0,1,0,p;\n\t}"
         : "=r"(ok)
-        : "r"(u_smem(bar)), "r"(parity)
+        : "r"(u_smem(bar)), "r"(parity), "r"(kUSuspendNs)
         : "memory");
     if (ok) return true;
   }
