@@ -4,9 +4,10 @@ to m' = 2^ceil(log2 m) rows).  SA and Sb within ||SA_gpu - SA_ref||_F /
 ||[A | b]||_F <= 1e-6 for FP32 data (1e-13 for FP64 data).  Each output row is
 a signed sum over all m' rows, so a wrong sampled row or sign shows up as an
 O(1) relative error, not a rounding one.  The cases cover both samplers
-(shared-memory bitmap for m' <= 2^20, hash set above), the 1024-row-block fast
-path and the generic path (m' < 1024, lda not a multiple of 4, FP64), ragged
-m and d = m'."""
+(shared-memory bitmap for m' <= 2^20, hash set above), the one-pass FP32 form
+(m' >= 1024, d <= 1024, with and without a b-only column tile, aligned and
+unaligned rows), the two-pass forms (d > 1024; m' < 1024; FP64), ragged m and
+d = m'."""
 import numpy as np
 import pytest
 
@@ -31,6 +32,29 @@ def test_srht_dense_f32(m, n, d):
     scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
     assert rel_fro(SA.cpu().numpy(), OS.srht_apply(A, d, m % 97), scale) <= TOL32
     assert rel_fro(Sb.cpu().numpy(), OS.srht_apply(b, d, m % 97), scale) <= TOL32
+
+
+@pytest.mark.parametrize("m,n,d,pad", [(5000, 31, 200, 0), (70001, 47, 300, 3), (20000, 256, 1024, 1)])
+def test_srht_one_pass_tiles_and_strides(m, n, d, pad):
+    """The one-pass FP32 form (m' >= 1024, d <= 1024): n + 1 a multiple of the
+    16-column tile (no b-only tile), and rows padded so that lda is not a
+    multiple of 4 (element loads instead of float4) with a partial last tile."""
+    import torch
+    c = ctx()
+    rng = np.random.default_rng(m + n + pad)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    big = torch.zeros((m, n + pad), dtype=torch.float32, device="cuda")
+    big[:, :n] = dev(A)
+    Ad = big[:, :n]
+    assert Ad.stride(0) == n + pad
+    SA, Sb = c.sketch(Ad, dev(b), d, kind="srht", seed=7)
+    scale = np.sqrt(np.linalg.norm(A.astype(np.float64)) ** 2 + np.linalg.norm(b.astype(np.float64)) ** 2)
+    assert rel_fro(SA.cpu().numpy(), OS.srht_apply(A, d, 7), scale) <= TOL32
+    assert rel_fro(Sb.cpu().numpy(), OS.srht_apply(b, d, 7), scale) <= TOL32
+    # bitwise repeatable: fixed block order inside a CTA, CTA order in the reduction
+    SA2, Sb2 = c.sketch(Ad, dev(b), d, kind="srht", seed=7)
+    assert torch.equal(SA, SA2) and torch.equal(Sb, Sb2)
 
 
 @pytest.mark.parametrize("m,n,d", [(9, 3, 4), (4097, 10, 100)])
