@@ -118,3 +118,70 @@ def test_gaussian_table_matches_oracle(lib):
     bits = np.array(sns.gaussian_table_bits(), dtype=np.uint32)
     lib_vals = (bits << 16).astype(np.uint32).view(np.float32).astype(np.float64)
     assert np.array_equal(lib_vals, OS.gaussian_table())
+
+
+def test_gaussian_terms_and_solve_defaults(lib):
+    """Gaussian variant = BF16 terms of [A | b] (0 = auto, 1..3): out-of-range
+    values are refused; split tiles need more workspace; a solve resolves auto
+    to three terms, a sketch to one."""
+    from paper_2409_14309_gb300 import abi
+    sz = C.c_size_t()
+    p = _prob(m=100000, n=64)
+    ws = {}
+    for v in (0, 1, 2, 3):
+        sk = abi.sns_sketch_desc(kind=abi.SNS_GAUSSIAN, variant=v, d=256, seed=1)
+        assert lib.snsolve_sketch_workspace_size(C.byref(p), C.byref(sk), C.byref(sz)) == 0
+        ws[v] = sz.value
+    assert ws[0] == ws[1] < ws[2] < ws[3]
+    for v in (-1, 4):
+        sk = abi.sns_sketch_desc(kind=abi.SNS_GAUSSIAN, variant=v, d=256, seed=1)
+        assert lib.snsolve_sketch_workspace_size(C.byref(p), C.byref(sk), C.byref(sz)) == 1
+    ls = {}
+    for v in (0, 1, 3):
+        op = abi.sns_opts(sk=abi.sns_sketch_desc(kind=abi.SNS_GAUSSIAN, variant=v, d=256, seed=1), tol=1e-6)
+        assert lib.snsolve_lstsq_workspace_size(C.byref(p), C.byref(op), C.byref(sz)) == 0
+        ls[v] = sz.value
+    assert ls[0] == ls[3] > ls[1]
+
+
+def test_csr_reproducible_solve_size_limit(lib):
+    """CountSketch variant SORTED on CSR asks for the reproducible solve, whose
+    passes keep per-warp rows of n doubles: n up to 1422 is accepted, larger n
+    refused; the default variant has no such limit."""
+    from paper_2409_14309_gb300 import abi
+    sz = C.c_size_t()
+
+    def csr(n):
+        return abi.sns_problem(m=100000, n=n, fmt=abi.SNS_CSR_F32, rowptr=0x1000, col=0x2000, val=0x3000,
+                               nnz=10, b=0x4000)
+
+    def op(variant, n):
+        return abi.sns_opts(sk=abi.sns_sketch_desc(kind=abi.SNS_COUNTSKETCH, variant=variant, d=2 * n, seed=1),
+                            tol=1e-8)
+    assert lib.snsolve_lstsq_workspace_size(C.byref(csr(1422)), C.byref(op(abi.SNS_CS_SORTED, 1422)),
+                                            C.byref(sz)) == 0
+    assert lib.snsolve_lstsq_workspace_size(C.byref(csr(1423)), C.byref(op(abi.SNS_CS_SORTED, 1423)),
+                                            C.byref(sz)) == 1
+    assert lib.snsolve_lstsq_workspace_size(C.byref(csr(1500)), C.byref(op(abi.SNS_CS_AUTO, 1500)),
+                                            C.byref(sz)) == 0
+
+
+def test_srht_workspace_one_pass_form_needs_no_y(lib):
+    """FP32 SRHT with m' >= 1024 and d <= 1024 runs in one pass: its workspace
+    holds per-CTA partials and sign bits, far less than the transformed copy Y
+    (m' x (n + 1) floats) that the two-pass form (d > 1024, FP64) needs."""
+    from paper_2409_14309_gb300 import abi
+    sz = C.c_size_t()
+    m, n = 100000, 64
+    mp = 1 << 17
+    y_bytes = mp * (n + 4) * 4
+    p32 = _prob(m=m, n=n)
+    sk = abi.sns_sketch_desc(kind=abi.SNS_SRHT, d=512, seed=1)
+    assert lib.snsolve_sketch_workspace_size(C.byref(p32), C.byref(sk), C.byref(sz)) == 0
+    assert sz.value < y_bytes
+    sk_big = abi.sns_sketch_desc(kind=abi.SNS_SRHT, d=2048, seed=1)
+    assert lib.snsolve_sketch_workspace_size(C.byref(p32), C.byref(sk_big), C.byref(sz)) == 0
+    assert sz.value >= y_bytes
+    p64 = _prob(m=m, n=n, fmt=abi.SNS_DENSE_F64)
+    assert lib.snsolve_sketch_workspace_size(C.byref(p64), C.byref(sk), C.byref(sz)) == 0
+    assert sz.value >= 2 * y_bytes
